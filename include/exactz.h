@@ -1,0 +1,186 @@
+/*
+ * exactz.h -- C ABI of the B300 (sm_103a) EXaCTz topology correction.
+ *
+ * The operation (Li et al., EXaCTz, Sec. 4.1 problem statement and Algorithm 1):
+ * given an original float32 scalar field f on a regular grid, an error-bounded
+ * decompressed version f_hat with |f_hat - f| <= xi, and the bound xi, edit
+ * f_hat by monotone decreasing steps of Delta = xi / N (Sec. 3.3) until, on the
+ * Freudenthal triangulation of the grid with ties broken by vertex index
+ * (Sec. 3.3 footnote):
+ *   - every vertex has the same steepest-ascent and steepest-descent vertex in
+ *     its closed neighbourhood as in f (EG constraints, Sec. 4.2);
+ *   - every vertex that is a saddle of f or of the edited field orders against
+ *     all its neighbours as in f (Sec. 4.2, saddles);
+ *   - all critical points of f keep f's global order (reformulated event
+ *     constraints, Sec. 4.3, which subsume the saddle-ordering constraint C2).
+ * A vertex needing more than N edits stores the lossless bound fl(f - xi).
+ * The result is the edited field g, the sparse edit list and the number of
+ * edit passes; at the fixpoint the extremum graphs and the contour tree of g
+ * equal those of f.
+ *
+ * Layout: a field of dims (nx, ny, nz) is nx*ny*nz float32 values with x
+ * fastest: vertex index = x + nx * (y + ny * z).  nz = 1 gives a 2D field,
+ * ny = nz = 1 a 1D field.  Every dimension must be >= 1 and the field must hold
+ * at least 2 vertices and fewer than 2^40.
+ *
+ * Memory: unless a call says otherwise, every array pointer is a DEVICE pointer
+ * owned by the caller (for example a torch CUDA tensor's data pointer).  The
+ * library never frees caller memory.  It allocates its own device workspace
+ * (about 40-70 bytes per vertex, depending on the number of critical points):
+ * exactz_correct / exactz_correct_batch allocate and free it inside the call;
+ * an exactz_workspace keeps it across calls.
+ *
+ * Streams: `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Every call is synchronous with respect to that stream on return: the
+ * results are in device memory and the result structs are filled.  There is
+ * no CPU fallback: without a usable CUDA device every call returns
+ * EXACTZ_ENODEV.
+ */
+#ifndef EXACTZ_H
+#define EXACTZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes (negative = error, the call did not produce a result). */
+#define EXACTZ_OK 0
+#define EXACTZ_EINVAL (-1)     /* bad dims, xi <= 0 or non-finite, N out of [1, 254], NULL pointer */
+#define EXACTZ_ENONFINITE (-2) /* NaN or Inf in f or f_hat */
+#define EXACTZ_EBOUND (-3)     /* some f_hat_i < fl(f_i - xi) or f_hat_i > fl(f_i + xi) */
+#define EXACTZ_ENOMEM (-4)     /* device allocation failed */
+#define EXACTZ_ECAP (-5)       /* edit list longer than edits_cap: first edits_cap records written */
+#define EXACTZ_ENODEV (-6)     /* no CUDA device / CUDA error */
+#define EXACTZ_ESIZE (-7)      /* workspace too small for these fields */
+
+/* Positive outcome codes in exactz_result.status. */
+#define EXACTZ_CONVERGED 1   /* no constraint is violated */
+#define EXACTZ_STUCK 2       /* violations remain only on vertices already at fl(f - xi) */
+#define EXACTZ_ITER_LIMIT 3  /* opts.max_iters edit passes done, violations remain */
+
+/* Iteration strategies (opts.mode). */
+#define EXACTZ_MODE_PLAIN 0     /* Algorithm 1 literally: full sweep each pass, host-driven loop */
+#define EXACTZ_MODE_FRONTIER 1  /* re-check only tiles touched by last pass's edits, host-driven loop */
+#define EXACTZ_MODE_GRAPH 2     /* frontier passes in a CUDA graph; device-side while-loop exit */
+
+typedef struct {
+    uint32_t nx, ny, nz;
+} exactz_dims;
+
+typedef struct {
+    uint32_t N;              /* edit steps per vertex before the lossless bound (paper: 5) */
+    uint32_t mode;           /* EXACTZ_MODE_* (default EXACTZ_MODE_GRAPH) */
+    uint64_t max_iters;      /* cap on edit passes (0 = no edit is applied) */
+    uint32_t want_edit_list; /* 0: skip the edit-list compaction */
+    uint32_t profile;        /* 1: time the stages with CUDA events (see exactz_ws_stats) */
+} exactz_opts;
+
+/* One applied edit.  value = g at idx; k = number of decrements applied (1..N)
+ * or N+1 for the lossless bound fl(f - xi) (lossless = 1).  16 bytes. */
+typedef struct {
+    uint64_t idx;
+    float value;
+    uint8_t k;
+    uint8_t lossless;
+    uint16_t reserved;
+} exactz_edit;
+
+typedef struct {
+    uint64_t iterations;          /* edit passes executed */
+    uint64_t n_edits;             /* vertices with k > 0 */
+    uint64_t n_lossless;          /* vertices with k = N + 1 */
+    uint64_t residual_violations; /* |request set| at exit (0 when converged) */
+    uint64_t n_critical;          /* critical points of f */
+    int32_t status;               /* EXACTZ_CONVERGED / _STUCK / _ITER_LIMIT, or a negative error */
+    int32_t reserved;
+} exactz_result;
+
+/* Fill *o with the defaults: N = 5, mode = GRAPH, max_iters = 1000000,
+ * want_edit_list = 1. */
+void exactz_default_opts(exactz_opts *o);
+
+/* Correct one field (Algorithm 1).  f, fhat, g_out: device arrays of n floats
+ * (g_out may alias neither input).  edits_out: device array of edits_cap
+ * records, or NULL with edits_cap = 0 (then only counts are returned).
+ * opts may be NULL (defaults).  Returns EXACTZ_OK, EXACTZ_ECAP (result valid,
+ * list truncated) or a negative error; res->status holds the outcome. */
+int exactz_correct(const float *f, const float *fhat, exactz_dims d, float xi,
+                   const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
+                   uint64_t edits_cap, exactz_result *res, void *cuda_stream);
+
+/* Correct nfields independent fields in one run: every pass of the loop
+ * covers all fields still violating a constraint (one launch per stage per
+ * pass over all of them).  Arrays of per-field device pointers / values are
+ * HOST arrays of length nfields; edits_out / edits_cap may be NULL.  Each
+ * field's result equals what exactz_correct returns for it alone.
+ * Returns the first error met (per-field status in res[i]). */
+int exactz_correct_batch(uint32_t nfields, const float *const *f, const float *const *fhat,
+                         const exactz_dims *d, const float *xi, const exactz_opts *opts,
+                         float *const *g_out, exactz_edit *const *edits_out,
+                         const uint64_t *edits_cap, exactz_result *res, void *cuda_stream);
+
+/* ---- reusable workspace (allocation outside the timed / serving path) ---- */
+
+typedef struct exactz_workspace exactz_workspace;
+
+/* Plan device memory for up to nfields fields of the given dims (a HOST
+ * array).  Any later call may pass fields whose vertex count does not exceed
+ * the planned one field by field.  Returns NULL on failure (no device or out
+ * of memory). */
+exactz_workspace *exactz_workspace_create(uint32_t nfields, const exactz_dims *dims);
+void exactz_workspace_destroy(exactz_workspace *ws);
+/* Device bytes held by the workspace. */
+uint64_t exactz_workspace_bytes(const exactz_workspace *ws);
+
+/* exactz_correct_batch on a workspace (same arguments and results).  With
+ * host_buffers = 1 every f / fhat / g_out / edits_out pointer is a HOST
+ * pointer: the call copies inputs in and results out (both inside the call,
+ * on cuda_stream), using device staging buffers held by the workspace. */
+int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const *f,
+                      const float *const *fhat, const exactz_dims *d, const float *xi,
+                      const exactz_opts *opts, float *const *g_out,
+                      exactz_edit *const *edits_out, const uint64_t *edits_cap,
+                      exactz_result *res, void *cuda_stream, int host_buffers);
+
+/* Statistics of the last exactz_ws_correct on a workspace.  stage_ms holds
+ * CUDA-event times on the call's stream when opts.profile was 1 (else 0):
+ * [0] set-up stencil kernel, [1] critical-point compaction, [2] radix sort,
+ * [3] first pass (pair check, apply, bookkeeping), [4] the loop,
+ * [5] residual and status, [6] edit list, [7] whole call on the device. */
+typedef struct {
+    uint64_t kernel_launches; /* kernels the call executed (graph bodies counted per pass) */
+    uint64_t passes;          /* edit passes run for the slowest field, including the last check */
+    uint64_t total_critical;  /* critical points over all fields */
+    float stage_ms[8];
+} exactz_stats;
+
+int exactz_ws_stats(const exactz_workspace *ws, exactz_stats *out);
+
+/* ---- inspection of the set-up stage (Sec. 3.2, Sec. 4.3) ---- */
+
+/* Per-vertex descriptor of field h (device arrays of n entries):
+ *   bits 0-3  rank (0..14) of the steepest-ascent vertex of the closed
+ *             neighbourhood, bits 4-7 that of the steepest-descent vertex,
+ *             where ranks list the closed neighbourhood in increasing vertex
+ *             index (7 = the vertex itself);
+ *   bits 8-21 lower-link mask (bit s for neighbour rank s < 7, s+1 otherwise);
+ *   bit 22    saddle; bit 23 critical point.
+ * type_out (may be NULL): 0 regular, 1 minimum, 2 maximum, 4|8 join|split saddle. */
+int exactz_classify(const float *h, exactz_dims d, uint32_t *desc_out, uint8_t *type_out,
+                    void *cuda_stream);
+
+/* Critical points of f sorted by (value, index) into order_out (device array
+ * of at least n uint64); *count_out (HOST) receives their number. */
+int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t *count_out,
+                    void *cuda_stream);
+
+/* Library build / device information (host string, static storage). */
+const char *exactz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXACTZ_H */

@@ -1,0 +1,111 @@
+"""ctypes declarations of the C ABI in include/exactz.h (marshalling only).
+
+The shared library is loaded from this package directory.  There is no
+fallback: if it is missing or cannot be loaded, importing raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libexactz.so")
+
+EXACTZ_OK = 0
+EXACTZ_EINVAL = -1
+EXACTZ_ENONFINITE = -2
+EXACTZ_EBOUND = -3
+EXACTZ_ENOMEM = -4
+EXACTZ_ECAP = -5
+EXACTZ_ENODEV = -6
+EXACTZ_ESIZE = -7
+ERROR_NAMES = {-1: "EINVAL", -2: "ENONFINITE", -3: "EBOUND", -4: "ENOMEM", -5: "ECAP",
+               -6: "ENODEV", -7: "ESIZE"}
+
+CONVERGED, STUCK, ITER_LIMIT = 1, 2, 3
+MODE_PLAIN, MODE_FRONTIER, MODE_GRAPH = 0, 1, 2
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_uint32), ("ny", ctypes.c_uint32), ("nz", ctypes.c_uint32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_iters", ctypes.c_uint64),
+                ("want_edit_list", ctypes.c_uint32), ("profile", ctypes.c_uint32)]
+
+
+class Edit(ctypes.Structure):
+    _fields_ = [("idx", ctypes.c_uint64), ("value", ctypes.c_float), ("k", ctypes.c_uint8),
+                ("lossless", ctypes.c_uint8), ("reserved", ctypes.c_uint16)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint64), ("n_edits", ctypes.c_uint64),
+                ("n_lossless", ctypes.c_uint64), ("residual_violations", ctypes.c_uint64),
+                ("n_critical", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("passes", ctypes.c_uint64),
+                ("total_critical", ctypes.c_uint64), ("stage_ms", ctypes.c_float * 8)]
+
+
+STAGES = ["setup", "compact", "sort", "first_pass", "loop", "finish", "edit_list", "total"]
+
+assert ctypes.sizeof(Edit) == 16 and ctypes.sizeof(Result) == 48
+
+EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exactz_workspace_create",
+           "exactz_workspace_destroy", "exactz_workspace_bytes", "exactz_ws_correct", "exactz_classify",
+           "exactz_cp_order", "exactz_version", "exactz_ws_stats"]
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree CUDA library (raises if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run paper_2604_01397_b300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    L.exactz_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.exactz_default_opts.restype = None
+    L.exactz_correct.argtypes = [P, P, Dims, ctypes.c_float, ctypes.POINTER(Opts), P, P, ctypes.c_uint64,
+                                 ctypes.POINTER(Result), P]
+    L.exactz_correct.restype = ctypes.c_int
+    L.exactz_correct_batch.argtypes = [ctypes.c_uint32, PP, PP, ctypes.POINTER(Dims),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Opts), PP, PP,
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), P]
+    L.exactz_correct_batch.restype = ctypes.c_int
+    L.exactz_workspace_create.argtypes = [ctypes.c_uint32, ctypes.POINTER(Dims)]
+    L.exactz_workspace_create.restype = P
+    L.exactz_workspace_destroy.argtypes = [P]
+    L.exactz_workspace_destroy.restype = None
+    L.exactz_workspace_bytes.argtypes = [P]
+    L.exactz_workspace_bytes.restype = ctypes.c_uint64
+    L.exactz_ws_correct.argtypes = [P, ctypes.c_uint32, PP, PP, ctypes.POINTER(Dims),
+                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Opts), PP, PP,
+                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), P, ctypes.c_int]
+    L.exactz_ws_correct.restype = ctypes.c_int
+    L.exactz_ws_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.exactz_ws_stats.restype = ctypes.c_int
+    L.exactz_classify.argtypes = [P, Dims, P, P, P]
+    L.exactz_classify.restype = ctypes.c_int
+    L.exactz_cp_order.argtypes = [P, Dims, P, ctypes.POINTER(ctypes.c_uint64), P]
+    L.exactz_cp_order.restype = ctypes.c_int
+    L.exactz_version.argtypes = []
+    L.exactz_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = ctypes.c_void_p(p) if p else None
+    return arr

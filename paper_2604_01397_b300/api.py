@@ -1,0 +1,255 @@
+"""Python front end of the CUDA library: torch tensors in, torch tensors out.
+
+Every function marshals arguments to the C ABI (include/exactz.h) and reads
+the results back; all computation runs in the library's kernels.  Fields are
+float32 tensors of shape (nz, ny, nx) (or flat with explicit dims), contiguous,
+on a CUDA device; the current torch stream is used unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+MODES = {"plain": N.MODE_PLAIN, "frontier": N.MODE_FRONTIER, "graph": N.MODE_GRAPH}
+STATUS = {N.CONVERGED: "CONVERGED", N.STUCK: "STUCK", N.ITER_LIMIT: "ITER_LIMIT"}
+
+
+class ExactzError(RuntimeError):
+    def __init__(self, rc: int, where: str):
+        super().__init__(f"{where}: {N.ERROR_NAMES.get(rc, rc)} ({rc})")
+        self.rc = rc
+
+
+def version() -> str:
+    return N.lib().exactz_version().decode()
+
+
+def dims_of(t: torch.Tensor, dims=None):
+    if dims is not None:
+        nx, ny, nz = (int(d) for d in dims)
+    elif t.dim() == 3:
+        nz, ny, nx = t.shape
+    elif t.dim() == 2:
+        nz, (ny, nx) = 1, t.shape
+    elif t.dim() == 1:
+        nz, ny, nx = 1, 1, t.shape[0]
+    else:
+        raise ValueError("field must be 1D, 2D or 3D")
+    if nx * ny * nz != t.numel():
+        raise ValueError("dims do not match the tensor size")
+    return int(nx), int(ny), int(nz)
+
+
+def _check(t: torch.Tensor, name: str, host: bool = False):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 tensor")
+    if host and t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor for host_buffers")
+    if not host and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU fallback)")
+
+
+def make_opts(N_steps: int = 5, mode: str = "graph", max_iters: int = 1_000_000,
+              want_edit_list: bool = True, profile: bool = False) -> N.Opts:
+    o = N.Opts()
+    N.lib().exactz_default_opts(ctypes.byref(o))
+    o.N = int(N_steps)
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.max_iters = int(max_iters)
+    o.want_edit_list = int(bool(want_edit_list))
+    o.profile = int(bool(profile))
+    return o
+
+
+def default_edits_cap(n: int) -> int:
+    return n if n <= (1 << 26) else n // 4
+
+
+def decode_edits(buf: torch.Tensor, count: int) -> Dict[str, torch.Tensor]:
+    """Split a (cap, 16) uint8 record buffer into idx / value / k / lossless."""
+    count = min(int(count), buf.shape[0])
+    b = buf[:count]
+    return dict(idx=b[:, 0:8].contiguous().view(torch.int64).reshape(-1),
+                value=b[:, 8:12].contiguous().view(torch.float32).reshape(-1),
+                k=b[:, 12].contiguous(),
+                lossless=b[:, 13].contiguous().to(torch.bool))
+
+
+def _result_dict(r: N.Result) -> dict:
+    return dict(iterations=int(r.iterations), n_edits=int(r.n_edits), n_lossless=int(r.n_lossless),
+                residual=int(r.residual_violations), n_critical=int(r.n_critical), status=int(r.status),
+                status_name=STATUS.get(int(r.status), N.ERROR_NAMES.get(int(r.status), str(r.status))))
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Workspace:
+    """Device workspace planned for a list of field dims (x, y, z sizes)."""
+
+    def __init__(self, dims_list: Sequence[Sequence[int]]):
+        self.dims_list = [tuple(int(v) for v in d) for d in dims_list]
+        arr = (N.Dims * len(self.dims_list))(*[N.Dims(*d) for d in self.dims_list])
+        self._h = N.lib().exactz_workspace_create(len(self.dims_list), arr)
+        if not self._h:
+            raise ExactzError(N.EXACTZ_ENOMEM, "exactz_workspace_create")
+
+    def stats(self) -> dict:
+        """Launch count, passes and (with profile=True) per-stage device ms of the last call."""
+        st = N.Stats()
+        N.lib().exactz_ws_stats(self._h, ctypes.byref(st))
+        return dict(kernel_launches=int(st.kernel_launches), passes=int(st.passes),
+                    total_critical=int(st.total_critical),
+                    stage_ms={k: float(v) for k, v in zip(N.STAGES, st.stage_ms)})
+
+    @property
+    def nbytes(self) -> int:
+        return int(N.lib().exactz_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().exactz_workspace_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def correct(self, fs: List[torch.Tensor], fhats: List[torch.Tensor], xis: Sequence[float],
+                dims: Optional[List] = None, N_steps: int = 5, mode: str = "graph",
+                max_iters: int = 1_000_000, edits: bool = True, edits_caps=None,
+                g_out: Optional[List[torch.Tensor]] = None, edit_bufs: Optional[List[torch.Tensor]] = None,
+                stream=None, host_buffers: bool = False, raise_on_error: bool = True,
+                profile: bool = False) -> List[dict]:
+        nf = len(fs)
+        dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
+        for i in range(nf):
+            _check(fs[i], "f", host_buffers)
+            _check(fhats[i], "fhat", host_buffers)
+        if g_out is None:
+            g_out = [torch.empty_like(f) for f in fs]
+        if edits and edit_bufs is None:
+            caps = [default_edits_cap(f.numel()) if edits_caps is None else int(edits_caps[i])
+                    for i, f in enumerate(fs)]
+            dev = None if host_buffers else fs[0].device
+            edit_bufs = [torch.empty((c, 16), dtype=torch.uint8, device=dev) for c in caps]
+        caps = [b.shape[0] for b in edit_bufs] if edits else [0] * nf
+        darr = (N.Dims * nf)(*[N.Dims(*d) for d in dl])
+        xarr = (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis])
+        carr = (ctypes.c_uint64 * nf)(*caps)
+        res = (N.Result * nf)()
+        o = make_opts(N_steps, mode, max_iters, edits, profile)
+        rc = N.lib().exactz_ws_correct(
+            self._h, nf, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
+            darr, xarr, ctypes.byref(o), N.ptr_array([t.data_ptr() for t in g_out]),
+            N.ptr_array([b.data_ptr() for b in edit_bufs] if edits else [0] * nf), carr, res,
+            ctypes.c_void_p(0 if host_buffers and not torch.cuda.is_available() else _stream(stream)),
+            int(host_buffers))
+        if rc not in (N.EXACTZ_OK, N.EXACTZ_ECAP) and raise_on_error:
+            raise ExactzError(rc, "exactz_ws_correct")
+        out = []
+        for i in range(nf):
+            d = _result_dict(res[i])
+            d["rc"] = rc
+            d["g"] = g_out[i]
+            if edits:
+                d["edits"] = decode_edits(edit_bufs[i], d["n_edits"])
+                d["edits_truncated"] = d["n_edits"] > caps[i]
+            out.append(d)
+        return out
+
+
+def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: int = 5,
+            mode: str = "graph", max_iters: int = 1_000_000, edits: bool = True, edits_cap=None,
+            stream=None, raise_on_error: bool = True) -> dict:
+    """Correct one field to its fixpoint (exactz_correct)."""
+    _check(f, "f")
+    _check(fhat, "fhat")
+    d = dims_of(f, dims)
+    g = torch.empty_like(f)
+    cap = default_edits_cap(f.numel()) if edits_cap is None else int(edits_cap)
+    buf = torch.empty((cap if edits else 0, 16), dtype=torch.uint8, device=f.device)
+    res = N.Result()
+    o = make_opts(N_steps, mode, max_iters, edits)
+    rc = N.lib().exactz_correct(ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(fhat.data_ptr()), N.Dims(*d),
+                                ctypes.c_float(float(np.float32(xi))), ctypes.byref(o),
+                                ctypes.c_void_p(g.data_ptr()),
+                                ctypes.c_void_p(buf.data_ptr() if edits and cap else 0),
+                                cap if edits else 0, ctypes.byref(res), ctypes.c_void_p(_stream(stream)))
+    if rc not in (N.EXACTZ_OK, N.EXACTZ_ECAP) and raise_on_error:
+        raise ExactzError(rc, "exactz_correct")
+    out = _result_dict(res)
+    out["rc"] = rc
+    out["g"] = g
+    if edits:
+        out["edits"] = decode_edits(buf, out["n_edits"])
+        out["edits_truncated"] = out["n_edits"] > cap
+    return out
+
+
+def correct_batch(fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "graph",
+                  max_iters: int = 1_000_000, edits: bool = True, edits_caps=None, stream=None,
+                  raise_on_error: bool = True) -> List[dict]:
+    """Correct many independent fields in one run (exactz_correct_batch)."""
+    nf = len(fs)
+    dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
+    for i in range(nf):
+        _check(fs[i], "f")
+        _check(fhats[i], "fhat")
+    gs = [torch.empty_like(f) for f in fs]
+    caps = [default_edits_cap(f.numel()) if edits_caps is None else int(edits_caps[i]) for i, f in enumerate(fs)]
+    bufs = [torch.empty((c if edits else 0, 16), dtype=torch.uint8, device=fs[0].device) for c in caps]
+    res = (N.Result * nf)()
+    o = make_opts(N_steps, mode, max_iters, edits)
+    rc = N.lib().exactz_correct_batch(
+        nf, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
+        (N.Dims * nf)(*[N.Dims(*d) for d in dl]), (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis]),
+        ctypes.byref(o), N.ptr_array([t.data_ptr() for t in gs]),
+        N.ptr_array([b.data_ptr() for b in bufs] if edits else [0] * nf),
+        (ctypes.c_uint64 * nf)(*[c if edits else 0 for c in caps]), res, ctypes.c_void_p(_stream(stream)))
+    if rc not in (N.EXACTZ_OK, N.EXACTZ_ECAP) and raise_on_error:
+        raise ExactzError(rc, "exactz_correct_batch")
+    out = []
+    for i in range(nf):
+        d = _result_dict(res[i])
+        d["rc"] = rc
+        d["g"] = gs[i]
+        if edits:
+            d["edits"] = decode_edits(bufs[i], d["n_edits"])
+        out.append(d)
+    return out
+
+
+def classify(h: torch.Tensor, dims=None, stream=None):
+    """Per-vertex descriptor (int32 bit fields, see exactz.h) and type of field h."""
+    _check(h, "h")
+    d = dims_of(h, dims)
+    desc = torch.empty(h.numel(), dtype=torch.int32, device=h.device)
+    ty = torch.empty(h.numel(), dtype=torch.uint8, device=h.device)
+    rc = N.lib().exactz_classify(ctypes.c_void_p(h.data_ptr()), N.Dims(*d), ctypes.c_void_p(desc.data_ptr()),
+                                 ctypes.c_void_p(ty.data_ptr()), ctypes.c_void_p(_stream(stream)))
+    if rc != N.EXACTZ_OK:
+        raise ExactzError(rc, "exactz_classify")
+    return desc, ty
+
+
+def cp_order(f: torch.Tensor, dims=None, stream=None) -> torch.Tensor:
+    """Critical points of f sorted by (value, index), as int64 vertex indices."""
+    _check(f, "f")
+    d = dims_of(f, dims)
+    out = torch.empty(f.numel(), dtype=torch.int64, device=f.device)
+    cnt = ctypes.c_uint64()
+    rc = N.lib().exactz_cp_order(ctypes.c_void_p(f.data_ptr()), N.Dims(*d), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.byref(cnt), ctypes.c_void_p(_stream(stream)))
+    if rc != N.EXACTZ_OK:
+        raise ExactzError(rc, "exactz_cp_order")
+    return out[: cnt.value]

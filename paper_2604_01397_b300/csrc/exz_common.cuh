@@ -1,0 +1,198 @@
+// exz_common.cuh -- shared device-side definitions of the B300 correction.
+//
+// Grid and order (EXaCTz Sec. 3, Sec. 3.3 footnote): vertices of an
+// nx*ny*nz grid, index x + nx*(y + ny*z); neighbours are the 14 offsets of the
+// Freudenthal triangulation (every component in {0,1}, or every component in
+// {0,-1}); ties in value are broken by vertex index.  The closed
+// neighbourhood of a vertex is listed by "rank" 0..14 in increasing vertex
+// index (rank 7 is the vertex itself), which is the lexicographic order of
+// the offsets by (dz, dy, dx).  A running arg-max with ">=" (arg-min with "<")
+// over ranks in that order therefore implements the index tie-break.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace exz {
+
+// ---------------------------------------------------------------- geometry
+constexpr int TX = 32;   // tile width: one warp per tile row, one cp-bitmap word
+constexpr int TY = 4;
+constexpr int TZ = 4;
+constexpr int TILE_V = TX * TY * TZ;
+constexpr int HXP = TX + 2;  // halo tile row length (x0-1 .. x0+TX)
+constexpr int HY = TY + 2;
+constexpr int HZ = TZ + 2;
+constexpr int HALO_N = HXP * HY * HZ;
+constexpr int CTA = 256;
+constexpr int WARPS = CTA / 32;
+constexpr int ROWS = TY * TZ;
+constexpr int VBLOCK = 4096;  // arena alignment of a field (vertices) = edit-list block
+constexpr int WBLOCK = 2048;  // cp-bitmap alignment of a field (words) = compaction block
+constexpr uint64_t LOCAL_BITS = 40;
+constexpr uint64_t LOCAL_MASK = (1ull << LOCAL_BITS) - 1;
+
+// offset (dx, dy, dz) of rank r; rank 14 - r is the opposite offset
+__host__ __device__ constexpr int rdx(int r)
+{
+    return r == 7 ? 0 : (r < 7 ? ((r & 1) ? 0 : -1) : (((14 - r) & 1) ? 0 : 1));
+}
+__host__ __device__ constexpr int rdy(int r)
+{
+    return r == 7 ? 0 : (r < 7 ? (((r >> 1) & 1) ? 0 : -1) : ((((14 - r) >> 1) & 1) ? 0 : 1));
+}
+__host__ __device__ constexpr int rdz(int r)
+{
+    return r == 7 ? 0 : (r < 7 ? (r < 4 ? -1 : 0) : ((14 - r) < 4 ? 1 : 0));
+}
+// mask bit of rank r (r != 7) and the inverse
+__host__ __device__ constexpr int slot_of(int r) { return r < 7 ? r : r - 1; }
+__host__ __device__ constexpr int rank_of(int s) { return s < 7 ? s : s + 1; }
+// smem offset of rank r inside a halo tile
+__host__ __device__ constexpr int soff(int r) { return rdx(r) + HXP * rdy(r) + HXP * HY * rdz(r); }
+
+// Descriptor bits (per vertex of f)
+constexpr uint32_t D_UP_SHIFT = 0, D_DN_SHIFT = 4, D_MASK_SHIFT = 8;
+constexpr uint32_t D_SADDLE = 1u << 22;
+constexpr uint32_t D_CP = 1u << 23;
+
+// Field errors (FieldState::err bits)
+constexpr uint32_t ERR_NONFINITE = 1, ERR_BOUND = 2;
+// Status codes (match the C ABI)
+constexpr int32_t ST_CONVERGED = 1, ST_STUCK = 2, ST_ITER_LIMIT = 3;
+
+// ------------------------------------------------------------ field table
+struct FieldDesc {
+    uint32_t nx, ny, nz, N;
+    uint64_t n;
+    uint32_t tnx, tny, tnz, pad0;  // tiles per axis (tnx = cp-bitmap words per row)
+    uint64_t tbase;                // first global tile id
+    uint64_t vbase;                // arena offset (vertices): k, desc, cp_rank, request bits
+    uint64_t wbase;                // cp-bitmap offset (words)
+    const float *f;
+    const float *fhat;
+    float *g;
+    float xi, delta;
+    uint64_t max_iters;
+    struct EditRec *edits;  // output edit list (device), may be null
+    uint64_t edits_cap;
+};
+
+// One applied edit; same layout as exactz_edit (16 bytes).
+struct EditRec {
+    uint64_t idx;
+    float value;
+    uint8_t k;
+    uint8_t lossless;
+    uint16_t reserved;
+};
+
+struct FieldState {
+    unsigned long long iterations;
+    unsigned long long cp_base;
+    unsigned long long ncp;
+    unsigned long long capped;      // unpinned requests left unapplied at the cap
+    unsigned long long pinned_res;  // pinned vertices still requested at exit
+    unsigned long long n_edits;
+    unsigned long long n_lossless;
+    uint32_t had_req, done, err, status;
+};
+
+struct LoopState {
+    unsigned long long req_count;
+    unsigned long long tile_count[2];
+    unsigned long long pair_count[2];
+    unsigned long long pin_tile_count;
+    unsigned long long pin_pair_count;
+    unsigned long long total_cp;
+    uint32_t cur;
+    uint32_t any_active;
+    uint32_t pass;
+    uint32_t overflow;
+};
+
+// All device pointers of one workspace, passed to kernels by value.
+struct Dev {
+    const FieldDesc *fields;
+    FieldState *fst;
+    LoopState *ls;
+    uint32_t nfields;
+    uint32_t total_tiles;
+    uint64_t total_v;   // arena vertices (padded)
+    uint64_t total_w;   // cp-bitmap words (padded)
+    uint8_t *k;
+    uint32_t *desc;
+    uint32_t *cp_rank;
+    uint32_t *reqbits;
+    uint32_t *cpwords;
+    unsigned long long *req_list;
+    uint32_t *tile_list[2];
+    uint32_t *tile_bits;
+    uint32_t *pin_tile_list;
+    uint32_t *pin_tile_bits;
+    uint32_t *pair_list[2];
+    uint32_t *pin_pair_list;
+    uint32_t *cp_key[2];
+    unsigned long long *cp_ent[2];
+    unsigned long long *o;  // sorted critical points (aliases one of cp_ent)
+    const uint32_t *multi;  // 2^14-bit table: link subset has >= 2 components
+    uint64_t cp_cap;
+    uint64_t pair_cap;
+    uint64_t req_cap;
+    // scratch for scans, histograms and block counts
+    uint32_t *blk;
+    unsigned long long *blk_off;
+    uint32_t *hist;
+    uint32_t sort_blocks;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t field_of_tile(const Dev &D, uint32_t tile)
+{
+    uint32_t lo = 0, hi = D.nfields - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (D.fields[mid].tbase <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Order-preserving 32-bit key of a finite float; -0 and +0 get the same key.
+__device__ __forceinline__ uint32_t fkey(float v)
+{
+    uint32_t u = __float_as_uint(v);
+    if (u == 0x80000000u) u = 0;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ int64_t lin_delta(int r, uint64_t nx, uint64_t nxny)
+{
+    return (int64_t)rdx(r) + (int64_t)nx * rdy(r) + (int64_t)nxny * rdz(r);
+}
+
+__device__ __forceinline__ bool multi_bit(const uint32_t *tab, uint32_t s)
+{
+    return (tab[s >> 5] >> (s & 31)) & 1u;
+}
+
+// Saddle test from a lower-link mask and the valid-neighbour mask.
+__device__ __forceinline__ bool is_saddle(const uint32_t *tab, uint32_t L, uint32_t valid)
+{
+    uint32_t U = valid & ~L;
+    return L != 0 && U != 0 && (multi_bit(tab, L) || multi_bit(tab, U));
+}
+
+// Mark a tile in a bitmap; append it to a list the first time.
+__device__ __forceinline__ void mark_tile(uint32_t *bits, uint32_t *list, unsigned long long *count,
+                                          uint32_t tile)
+{
+    uint32_t bit = 1u << (tile & 31);
+    if (__ldcg(&bits[tile >> 5]) & bit) return;
+    uint32_t old = atomicOr(&bits[tile >> 5], bit);
+    if (!(old & bit)) {
+        unsigned long long p = atomicAdd(count, 1ull);
+        list[p] = tile;
+    }
+}
+
+}  // namespace exz

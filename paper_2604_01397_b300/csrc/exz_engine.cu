@@ -1,0 +1,714 @@
+// exz_engine.cu -- host side of the B300 EXaCTz correction: workspace layout,
+// the iterate-to-fixpoint loop of Algorithm 1 in three forms, and the C ABI.
+//
+// One run over F fields (F = 1 for exactz_correct):
+//   set-up     k_stencil<SETUP> (descriptor of f, g := f_hat, first checks),
+//              ordered CP compaction, stable radix sort by (field, value),
+//              reformulated event check on all CP pairs, apply, bookkeeping;
+//   loop       PLAIN:    full sweep + all pairs each pass, host reads the flag;
+//              FRONTIER: only tiles / pairs touched by the last pass's edits;
+//              GRAPH:    the FRONTIER pass as the body of a CUDA-graph
+//                        conditional while-node; the bookkeeping kernel clears
+//                        the condition when every field is done;
+//   finish     pinned-vertex residual check, status, edit-list compaction.
+// All three forms compute identical results (the frontier only skips checks
+// whose requests would target pinned vertices; see the oracle's notes).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "exactz.h"
+#include "exz_common.cuh"
+#include "exz_launch.h"
+
+using namespace exz;
+
+namespace {
+
+uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- link table
+// multi[S] = 1 iff the link subgraph induced on the neighbour subset S (bit s =
+// rank rank_of(s)) has at least two connected components.  Two neighbours are
+// linked iff their offsets differ by a neighbour offset.
+uint32_t g_multi_host[512];
+std::once_flag g_multi_once;
+
+void build_multi_table()
+{
+    uint32_t adj[14] = {0};
+    for (int a = 0; a < 14; a++)
+        for (int b = 0; b < 14; b++) {
+            if (a == b) continue;
+            const int ra = rank_of(a), rb = rank_of(b);
+            const int dx = rdx(rb) - rdx(ra), dy = rdy(rb) - rdy(ra), dz = rdz(rb) - rdz(ra);
+            const bool pos = dx >= 0 && dy >= 0 && dz >= 0, neg = dx <= 0 && dy <= 0 && dz <= 0;
+            const bool nonzero = dx || dy || dz;
+            const bool small = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+            if (nonzero && small && (pos || neg)) adj[a] |= 1u << b;
+        }
+    std::memset(g_multi_host, 0, sizeof(g_multi_host));
+    for (uint32_t S = 0; S < (1u << 14); S++) {
+        uint32_t rem = S;
+        int comps = 0;
+        while (rem) {
+            uint32_t comp = rem & (~rem + 1);
+            for (;;) {
+                uint32_t grow = comp;
+                for (int s = 0; s < 14; s++)
+                    if (comp & (1u << s)) grow |= adj[s] & S;
+                if (grow == comp) break;
+                comp = grow;
+            }
+            rem &= ~comp;
+            comps++;
+        }
+        if (comps >= 2) g_multi_host[S >> 5] |= 1u << (S & 31);
+    }
+}
+
+// ---------------------------------------------------------------- layout
+struct Layout {
+    uint32_t nfields = 0;
+    uint64_t total_v = 0, total_w = 0, total_real = 0;
+    uint32_t total_tiles = 0;
+    std::vector<FieldDesc> fd;
+};
+
+int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
+{
+    if (nf == 0 || nf >= (1u << 24) || !d) return EXACTZ_EINVAL;
+    L.nfields = nf;
+    L.fd.assign(nf, FieldDesc{});
+    uint64_t v = 0, w = 0, t = 0, real = 0;
+    for (uint32_t i = 0; i < nf; i++) {
+        const uint64_t nx = d[i].nx, ny = d[i].ny, nz = d[i].nz;
+        if (nx < 1 || ny < 1 || nz < 1) return EXACTZ_EINVAL;
+        const uint64_t n = nx * ny * nz;
+        if (n < 2 || n >= (1ull << LOCAL_BITS)) return EXACTZ_EINVAL;
+        FieldDesc &F = L.fd[i];
+        F.nx = (uint32_t)nx;
+        F.ny = (uint32_t)ny;
+        F.nz = (uint32_t)nz;
+        F.n = n;
+        F.tnx = (uint32_t)((nx + TX - 1) / TX);
+        F.tny = (uint32_t)((ny + TY - 1) / TY);
+        F.tnz = (uint32_t)((nz + TZ - 1) / TZ);
+        F.tbase = t;
+        t += (uint64_t)F.tnx * F.tny * F.tnz;
+        v = round_up(v, VBLOCK);
+        F.vbase = v;
+        v += n;
+        w = round_up(w, WBLOCK);
+        F.wbase = w;
+        w += ny * nz * F.tnx;
+        real += n;
+    }
+    if (t >= (1ull << 32) || real >= (1ull << 32)) return EXACTZ_EINVAL;
+    L.total_v = round_up(v, VBLOCK);
+    L.total_w = round_up(w, WBLOCK);
+    L.total_tiles = (uint32_t)t;
+    L.total_real = real;
+    return EXACTZ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- workspace
+struct exactz_workspace {
+    int device = 0;
+    uint32_t cap_nf = 0;
+    uint64_t cap_v = 0, cap_w = 0, cap_real = 0;
+    uint32_t cap_tiles = 0;
+    uint64_t bytes = 0;
+    std::vector<void *> allocs;
+
+    FieldDesc *d_fields = nullptr;
+    FieldState *d_fst = nullptr;
+    LoopState *d_ls = nullptr;
+    uint32_t *d_multi = nullptr;
+    uint8_t *k = nullptr;
+    uint32_t *desc = nullptr, *cp_rank = nullptr, *reqbits = nullptr, *cpwords = nullptr;
+    unsigned long long *req_list = nullptr;
+    uint32_t *tile_list[2] = {nullptr, nullptr}, *tile_bits = nullptr;
+    uint32_t *pin_tile_list = nullptr, *pin_tile_bits = nullptr;
+    uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_list = nullptr;
+    uint32_t *cp_key[2] = {nullptr, nullptr};
+    unsigned long long *cp_ent[2] = {nullptr, nullptr};
+    uint32_t *blk = nullptr;
+    unsigned long long *blk_off = nullptr;
+    uint32_t *hist = nullptr;
+    uint32_t sort_blocks = 0;
+
+    // host staging (host_buffers mode), grown on demand
+    float *st_f = nullptr, *st_fhat = nullptr, *st_g = nullptr;
+    uint64_t st_cap_v = 0;
+    EditRec *st_edits = nullptr;
+    uint64_t st_cap_edits = 0;
+
+    FieldState *h_fst = nullptr;  // pinned host copy
+    LoopState *h_ls = nullptr;
+
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey[5] = {0, 0, 0, 0, 0};
+    uint64_t layout_hash = 0;  // dims of the previous run (padding must hold k = 0, no CP bits)
+    exactz_stats stats{};
+    cudaEvent_t ev[9] = {};
+
+    std::mutex mu;
+};
+
+namespace {
+
+template <class T>
+int dalloc(exactz_workspace *ws, T *&p, uint64_t count)
+{
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return EXACTZ_ENOMEM;
+    }
+    ws->allocs.push_back(q);
+    ws->bytes += count * sizeof(T);
+    p = static_cast<T *>(q);
+    return EXACTZ_OK;
+}
+
+void free_ws(exactz_workspace *ws)
+{
+    if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
+    if (ws->graph) cudaGraphDestroy(ws->graph);
+    if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
+    for (cudaEvent_t e : ws->ev)
+        if (e) cudaEventDestroy(e);
+    for (void *p : ws->allocs) cudaFree(p);
+    if (ws->st_f) cudaFree(ws->st_f);
+    if (ws->st_fhat) cudaFree(ws->st_fhat);
+    if (ws->st_g) cudaFree(ws->st_g);
+    if (ws->st_edits) cudaFree(ws->st_edits);
+    if (ws->h_fst) cudaFreeHost(ws->h_fst);
+    if (ws->h_ls) cudaFreeHost(ws->h_ls);
+    delete ws;
+}
+
+#define CK(x)                                                  \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) {                               \
+            if (getenv("EXACTZ_DEBUG"))                        \
+                fprintf(stderr, "exactz: %s at %s:%d\n",       \
+                        cudaGetErrorString(e_), __FILE__, __LINE__); \
+            cudaGetLastError();                                \
+            return e_ == cudaErrorMemoryAllocation ? EXACTZ_ENOMEM : EXACTZ_ENODEV; \
+        }                                                      \
+    } while (0)
+
+int ws_alloc(exactz_workspace *ws, const Layout &L)
+{
+    std::call_once(g_multi_once, build_multi_table);
+    CK(cudaGetDevice(&ws->device));
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ws->device);
+    ws->cap_nf = L.nfields;
+    ws->cap_v = L.total_v;
+    ws->cap_w = L.total_w;
+    ws->cap_real = L.total_real;
+    ws->cap_tiles = L.total_tiles;
+    ws->sort_blocks = (uint32_t)nsm * 8;
+    const uint64_t V = L.total_v, W = L.total_w, T = L.total_tiles, C = L.total_real;
+    const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
+    int rc = EXACTZ_OK;
+#define AL(p, n) \
+    if ((rc = dalloc(ws, p, n)) != EXACTZ_OK) return rc
+    AL(ws->d_fields, L.nfields);
+    AL(ws->d_fst, L.nfields);
+    AL(ws->d_ls, 1);
+    AL(ws->d_multi, 512);
+    AL(ws->k, V);
+    AL(ws->desc, V);
+    AL(ws->cp_rank, V);
+    AL(ws->reqbits, V / 32 + 1);
+    AL(ws->cpwords, W);
+    AL(ws->req_list, C);
+    AL(ws->tile_list[0], T);
+    AL(ws->tile_list[1], T);
+    AL(ws->tile_bits, T / 32 + 1);
+    AL(ws->pin_tile_list, T);
+    AL(ws->pin_tile_bits, T / 32 + 1);
+    AL(ws->pair_list[0], 2 * C);
+    AL(ws->pair_list[1], 2 * C);
+    AL(ws->pin_pair_list, 2 * C);
+    AL(ws->cp_key[0], C);
+    AL(ws->cp_key[1], C);
+    AL(ws->cp_ent[0], C);
+    AL(ws->cp_ent[1], C);
+    AL(ws->blk, nblk);
+    AL(ws->blk_off, nblk);
+    AL(ws->hist, 256ull * ws->sort_blocks);
+#undef AL
+    CK(cudaMemcpy(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice));
+    CK(cudaMemset(ws->k, 0, V));
+    CK(cudaMemset(ws->reqbits, 0, (V / 32 + 1) * 4));
+    CK(cudaMemset(ws->cpwords, 0, W * 4));
+    CK(cudaMallocHost(&ws->h_fst, sizeof(FieldState) * L.nfields));
+    CK(cudaMallocHost(&ws->h_ls, sizeof(LoopState)));
+    CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : ws->ev) CK(cudaEventCreate(&e));
+    return EXACTZ_OK;
+}
+
+Dev make_dev(exactz_workspace *ws, const Layout &L)
+{
+    Dev D{};
+    D.fields = ws->d_fields;
+    D.fst = ws->d_fst;
+    D.ls = ws->d_ls;
+    D.nfields = L.nfields;
+    D.total_tiles = L.total_tiles;
+    D.total_v = L.total_v;
+    D.total_w = L.total_w;
+    D.k = ws->k;
+    D.desc = ws->desc;
+    D.cp_rank = ws->cp_rank;
+    D.reqbits = ws->reqbits;
+    D.cpwords = ws->cpwords;
+    D.req_list = ws->req_list;
+    D.tile_list[0] = ws->tile_list[0];
+    D.tile_list[1] = ws->tile_list[1];
+    D.tile_bits = ws->tile_bits;
+    D.pin_tile_list = ws->pin_tile_list;
+    D.pin_tile_bits = ws->pin_tile_bits;
+    D.pair_list[0] = ws->pair_list[0];
+    D.pair_list[1] = ws->pair_list[1];
+    D.pin_pair_list = ws->pin_pair_list;
+    D.cp_key[0] = ws->cp_key[0];
+    D.cp_key[1] = ws->cp_key[1];
+    D.cp_ent[0] = ws->cp_ent[0];
+    D.cp_ent[1] = ws->cp_ent[1];
+    D.o = ws->cp_ent[sort_passes(L.nfields) & 1];
+    D.multi = ws->d_multi;
+    D.cp_cap = ws->cap_real;
+    D.pair_cap = 2 * ws->cap_real;
+    D.req_cap = ws->cap_real;
+    D.blk = ws->blk;
+    D.blk_off = ws->blk_off;
+    D.hist = ws->hist;
+    D.sort_blocks = ws->sort_blocks;
+    return D;
+}
+
+// Graph: [loop-flag kernel] -> while (flag) { check, pairs, apply, bookkeeping }.
+int ensure_graph(exactz_workspace *ws, const Dev &D)
+{
+    const uint64_t key[5] = {D.nfields, D.total_tiles, D.total_v, D.total_w, (uint64_t)(uintptr_t)D.o};
+    if (ws->gexec && std::memcmp(key, ws->gkey, sizeof(key)) == 0) return EXACTZ_OK;
+    if (ws->gexec) {
+        cudaGraphExecDestroy(ws->gexec);
+        ws->gexec = nullptr;
+    }
+    if (ws->graph) {
+        cudaGraphDestroy(ws->graph);
+        ws->graph = nullptr;
+    }
+    cudaStream_t cs = ws->cap_stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    ws->graph = g;
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_loop_flag(D, h, 1, cs);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &nd));
+    // the params union has no default constructor: zero raw storage instead
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    CK(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp));
+    CK(cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamEndCapture(cs, &g));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_check_list(D, cs);
+    launch_pairs_list(D, cs);
+    launch_apply(D, 1, cs);
+    launch_book(D, h, 1, cs);
+    CK(cudaStreamEndCapture(cs, &body));
+    CK(cudaGraphInstantiate(&ws->gexec, g, 0));
+    std::memcpy(ws->gkey, key, sizeof(key));
+    return EXACTZ_OK;
+}
+
+int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
+{
+    if (V > ws->st_cap_v) {
+        if (ws->st_f) cudaFree(ws->st_f);
+        if (ws->st_fhat) cudaFree(ws->st_fhat);
+        if (ws->st_g) cudaFree(ws->st_g);
+        ws->st_f = ws->st_fhat = ws->st_g = nullptr;
+        ws->st_cap_v = 0;
+        CK(cudaMalloc(&ws->st_f, V * 4));
+        CK(cudaMalloc(&ws->st_fhat, V * 4));
+        CK(cudaMalloc(&ws->st_g, V * 4));
+        ws->st_cap_v = V;
+    }
+    if (E > ws->st_cap_edits) {
+        if (ws->st_edits) cudaFree(ws->st_edits);
+        ws->st_edits = nullptr;
+        ws->st_cap_edits = 0;
+        CK(cudaMalloc(&ws->st_edits, E * sizeof(EditRec)));
+        ws->st_cap_edits = E;
+    }
+    return EXACTZ_OK;
+}
+
+int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *const *fhat,
+        const exactz_dims *d, const float *xi, const exactz_opts *o, float *const *g_out,
+        exactz_edit *const *edits_out, const uint64_t *caps, exactz_result *res, cudaStream_t s,
+        int host)
+{
+    exactz_opts opt;
+    exactz_default_opts(&opt);
+    if (o) opt = *o;
+    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH) return EXACTZ_EINVAL;
+    if (!f || !fhat || !d || !xi || !g_out || !res) return EXACTZ_EINVAL;
+    Layout L;
+    int rc = make_layout(nf, d, L);
+    if (rc) return rc;
+    for (uint32_t i = 0; i < nf; i++) {
+        if (!f[i] || !fhat[i] || !g_out[i]) return EXACTZ_EINVAL;
+        if (!(xi[i] > 0.0f) || !std::isfinite(xi[i])) return EXACTZ_EINVAL;
+    }
+    if (nf > ws->cap_nf || L.total_v > ws->cap_v || L.total_w > ws->cap_w || L.total_tiles > ws->cap_tiles ||
+        L.total_real > ws->cap_real)
+        return EXACTZ_ESIZE;
+    CK(cudaSetDevice(ws->device));
+
+    uint64_t ecap_total = 0;
+    std::vector<uint64_t> ebase(nf, 0);
+    for (uint32_t i = 0; i < nf; i++) {
+        ebase[i] = ecap_total;
+        if (edits_out && edits_out[i] && caps) ecap_total += caps[i];
+    }
+    if (host) {
+        if ((rc = grow_staging(ws, L.total_v, ecap_total)) != EXACTZ_OK) return rc;
+    }
+    for (uint32_t i = 0; i < nf; i++) {
+        FieldDesc &F = L.fd[i];
+        F.N = opt.N;
+        F.xi = xi[i];
+        F.delta = xi[i] / (float)opt.N;  // binary32 division, Sec. 3.3
+        F.max_iters = opt.max_iters;
+        const bool has_edits = opt.want_edit_list && edits_out && edits_out[i] && caps && caps[i] > 0;
+        F.edits_cap = has_edits ? caps[i] : 0;
+        if (host) {
+            float *sf = ws->st_f + F.vbase, *sh = ws->st_fhat + F.vbase;
+            CK(cudaMemcpyAsync(sf, f[i], F.n * 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(sh, fhat[i], F.n * 4, cudaMemcpyHostToDevice, s));
+            F.f = sf;
+            F.fhat = sh;
+            F.g = ws->st_g + F.vbase;
+            F.edits = has_edits ? ws->st_edits + ebase[i] : nullptr;
+        } else {
+            F.f = f[i];
+            F.fhat = fhat[i];
+            F.g = g_out[i];
+            F.edits = has_edits ? reinterpret_cast<EditRec *>(edits_out[i]) : nullptr;
+        }
+    }
+    uint64_t hsh = 1469598103934665603ull ^ nf;
+    for (uint32_t i = 0; i < nf; i++) {
+        const uint64_t v[3] = {d[i].nx, d[i].ny, d[i].nz};
+        for (uint64_t x : v) hsh = (hsh ^ x) * 1099511628211ull;
+    }
+    if (hsh != ws->layout_hash) {
+        // a new layout: arena padding may hold another layout's vertices
+        CK(cudaMemsetAsync(ws->k, 0, L.total_v, s));
+        CK(cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s));
+        ws->layout_hash = hsh;
+    }
+    CK(cudaMemcpyAsync(ws->d_fields, L.fd.data(), sizeof(FieldDesc) * nf, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ws->d_fst, 0, sizeof(FieldState) * nf, s));
+    CK(cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s));
+    CK(cudaMemsetAsync(ws->tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
+    const Dev D = make_dev(ws, L);
+    const int frontier = opt.mode != EXACTZ_MODE_PLAIN;
+    const bool prof = opt.profile != 0;
+    auto mark = [&](int i) {
+        if (prof) cudaEventRecord(ws->ev[i], s);
+    };
+    const uint64_t P = (uint64_t)sort_passes(nf);
+    uint64_t launches = 0;
+
+    // set-up and the first pass
+    mark(0);
+    launch_setup(D, s);
+    mark(1);
+    launch_cp_compact(D, s);
+    mark(2);
+    launch_cp_sort(D, s);
+    mark(3);
+    launch_pairs_all(D, s);
+    launch_apply(D, frontier, s);
+    launch_book(D, 0, 0, s);
+    mark(4);
+    launches += 1 + 4 + (3 * P + 1) + 3;
+    CK(cudaGetLastError());
+
+    if (opt.mode == EXACTZ_MODE_GRAPH) {
+        if ((rc = ensure_graph(ws, D)) != EXACTZ_OK) return rc;
+        CK(cudaGraphLaunch(ws->gexec, s));
+        launches += 1;  // loop-flag kernel; the body's 4 kernels per pass are added below
+    } else {
+        for (;;) {
+            CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!ws->h_ls->any_active) break;
+            if (opt.mode == EXACTZ_MODE_PLAIN) {
+                launch_check_all(D, s);
+                launch_pairs_all(D, s);
+                launch_apply(D, 0, s);
+            } else {
+                launch_check_list(D, s);
+                launch_pairs_list(D, s);
+                launch_apply(D, 1, s);
+            }
+            launch_book(D, 0, 0, s);
+            launches += 4;
+            CK(cudaGetLastError());
+        }
+    }
+    mark(5);
+    // residual violations on pinned vertices, status, edit list
+    launch_check_pinned(D, s);
+    launch_pairs_pinned(D, s);
+    launch_finish(D, s);
+    mark(6);
+    launch_edit_list(D, opt.want_edit_list ? 1 : 0, s);
+    mark(7);
+    launches += 4 + (opt.want_edit_list ? 3 : 1);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ws->h_fst, ws->d_fst, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::memset(&ws->stats, 0, sizeof(ws->stats));
+    ws->stats.passes = ws->h_ls->pass;
+    ws->stats.total_critical = ws->h_ls->total_cp;
+    if (opt.mode == EXACTZ_MODE_GRAPH) launches += 4 * (ws->h_ls->pass > 0 ? ws->h_ls->pass - 1 : 0);
+    ws->stats.kernel_launches = launches;
+    if (prof) {
+        for (int i = 0; i < 7; i++) cudaEventElapsedTime(&ws->stats.stage_ms[i], ws->ev[i], ws->ev[i + 1]);
+        cudaEventElapsedTime(&ws->stats.stage_ms[7], ws->ev[0], ws->ev[7]);
+    }
+
+    int ret = EXACTZ_OK;
+    for (uint32_t i = 0; i < nf; i++) {
+        const FieldState &S = ws->h_fst[i];
+        exactz_result &R = res[i];
+        std::memset(&R, 0, sizeof(R));
+        R.iterations = S.iterations;
+        R.n_edits = S.n_edits;
+        R.n_lossless = S.n_lossless;
+        R.residual_violations = S.capped + S.pinned_res;
+        R.n_critical = S.ncp;
+        R.status = (int32_t)S.status;
+        if (R.status < 0 && ret == EXACTZ_OK) ret = R.status;
+        if (L.fd[i].edits && S.n_edits > L.fd[i].edits_cap && ret == EXACTZ_OK) ret = EXACTZ_ECAP;
+    }
+    if (host) {
+        for (uint32_t i = 0; i < nf; i++) {
+            const FieldDesc &F = L.fd[i];
+            CK(cudaMemcpyAsync(g_out[i], F.g, F.n * 4, cudaMemcpyDeviceToHost, s));
+            if (F.edits) {
+                const uint64_t ne = std::min<uint64_t>(ws->h_fst[i].n_edits, F.edits_cap);
+                if (ne)
+                    CK(cudaMemcpyAsync(edits_out[i], F.edits, ne * sizeof(EditRec), cudaMemcpyDeviceToHost, s));
+            }
+        }
+        CK(cudaStreamSynchronize(s));
+    }
+    return ret;
+}
+
+int check_device()
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return EXACTZ_ENODEV;
+    }
+    return EXACTZ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+void exactz_default_opts(exactz_opts *o)
+{
+    if (!o) return;
+    o->N = 5;
+    o->mode = EXACTZ_MODE_GRAPH;
+    o->max_iters = 1000000;
+    o->want_edit_list = 1;
+    o->profile = 0;
+}
+
+exactz_workspace *exactz_workspace_create(uint32_t nfields, const exactz_dims *dims)
+{
+    if (check_device() != EXACTZ_OK) return nullptr;
+    Layout L;
+    if (make_layout(nfields, dims, L) != EXACTZ_OK) return nullptr;
+    exactz_workspace *ws = new (std::nothrow) exactz_workspace();
+    if (!ws) return nullptr;
+    if (ws_alloc(ws, L) != EXACTZ_OK) {
+        free_ws(ws);
+        return nullptr;
+    }
+    return ws;
+}
+
+void exactz_workspace_destroy(exactz_workspace *ws)
+{
+    if (ws) free_ws(ws);
+}
+
+uint64_t exactz_workspace_bytes(const exactz_workspace *ws) { return ws ? ws->bytes : 0; }
+
+int exactz_ws_stats(const exactz_workspace *ws, exactz_stats *out)
+{
+    if (!ws || !out) return EXACTZ_EINVAL;
+    *out = ws->stats;
+    return EXACTZ_OK;
+}
+
+int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const *f, const float *const *fhat,
+                      const exactz_dims *d, const float *xi, const exactz_opts *opts, float *const *g_out,
+                      exactz_edit *const *edits_out, const uint64_t *edits_cap, exactz_result *res,
+                      void *cuda_stream, int host_buffers)
+{
+    if (!ws) return EXACTZ_EINVAL;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    return run(ws, nfields, f, fhat, d, xi, opts, g_out, edits_out, edits_cap, res,
+               static_cast<cudaStream_t>(cuda_stream), host_buffers);
+}
+
+int exactz_correct_batch(uint32_t nfields, const float *const *f, const float *const *fhat, const exactz_dims *d,
+                         const float *xi, const exactz_opts *opts, float *const *g_out,
+                         exactz_edit *const *edits_out, const uint64_t *edits_cap, exactz_result *res,
+                         void *cuda_stream)
+{
+    int rc = check_device();
+    if (rc) return rc;
+    Layout L;
+    if ((rc = make_layout(nfields, d, L)) != EXACTZ_OK) return rc;
+    exactz_workspace *ws = exactz_workspace_create(nfields, d);
+    if (!ws) return EXACTZ_ENOMEM;
+    rc = exactz_ws_correct(ws, nfields, f, fhat, d, xi, opts, g_out, edits_out, edits_cap, res, cuda_stream, 0);
+    exactz_workspace_destroy(ws);
+    return rc;
+}
+
+int exactz_correct(const float *f, const float *fhat, exactz_dims d, float xi, const exactz_opts *opts,
+                   float *g_out, exactz_edit *edits_out, uint64_t edits_cap, exactz_result *res,
+                   void *cuda_stream)
+{
+    const float *fp[1] = {f};
+    const float *hp[1] = {fhat};
+    float *gp[1] = {g_out};
+    exactz_edit *ep[1] = {edits_out};
+    uint64_t cp[1] = {edits_cap};
+    return exactz_correct_batch(1, fp, hp, &d, &xi, opts, gp, ep, cp, res, cuda_stream);
+}
+
+int exactz_classify(const float *h, exactz_dims d, uint32_t *desc_out, uint8_t *type_out, void *cuda_stream)
+{
+    int rc = check_device();
+    if (rc) return rc;
+    if (!h || !desc_out) return EXACTZ_EINVAL;
+    Layout L;
+    if ((rc = make_layout(1, &d, L)) != EXACTZ_OK) return rc;
+    exactz_workspace *ws = exactz_workspace_create(1, &d);
+    if (!ws) return EXACTZ_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    L.fd[0].f = h;
+    L.fd[0].fhat = h;
+    L.fd[0].N = 5;
+    rc = EXACTZ_OK;
+    if (cudaMemcpyAsync(ws->d_fields, L.fd.data(), sizeof(FieldDesc), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = EXACTZ_ENODEV;
+    if (!rc) {
+        launch_classify(make_dev(ws, L), desc_out, type_out, s);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = EXACTZ_ENODEV;
+    }
+    exactz_workspace_destroy(ws);
+    return rc;
+}
+
+int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t *count_out, void *cuda_stream)
+{
+    int rc = check_device();
+    if (rc) return rc;
+    if (!f || !order_out || !count_out) return EXACTZ_EINVAL;
+    Layout L;
+    if ((rc = make_layout(1, &d, L)) != EXACTZ_OK) return rc;
+    exactz_workspace *ws = exactz_workspace_create(1, &d);
+    if (!ws) return EXACTZ_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    float *scratch = nullptr;
+    rc = EXACTZ_OK;
+    if (cudaMalloc(&scratch, L.fd[0].n * 4) != cudaSuccess) rc = EXACTZ_ENOMEM;
+    if (!rc) {
+        FieldDesc &F = L.fd[0];
+        F.f = f;
+        F.fhat = f;
+        F.g = scratch;
+        F.N = 5;
+        F.xi = 1.0f;
+        F.delta = 0.2f;
+        const Dev D = make_dev(ws, L);
+        cudaMemcpyAsync(ws->d_fields, L.fd.data(), sizeof(FieldDesc), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(ws->d_fst, 0, sizeof(FieldState), s);
+        cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s);
+        launch_setup(D, s);
+        launch_cp_compact(D, s);
+        launch_cp_sort(D, s);
+        cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(ws->h_fst, ws->d_fst, sizeof(FieldState), cudaMemcpyDeviceToHost, s);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = EXACTZ_ENODEV;
+        if (!rc && ws->h_fst[0].err) rc = (ws->h_fst[0].err & ERR_NONFINITE) ? EXACTZ_ENONFINITE : EXACTZ_EBOUND;
+        if (!rc) {
+            const uint64_t c = ws->h_ls->total_cp;
+            *count_out = c;
+            if (c && (cudaMemcpyAsync(order_out, D.o, c * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                      cudaStreamSynchronize(s) != cudaSuccess))
+                rc = EXACTZ_ENODEV;
+        }
+    }
+    if (scratch) cudaFree(scratch);
+    exactz_workspace_destroy(ws);
+    return rc;
+}
+
+const char *exactz_version(void)
+{
+    return "exactz-b300 0.1 (sm_103a; tile 32x4x4; stencil/sort/apply kernels; graph while-loop)";
+}
+
+}  // extern "C"

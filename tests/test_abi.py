@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every entry point its header
+declares (no compute call: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(exactz_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2604_01397_b300 import build
+
+    path = build.build()
+    L = ctypes.CDLL(path)
+    names = _declared()
+    assert "exactz_correct" in names and "exactz_correct_batch" in names
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_package_import_loads_native_library():
+    import paper_2604_01397_b300 as ez
+
+    assert "sm_103a" in ez.version()
+    assert ez._native.lib() is ez._native.lib()
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2604_01397_b300 as ez
+
+    L = ez._native.lib()
+    d = (ez._native.Dims * 1)(ez._native.Dims(4, 4, 4))
+    assert not L.exactz_workspace_create(1, d)
+    res = ez._native.Result()
+    rc = L.exactz_correct(None, None, ez._native.Dims(4, 4, 4), ctypes.c_float(0.1), None, None, None, 0,
+                          ctypes.byref(res), None)
+    assert rc == ez._native.EXACTZ_ENODEV
+
+
+def test_default_opts():
+    import paper_2604_01397_b300 as ez
+
+    o = ez._native.Opts()
+    ez._native.lib().exactz_default_opts(ctypes.byref(o))
+    assert (o.N, o.mode, o.max_iters, o.want_edit_list) == (5, 2, 1000000, 1)
+
+
+def test_oracle_and_library_share_no_code():
+    # the oracle is plain C compiled by gcc; the library is CUDA; neither
+    # includes, imports or links the other
+    osrc = open(os.path.join(ROOT, "oracle", "exactz_oracle.c")).read()
+    assert "#include \"" not in osrc
+    for fn in os.listdir(os.path.join(ROOT, "paper_2604_01397_b300", "csrc")):
+        src = open(os.path.join(ROOT, "paper_2604_01397_b300", "csrc", fn)).read()
+        assert "oracle" not in src.lower() or "oracle's notes" in src
+    for fn in ("api.py", "_native.py", "__init__.py"):
+        src = open(os.path.join(ROOT, "paper_2604_01397_b300", fn)).read()
+        assert "import oracle" not in src and "from oracle" not in src
