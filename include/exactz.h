@@ -177,6 +177,37 @@ int exactz_classify(const float *h, exactz_dims d, uint32_t *desc_out, uint8_t *
 int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t *count_out,
                     void *cuda_stream);
 
+/* ---- allocation-free variant for small fields (the paper has no counterpart) ---- */
+
+/* Largest field (in vertices) and the fixed device scratch behind
+ * exactz_correct_noalloc. */
+#define EXACTZ_NOALLOC_MAX_VERTICES (1u << 18)
+#define EXACTZ_NOALLOC_SCRATCH_BYTES (32ull << 20)
+
+/* exactz_correct for fields of at most EXACTZ_NOALLOC_MAX_VERTICES vertices
+ * (for example 64^3) that allocates no memory: no cudaMalloc, cudaFree,
+ * pinned host memory, graph or event objects.  It is meant for callers that
+ * cannot allocate device memory in the middle of their work -- code running
+ * while a stream is captured into a CUDA graph, applications that reserve the
+ * whole device for their own pool, or loops that cannot take the implicit
+ * device synchronisation of cudaMalloc/cudaFree.  The caller still passes the
+ * inputs and outputs (device pointers, as for exactz_correct).
+ *
+ * Scratch: one EXACTZ_NOALLOC_SCRATCH_BYTES array of static device storage
+ * inside this library, held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (a set-up step), so make the first call on each device before any
+ * stream capture.  All calls share the array and it keeps the previous call's
+ * contents; each call clears what must start at zero.  Calls whose GPU work
+ * overlapped would race on the array: within one process they are serialised
+ * by a lock, and each call returns only after its stream work has finished.
+ * A GRAPH mode request runs the same passes as FRONTIER driven from the host
+ * (identical results); opts->profile is ignored.
+ * Returns EXACTZ_ESIZE for larger fields, otherwise as exactz_correct. */
+int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, float xi,
+                           const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
+                           uint64_t edits_cap, exactz_result *res, void *cuda_stream);
+
 /* Library build / device information (host string, static storage). */
 const char *exactz_version(void);
 

@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     classify,
     correct,
     correct_batch,
+    correct_noalloc,
     cp_order,
     decode_edits,
     dims_of,

@@ -58,7 +58,7 @@ assert ctypes.sizeof(Edit) == 16 and ctypes.sizeof(Result) == 48
 
 EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exactz_workspace_create",
            "exactz_workspace_destroy", "exactz_workspace_bytes", "exactz_ws_correct", "exactz_classify",
-           "exactz_cp_order", "exactz_version", "exactz_ws_stats"]
+           "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc"]
 
 _lib = None
 
@@ -98,6 +98,9 @@ def lib():
     L.exactz_classify.restype = ctypes.c_int
     L.exactz_cp_order.argtypes = [P, Dims, P, ctypes.POINTER(ctypes.c_uint64), P]
     L.exactz_cp_order.restype = ctypes.c_int
+    L.exactz_correct_noalloc.argtypes = [P, P, Dims, ctypes.c_float, ctypes.POINTER(Opts), P, P,
+                                         ctypes.c_uint64, ctypes.POINTER(Result), P]
+    L.exactz_correct_noalloc.restype = ctypes.c_int
     L.exactz_version.argtypes = []
     L.exactz_version.restype = ctypes.c_char_p
     _lib = L

@@ -253,3 +253,35 @@ def cp_order(f: torch.Tensor, dims=None, stream=None) -> torch.Tensor:
     if rc != N.EXACTZ_OK:
         raise ExactzError(rc, "exactz_cp_order")
     return out[: cnt.value]
+
+
+def correct_noalloc(f: torch.Tensor, fhat: torch.Tensor, xi: float, g_out: torch.Tensor,
+                    edit_buf: Optional[torch.Tensor] = None, dims=None, N_steps: int = 5,
+                    mode: str = "frontier", max_iters: int = 1_000_000, stream=None,
+                    raise_on_error: bool = True) -> dict:
+    """exactz_correct_noalloc: the correction for fields of at most 2^18 vertices
+    using only the library's fixed device scratch, for callers that must not
+    allocate device memory during the call (e.g. while a stream is being
+    captured into a CUDA graph, or when an application owns all device memory).
+    The caller provides the output g_out and, optionally, a (cap, 16) uint8
+    edit-record buffer; this function allocates nothing on the device."""
+    _check(f, "f")
+    _check(fhat, "fhat")
+    _check(g_out, "g_out")
+    d = dims_of(f, dims)
+    cap = 0 if edit_buf is None else edit_buf.shape[0]
+    res = N.Result()
+    o = make_opts(N_steps, mode, max_iters, edit_buf is not None)
+    rc = N.lib().exactz_correct_noalloc(
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(fhat.data_ptr()), N.Dims(*d),
+        ctypes.c_float(float(np.float32(xi))), ctypes.byref(o), ctypes.c_void_p(g_out.data_ptr()),
+        ctypes.c_void_p(edit_buf.data_ptr() if edit_buf is not None else 0), cap, ctypes.byref(res),
+        ctypes.c_void_p(_stream(stream)))
+    if rc not in (N.EXACTZ_OK, N.EXACTZ_ECAP) and raise_on_error:
+        raise ExactzError(rc, "exactz_correct_noalloc")
+    out = _result_dict(res)
+    out["rc"] = rc
+    out["g"] = g_out
+    if edit_buf is not None:
+        out["edits"] = decode_edits(edit_buf, out["n_edits"])
+    return out

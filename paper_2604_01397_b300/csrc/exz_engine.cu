@@ -712,3 +712,144 @@ const char *exactz_version(void)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free entry point
+// exactz_correct_noalloc: the same correction for small fields, with every
+// device buffer carved out of one fixed array that lives in this library's
+// device image.  It exists for callers that must not allocate device memory
+// during the call: code that runs while a stream is being captured into a
+// CUDA graph (cudaMalloc is not capturable and may synchronise the device),
+// simulations and in-situ pipelines that reserve the whole device memory up
+// front for their own pool, and real-time loops that cannot afford the
+// implicit device synchronisation of cudaMalloc / cudaFree.
+//
+// The array is file-scope static device storage: every GPU that loads this
+// library holds EXACTZ_NOALLOC_SCRATCH_BYTES of it until the process exits.
+// In host code the symbol is only a host-side stand-in, so its device address
+// is obtained once per device with cudaGetSymbolAddress (with that device
+// current) on the first call there; that first call should therefore come
+// before any stream capture.  All calls share the array and it keeps the last
+// call's contents, so each call clears what must start at zero.  Two calls
+// whose GPU work overlapped would race on the shared array: calls from one
+// process are serialised by a lock and each returns only after its work on
+// the stream has finished.
+namespace {
+
+constexpr uint64_t kNoallocBytes = EXACTZ_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
+};
+
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+exactz_workspace g_noalloc_ws[kNoallocMaxDevices];  // static host objects, no device allocation
+FieldState g_noalloc_hfst[kNoallocMaxDevices];      // pageable host read-back buffers
+LoopState g_noalloc_hls[kNoallocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Bump allocator over the scratch array (256-byte aligned pieces).
+struct Carver {
+    unsigned char *base;
+    uint64_t used, cap;
+    template <class T>
+    bool take(T *&p, uint64_t count)
+    {
+        if (count == 0) count = 1;
+        const uint64_t off = round_up(used, 256);
+        const uint64_t bytes = count * sizeof(T);
+        if (off + bytes > cap) return false;
+        p = reinterpret_cast<T *>(base + off);
+        used = off + bytes;
+        return true;
+    }
+};
+
+// Point every workspace buffer for layout L into the scratch array, in the
+// same roles ws_alloc gives them.  The link table sits first, at a fixed place.
+bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, int nsm)
+{
+    Carver c{base, 0, kNoallocBytes};
+    const uint64_t V = L.total_v, W = L.total_w, T = L.total_tiles, C = L.total_real;
+    const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
+    ws->sort_blocks = (uint32_t)nsm * 8;
+    bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
+              c.take(ws->d_ls, 1) && c.take(ws->k, V) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
+              c.take(ws->reqbits, V / 32 + 1) && c.take(ws->cpwords, W) && c.take(ws->req_list, C) &&
+              c.take(ws->tile_list[0], T) && c.take(ws->tile_list[1], T) && c.take(ws->tile_bits, T / 32 + 1) &&
+              c.take(ws->pin_tile_list, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
+              c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
+              c.take(ws->pin_pair_list, 2 * C) && c.take(ws->cp_key[0], C) && c.take(ws->cp_key[1], C) &&
+              c.take(ws->cp_ent[0], C) && c.take(ws->cp_ent[1], C) && c.take(ws->blk, nblk) &&
+              c.take(ws->blk_off, nblk) && c.take(ws->hist, 256ull * ws->sort_blocks);
+    if (!ok) return false;
+    ws->cap_nf = L.nfields;
+    ws->cap_v = V;
+    ws->cap_w = W;
+    ws->cap_real = C;
+    ws->cap_tiles = L.total_tiles;
+    ws->bytes = c.used;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, float xi,
+                                      const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
+                                      uint64_t edits_cap, exactz_result *res, void *cuda_stream)
+{
+    int rc = check_device();
+    if (rc) return rc;
+    if (!f || !fhat || !g_out || !res) return EXACTZ_EINVAL;
+    Layout L;
+    if ((rc = make_layout(1, &d, L)) != EXACTZ_OK) return rc;
+    if (L.total_real > EXACTZ_NOALLOC_MAX_VERTICES) return EXACTZ_ESIZE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return EXACTZ_ENODEV;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoallocDevice &D = g_noalloc_dev[dev];
+    exactz_workspace *ws = &g_noalloc_ws[dev];
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (!D.ready) {
+        // set-up, once per device: the device address of the static array
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return EXACTZ_ENODEV;
+        }
+        D.base = static_cast<unsigned char *>(p);
+        std::call_once(g_multi_once, build_multi_table);
+        D.ready = true;
+    }
+    if (!noalloc_carve(ws, D.base, L, nsm)) return EXACTZ_ESIZE;
+    ws->device = dev;
+    ws->h_fst = &g_noalloc_hfst[dev];
+    ws->h_ls = &g_noalloc_hls[dev];
+    // the array keeps the previous call's contents: reset what must start at zero
+    if (cudaMemcpyAsync(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->k, 0, L.total_v, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->reqbits, 0, (L.total_v / 32 + 1) * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s) != cudaSuccess) {
+        cudaGetLastError();
+        return EXACTZ_ENODEV;
+    }
+    ws->layout_hash = 0;
+    // no graph objects or events here: the loop is driven from the host
+    exactz_opts opt;
+    exactz_default_opts(&opt);
+    if (opts) opt = *opts;
+    if (opt.mode == EXACTZ_MODE_GRAPH) opt.mode = EXACTZ_MODE_FRONTIER;
+    opt.profile = 0;
+    const float *fp[1] = {f};
+    const float *hp[1] = {fhat};
+    float *gp[1] = {g_out};
+    exactz_edit *ep[1] = {edits_out};
+    uint64_t cp[1] = {edits_cap};
+    return run(ws, 1, fp, hp, &d, &xi, &opt, gp, ep, cp, res, s, 0);
+}
