@@ -13,11 +13,19 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
-@pytest.fixture(scope="session", autouse=True)
-def _oracle_built():
-    from oracle import build
+def _load_builder(path, name):
+    import importlib.util
 
-    build.build()
+    spec = importlib.util.spec_from_file_location(name, path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+# Build both shared libraries before any test imports them (nvcc cross-compiles
+# the sm_103a library without a GPU; gcc builds the oracle).
+_load_builder(os.path.join(ROOT, "paper_2604_01397_b300", "build.py"), "_exz_lib_build").build()
+_load_builder(os.path.join(ROOT, "oracle", "build.py"), "_exz_oracle_build").build()
 
 
 def read_golden(name):

@@ -20,9 +20,9 @@ def _declared():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_2604_01397_b300 import build
+    from conftest import _load_builder
 
-    path = build.build()
+    path = _load_builder(os.path.join(ROOT, "paper_2604_01397_b300", "build.py"), "_b").build()
     L = ctypes.CDLL(path)
     names = _declared()
     assert "exactz_correct" in names and "exactz_correct_batch" in names
