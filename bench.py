@@ -312,7 +312,8 @@ def run_ours(a):
             "traffic": ncu_traffic("k_stencil<SETUP>", c["name"]),
             "algorithmic_bytes": alg_bytes, "launch_ms": setup_avg, "tiles": n_tiles}
 
-    extras = {"iterations": r["iterations"], "status": r["status_name"], "n_edits": r["n_edits"],
+    extras = {"sum_requests": st["sum_requests"], "sum_tiles": st["sum_tiles"], "sum_pairs": st["sum_pairs"],
+              "iterations": r["iterations"], "status": r["status_name"], "n_edits": r["n_edits"],
               "n_lossless": r["n_lossless"], "n_critical": r["n_critical"], "passes": st["passes"],
               "stage_ms": stages, "mvertices_per_s": n / (ms / 1e3) / 1e6,
               "workspace_gib": ws.nbytes / 2 ** 30}

@@ -154,6 +154,9 @@ typedef struct {
     uint64_t kernel_launches; /* kernels the call executed (graph bodies counted per pass) */
     uint64_t passes;          /* edit passes run for the slowest field, including the last check */
     uint64_t total_critical;  /* critical points over all fields */
+    uint64_t sum_requests;    /* deduplicated edit requests over all passes */
+    uint64_t sum_tiles;       /* tiles re-checked by frontier passes (0 for PLAIN) */
+    uint64_t sum_pairs;       /* CP pairs re-checked by frontier passes (0 for PLAIN) */
     float stage_ms[8];
 } exactz_stats;
 

@@ -49,7 +49,9 @@ class Result(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("passes", ctypes.c_uint64),
-                ("total_critical", ctypes.c_uint64), ("stage_ms", ctypes.c_float * 8)]
+                ("total_critical", ctypes.c_uint64), ("sum_requests", ctypes.c_uint64),
+                ("sum_tiles", ctypes.c_uint64), ("sum_pairs", ctypes.c_uint64),
+                ("stage_ms", ctypes.c_float * 8)]
 
 
 STAGES = ["setup", "compact", "sort", "first_pass", "loop", "finish", "edit_list", "total"]

@@ -106,7 +106,8 @@ class Workspace:
         st = N.Stats()
         N.lib().exactz_ws_stats(self._h, ctypes.byref(st))
         return dict(kernel_launches=int(st.kernel_launches), passes=int(st.passes),
-                    total_critical=int(st.total_critical),
+                    total_critical=int(st.total_critical), sum_requests=int(st.sum_requests),
+                    sum_tiles=int(st.sum_tiles), sum_pairs=int(st.sum_pairs),
                     stage_ms={k: float(v) for k, v in zip(N.STAGES, st.stage_ms)})
 
     @property

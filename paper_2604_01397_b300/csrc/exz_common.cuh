@@ -60,6 +60,32 @@ constexpr uint32_t ERR_NONFINITE = 1, ERR_BOUND = 2;
 // Status codes (match the C ABI)
 constexpr int32_t ST_CONVERGED = 1, ST_STUCK = 2, ST_ITER_LIMIT = 3;
 
+// Division of 32-bit values by a run-time invariant divisor d with one
+// high multiply (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// t = hi32(n m), n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d) l++;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // ------------------------------------------------------------ field table
 struct FieldDesc {
     uint32_t nx, ny, nz, N;
@@ -75,6 +101,7 @@ struct FieldDesc {
     uint64_t max_iters;
     struct EditRec *edits;  // output edit list (device), may be null
     uint64_t edits_cap;
+    FastDiv div_nx, div_ny;  // x = t mod nx, row = t / nx, z = row / ny (fields below 2^32 vertices)
 };
 
 // One applied edit; same layout as exactz_edit (16 bytes).
@@ -104,6 +131,9 @@ struct LoopState {
     unsigned long long pin_tile_count;
     unsigned long long pin_pair_count;
     unsigned long long total_cp;
+    unsigned long long sum_requests;  // requests applied or skipped, over all passes
+    unsigned long long sum_tiles;     // tiles checked by frontier passes
+    unsigned long long sum_pairs;     // CP pairs checked by frontier passes
     uint32_t cur;
     uint32_t any_active;
     uint32_t pass;
@@ -124,6 +154,9 @@ struct Dev {
     uint32_t *cp_rank;
     uint32_t *reqbits;
     uint32_t *cpwords;
+    uint32_t *dirty;     // vertices whose closed star changed last pass (cp-bitmap layout)
+    float *gs;           // g of the critical points, in f's sorted order
+    uint32_t *pairbits;  // CP pairs already queued for the next pass
     unsigned long long *req_list;
     uint32_t *tile_list[2];
     uint32_t *tile_bits;

@@ -99,6 +99,8 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
         F.tny = (uint32_t)((ny + TY - 1) / TY);
         F.tnz = (uint32_t)((nz + TZ - 1) / TZ);
         F.tbase = t;
+        F.div_nx = make_fastdiv(F.nx);
+        F.div_ny = make_fastdiv(F.ny);
         t += (uint64_t)F.tnx * F.tny * F.tnz;
         v = round_up(v, VBLOCK);
         F.vbase = v;
@@ -133,6 +135,8 @@ struct exactz_workspace {
     uint32_t *d_multi = nullptr;
     uint8_t *k = nullptr;
     uint32_t *desc = nullptr, *cp_rank = nullptr, *reqbits = nullptr, *cpwords = nullptr;
+    uint32_t *dirty = nullptr, *pairbits = nullptr;
+    float *gs = nullptr;
     unsigned long long *req_list = nullptr;
     uint32_t *tile_list[2] = {nullptr, nullptr}, *tile_bits = nullptr;
     uint32_t *pin_tile_list = nullptr, *pin_tile_bits = nullptr;
@@ -236,6 +240,9 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->cp_rank, V);
     AL(ws->reqbits, V / 32 + 1);
     AL(ws->cpwords, W);
+    AL(ws->dirty, W);
+    AL(ws->gs, C);
+    AL(ws->pairbits, C / 32 + 1);
     AL(ws->req_list, C);
     AL(ws->tile_list[0], T);
     AL(ws->tile_list[1], T);
@@ -257,6 +264,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     CK(cudaMemset(ws->k, 0, V));
     CK(cudaMemset(ws->reqbits, 0, (V / 32 + 1) * 4));
     CK(cudaMemset(ws->cpwords, 0, W * 4));
+    CK(cudaMemset(ws->dirty, 0, W * 4));
     CK(cudaMallocHost(&ws->h_fst, sizeof(FieldState) * L.nfields));
     CK(cudaMallocHost(&ws->h_ls, sizeof(LoopState)));
     CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
@@ -279,6 +287,9 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.cp_rank = ws->cp_rank;
     D.reqbits = ws->reqbits;
     D.cpwords = ws->cpwords;
+    D.dirty = ws->dirty;
+    D.gs = ws->gs;
+    D.pairbits = ws->pairbits;
     D.req_list = ws->req_list;
     D.tile_list[0] = ws->tile_list[0];
     D.tile_list[1] = ws->tile_list[1];
@@ -439,6 +450,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         // a new layout: arena padding may hold another layout's vertices
         CK(cudaMemsetAsync(ws->k, 0, L.total_v, s));
         CK(cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s));
+        CK(cudaMemsetAsync(ws->dirty, 0, L.total_w * 4, s));
         ws->layout_hash = hsh;
     }
     CK(cudaMemcpyAsync(ws->d_fields, L.fd.data(), sizeof(FieldDesc) * nf, cudaMemcpyHostToDevice, s));
@@ -446,6 +458,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s));
     CK(cudaMemsetAsync(ws->tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->pairbits, 0, (L.total_real / 32 + 1) * 4, s));
     const Dev D = make_dev(ws, L);
     const int frontier = opt.mode != EXACTZ_MODE_PLAIN;
     const bool prof = opt.profile != 0;
@@ -467,7 +480,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     launch_apply(D, frontier, s);
     launch_book(D, 0, 0, s);
     mark(4);
-    launches += 1 + 4 + (3 * P + 1) + 3;
+    launches += 1 + 4 + 3 * P + 3;
     CK(cudaGetLastError());
 
     if (opt.mode == EXACTZ_MODE_GRAPH) {
@@ -509,6 +522,9 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     std::memset(&ws->stats, 0, sizeof(ws->stats));
     ws->stats.passes = ws->h_ls->pass;
     ws->stats.total_critical = ws->h_ls->total_cp;
+    ws->stats.sum_requests = ws->h_ls->sum_requests;
+    ws->stats.sum_tiles = ws->h_ls->sum_tiles;
+    ws->stats.sum_pairs = ws->h_ls->sum_pairs;
     if (opt.mode == EXACTZ_MODE_GRAPH) launches += 4 * (ws->h_ls->pass > 0 ? ws->h_ls->pass - 1 : 0);
     ws->stats.kernel_launches = launches;
     if (prof) {
@@ -778,7 +794,8 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
     ws->sort_blocks = (uint32_t)nsm * 8;
     bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
               c.take(ws->d_ls, 1) && c.take(ws->k, V) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
-              c.take(ws->reqbits, V / 32 + 1) && c.take(ws->cpwords, W) && c.take(ws->req_list, C) &&
+              c.take(ws->reqbits, V / 32 + 1) && c.take(ws->cpwords, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
+              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->req_list, C) &&
               c.take(ws->tile_list[0], T) && c.take(ws->tile_list[1], T) && c.take(ws->tile_bits, T / 32 + 1) &&
               c.take(ws->pin_tile_list, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
               c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
@@ -835,7 +852,8 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     if (cudaMemcpyAsync(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(ws->k, 0, L.total_v, s) != cudaSuccess ||
         cudaMemsetAsync(ws->reqbits, 0, (L.total_v / 32 + 1) * 4, s) != cudaSuccess ||
-        cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s) != cudaSuccess) {
+        cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->dirty, 0, L.total_w * 4, s) != cudaSuccess) {
         cudaGetLastError();
         return EXACTZ_ENODEV;
     }

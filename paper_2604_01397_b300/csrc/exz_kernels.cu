@@ -19,6 +19,8 @@
 //
 // Requests are deduplicated by an atomic bitmap over the arena; a vertex is
 // edited at most once per pass (synchronous semantics, Sec. 4.4 proof).
+// Requests to pinned vertices (already at the lossless bound) may enter the
+// list; k_apply leaves them unchanged and they do not keep the loop running.
 #include <cmath>
 #include <cstdio>
 
@@ -30,11 +32,16 @@ namespace exz {
 enum { SM_SETUP = 0, SM_CHECK_ALL = 1, SM_CHECK_LIST = 2, SM_PINNED = 3, SM_CLASSIFY = 4 };
 enum { EM_FIRST = 0, EM_NORMAL = 1, EM_PINNED = 2 };
 
-constexpr int QCAP = 1024;
+constexpr int QCAP = 2048;
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
 // ------------------------------------------------------------ emission
+// Requests leave a tile in two steps.  (1) While checking, a lane records each
+// target as its halo-cell index, deduplicated inside the tile by a shared bit
+// per halo cell.  (2) The block then claims the distinct targets in the
+// global request bitmap in one parallel round and queues the new ones; the
+// queue is flushed to the global request list when it is nearly full.
 struct EmitQ {
     unsigned long long e[QCAP];
     uint32_t n;
@@ -62,25 +69,49 @@ __device__ __forceinline__ void q_flush(EmitQ &q, const Dev &D)
     for (uint32_t j = threadIdx.x; j < n; j += CTA) D.req_list[q.base + j] = q.e[j];
     __syncthreads();
     if (threadIdx.x == 0) q.n = 0;
+    __syncthreads();
 }
 
-// Request a decrease of local vertex t of field fid (deduplicated).
-template <int EM>
-__device__ __forceinline__ void emit(const Dev &D, EmitQ &q, uint32_t fid, uint64_t vbase, uint32_t N,
-                                     uint64_t t)
+constexpr int TBW = (HALO_N + 31) / 32;  // words of the per-tile target bitmap
+
+struct TileTargets {
+    uint32_t bits[TBW];
+    uint16_t cell[HALO_N];
+    uint32_t n;
+};
+
+// Step (1): record the closed-star ranks in m of the vertex at halo cell c.
+__device__ __forceinline__ void tile_targets_add(TileTargets &T, int c, uint32_t m)
 {
-    uint64_t gid = vbase + t;
-    if (EM == EM_NORMAL) {
-        if (D.k[gid] > N) return;  // pinned at the lossless bound
-    } else if (EM == EM_PINNED) {
-        if (D.k[gid] <= N) return;
+    while (m) {
+        const int r = __ffs(m) - 1;
+        m &= m - 1;
+        const int h = c + soff(r);
+        const uint32_t bit = 1u << (h & 31);
+        if (!(atomicOr(&T.bits[h >> 5], bit) & bit)) T.cell[atomicAdd(&T.n, 1u)] = (uint16_t)h;
     }
-    uint32_t bit = 1u << (gid & 31);
-    uint32_t *w = &D.reqbits[gid >> 5];
-    if (__ldcg(w) & bit) return;
-    uint32_t old = atomicOr(w, bit);
-    if (old & bit) return;
-    q_push(q, D, ((unsigned long long)fid << LOCAL_BITS) | t);
+}
+
+// Step (2), after a barrier: claim the targets in the request bitmap, queue
+// the new ones, reset the tile state.  EM_PINNED keeps only pinned targets.
+template <int EM>
+__device__ __forceinline__ void tile_targets_flush(TileTargets &T, EmitQ &q, const Dev &D, uint32_t fid,
+                                                   uint64_t vbase, uint32_t N, int x0, int y0, int z0,
+                                                   uint32_t nx, uint32_t ny)
+{
+    const uint32_t n = T.n;
+    for (uint32_t j = threadIdx.x; j < n; j += CTA) {
+        const int h = T.cell[j];
+        const int hz = h / (HXP * HY), rem = h - hz * (HXP * HY), hy = rem / HXP, hx = rem - hy * HXP;
+        const uint64_t t = ((uint64_t)(z0 - 1 + hz) * ny + (uint64_t)(y0 - 1 + hy)) * nx + (uint64_t)(x0 - 1 + hx);
+        const uint64_t gid = vbase + t;
+        if (EM == EM_PINNED && D.k[gid] <= N) continue;
+        const uint32_t bit = 1u << (gid & 31);
+        if (!(atomicOr(&D.reqbits[gid >> 5], bit) & bit)) q_push(q, D, ((unsigned long long)fid << LOCAL_BITS) | t);
+    }
+    for (int w = threadIdx.x; w < TBW; w += CTA) T.bits[w] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) T.n = 0;
 }
 
 // ------------------------------------------------------------ stencil core
@@ -119,41 +150,61 @@ __device__ __forceinline__ Stn stencil15(const float *s, int c)
     return Stn{up, dn, mask, valid};
 }
 
-// Rules R1 (steepest neighbours) and R2 (saddle links) at one vertex.
-template <int EM>
-__device__ __forceinline__ void check_vertex(const Dev &D, EmitQ &q, const uint32_t *smulti,
-                                             const int64_t *sdl, uint32_t fid, uint64_t vbase,
-                                             uint32_t N, uint64_t i, uint32_t d, Stn g)
+// Rules R1 (steepest neighbours) and R2 (saddle links) at one vertex, as the
+// set of closed-star ranks whose vertices must be decreased:
+//   R1: up_g != up_f -> up_g;  down_g != down_f -> down_f;
+//   R2 (saddle in f or g): for each neighbour whose order against the vertex
+//       differs between f and g, whichever of the two is lower in f.
+__device__ __forceinline__ uint32_t request_mask(const uint32_t *smulti, uint32_t d, const Stn &g)
 {
     const uint32_t upf = d & 15u, dnf = (d >> 4) & 15u, mf = (d >> 8) & 0x3FFFu;
-    if (g.up != upf) emit<EM>(D, q, fid, vbase, N, (uint64_t)((int64_t)i + sdl[g.up]));
-    if (g.dn != dnf) emit<EM>(D, q, fid, vbase, N, (uint64_t)((int64_t)i + sdl[dnf]));
-    uint32_t diff = g.mask ^ mf;
+    uint32_t m = 0;
+    if (g.up != upf) m |= 1u << g.up;
+    if (g.dn != dnf) m |= 1u << dnf;
+    const uint32_t diff = g.mask ^ mf;
     if (diff && ((d & D_SADDLE) || is_saddle(smulti, g.mask, g.valid))) {
-        bool self = false;
-        while (diff) {
-            int s = __ffs(diff) - 1;
-            diff &= diff - 1;
-            if ((mf >> s) & 1u) emit<EM>(D, q, fid, vbase, N, (uint64_t)((int64_t)i + sdl[rank_of(s)]));
-            else self = true;
-        }
-        if (self) emit<EM>(D, q, fid, vbase, N, i);
+        const uint32_t nb = diff & mf;  // the neighbour is the lower one in f
+        m |= (nb & 0x7Fu) | ((nb & 0x3F80u) << 1);  // slot -> rank
+        if (diff & ~mf) m |= 1u << 7;   // the vertex itself is the lower one
     }
+    return m;
 }
 
+// Position of the n-th (0-based) set bit of m (m has more than n set bits).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
+{
+    int pos = 0, c = __popc(m & 0xFFFFu);
+    if (n >= c) { n -= c; pos += 16; m >>= 16; }
+    c = __popc(m & 0xFFu);
+    if (n >= c) { n -= c; pos += 8; m >>= 8; }
+    c = __popc(m & 0xFu);
+    if (n >= c) { n -= c; pos += 4; m >>= 4; }
+    c = __popc(m & 0x3u);
+    if (n >= c) { n -= c; pos += 2; m >>= 2; }
+    if (n >= (int)(m & 1u)) pos += 1;
+    return pos;
+}
+
+// One tile per block iteration: the tile's values plus a one-vertex halo are
+// staged in shared memory (NaN outside the domain), then every vertex (SETUP,
+// CHECK_ALL, PINNED, CLASSIFY) or every dirty vertex (CHECK_LIST) is checked.
 template <int MODE>
 __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out)
 {
     __shared__ float sa[HALO_N];
     __shared__ float sb[MODE == SM_SETUP ? HALO_N : 1];
     __shared__ uint32_t smulti[512];
-    __shared__ int64_t sdl[15];
     __shared__ EmitQ q;
+    __shared__ TileTargets tt;
     __shared__ uint32_t s_err;
+    __shared__ uint32_t s_rw[ROWS];       // dirty row words of the tile (CHECK_LIST)
+    __shared__ uint32_t s_pre[ROWS + 1];  // their prefix popcounts
 
     for (int j = threadIdx.x; j < 512; j += CTA) smulti[j] = D.multi[j];
+    for (int w = threadIdx.x; w < TBW; w += CTA) tt.bits[w] = 0;
     if (threadIdx.x == 0) {
         q.n = 0;
+        tt.n = 0;
         s_err = 0;
     }
     unsigned long long count;
@@ -175,40 +226,99 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
         const uint32_t tile = list ? list[it] : (uint32_t)it;
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
-        const uint64_t nx = F.nx, ny = F.ny, nz = F.nz, nxny = nx * ny;
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
         const uint64_t vbase = F.vbase;
         const uint32_t N = F.N;
-        const uint64_t lt = tile - F.tbase;
-        const uint32_t tx = (uint32_t)(lt % F.tnx);
-        const uint64_t rest = lt / F.tnx;
-        const uint32_t ty = (uint32_t)(rest % F.tny), tz = (uint32_t)(rest / F.tny);
-        const int64_t x0 = (int64_t)tx * TX, y0 = (int64_t)ty * TY, z0 = (int64_t)tz * TZ;
+        const uint32_t lt = (uint32_t)(tile - F.tbase);
+        const uint32_t tnx = F.tnx, tny = F.tny;
+        const uint32_t rest = lt / tnx;
+        const uint32_t tx = lt - rest * tnx;
+        const uint32_t tz = rest / tny, ty = rest - tz * tny;
+        const int x0 = (int)(tx * TX), y0 = (int)(ty * TY), z0 = (int)(tz * TZ);
         if (MODE == SM_CHECK_LIST && threadIdx.x == 0)
             atomicAnd(&D.tile_bits[tile >> 5], ~(1u << (tile & 31)));
-        if (threadIdx.x < 15) sdl[threadIdx.x] = lin_delta(threadIdx.x, nx, nxny);
+        if (MODE == SM_CHECK_LIST && threadIdx.x < ROWS) {
+            // take (and clear) the dirty bits of this tile's rows
+            const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
+            uint32_t w = 0;
+            if (y < ny && z < nz) {
+                uint32_t *p = D.dirty + F.wbase + ((uint64_t)z * ny + y) * tnx + tx;
+                w = *p;
+                if (w) *p = 0;
+            }
+            s_rw[threadIdx.x] = w;
+        }
 
+        // halo tile, one warp per row of HXP values (x0-1 .. x0+TX); NaN outside the domain
         const float *A = (MODE == SM_SETUP || MODE == SM_CLASSIFY) ? F.f : F.g;
-        for (int j = threadIdx.x; j < HALO_N; j += CTA) {
-            const int hx = j % HXP, r2 = j / HXP, hy = r2 % HY, hz = r2 / HY;
-            const int64_t X = x0 - 1 + hx, Y = y0 - 1 + hy, Z = z0 - 1 + hz;
-            const bool in = X >= 0 && Y >= 0 && Z >= 0 && X < (int64_t)nx && Y < (int64_t)ny &&
-                            Z < (int64_t)nz;
-            const uint64_t idx = (uint64_t)X + nx * ((uint64_t)Y + ny * (uint64_t)Z);
-            sa[j] = in ? A[idx] : __int_as_float(0x7fc00000);
-            if (MODE == SM_SETUP) sb[j] = in ? F.fhat[idx] : __int_as_float(0x7fc00000);
+        const float *B = F.fhat;
+        const float qnan = __int_as_float(0x7fc00000);
+        for (int row = warp; row < HY * HZ; row += WARPS) {
+            const int hz = row / HY, hy = row - hz * HY;
+            const int Y = y0 - 1 + hy, Z = z0 - 1 + hz;
+            const bool rin = Y >= 0 && Z >= 0 && Y < (int)ny && Z < (int)nz;
+            const uint64_t rb = rin ? ((uint64_t)Z * ny + (uint64_t)Y) * nx : 0;
+            const int X0 = x0 - 1 + lane, X1 = x0 + TX - 1 + lane;
+            const bool in0 = rin && X0 >= 0 && X0 < (int)nx;
+            const bool in1 = rin && lane < 2 && X1 < (int)nx;
+            float *sr = sa + row * HXP;
+            sr[lane] = in0 ? A[rb + X0] : qnan;
+            if (lane < 2) sr[TX + lane] = in1 ? A[rb + X1] : qnan;
+            if (MODE == SM_SETUP) {
+                float *tr = sb + row * HXP;
+                tr[lane] = in0 ? B[rb + X0] : qnan;
+                if (lane < 2) tr[TX + lane] = in1 ? B[rb + X1] : qnan;
+            }
+        }
+        if (MODE == SM_CHECK_LIST) {
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t c = lane < ROWS ? __popc(s_rw[lane]) : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+                    if (lane >= o) c += y;
+                }
+                if (lane < ROWS) s_pre[lane + 1] = c;
+                if (lane == 0) s_pre[0] = 0;
+            }
         }
         __syncthreads();
-        const bool interior = x0 >= 1 && x0 + TX < (int64_t)nx && y0 >= 1 && y0 + TY < (int64_t)ny &&
-                              z0 >= 1 && z0 + TZ < (int64_t)nz;
-
-        for (int rr = warp; rr < ROWS; rr += WARPS) {
-            const int ly = rr % TY, lz = rr / TY;
-            const uint64_t x = (uint64_t)(x0 + lane), y = (uint64_t)(y0 + ly), z = (uint64_t)(z0 + lz);
-            const bool in = x < nx && y < ny && z < nz;
-            const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lane + 1);
+        const bool interior = x0 >= 1 && x0 + TX < (int)nx && y0 >= 1 && y0 + TY < (int)ny && z0 >= 1 &&
+                              z0 + TZ < (int)nz;
+        // vertices of this tile to visit: all rows (one warp per row) or the dirty list
+        const int nvisit = MODE == SM_CHECK_LIST ? (int)s_pre[ROWS] : ROWS * TX;
+        for (int base = (MODE == SM_CHECK_LIST ? 0 : warp * TX); base < nvisit;
+             base += (MODE == SM_CHECK_LIST ? CTA : WARPS * TX)) {
+            int lx, ly, lz;
+            bool sel = true;
+            if (MODE == SM_CHECK_LIST) {
+                const int k = base + threadIdx.x;
+                sel = k < nvisit;
+                int row = 0;
+                if (sel) {
+#pragma unroll
+                    for (int step = 8; step >= 1; step >>= 1)
+                        if (row + step <= ROWS - 1 && (int)s_pre[row + step] <= k) row += step;
+                    lx = nth_set_bit(s_rw[row], k - (int)s_pre[row]);
+                } else {
+                    lx = 0;
+                }
+                ly = row % TY;
+                lz = row / TY;
+            } else {
+                const int rr = base / TX;
+                lx = lane;
+                ly = rr % TY;
+                lz = rr / TY;
+            }
+            const uint32_t x = (uint32_t)(x0 + lx), y = (uint32_t)(y0 + ly), z = (uint32_t)(z0 + lz);
+            const bool in = sel && x < nx && y < ny && z < nz;
+            const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lx + 1);
             bool cp = false;
+            uint32_t req = 0;
+            const uint64_t i = ((uint64_t)z * ny + y) * nx + x;
             if (in) {
-                const uint64_t i = x + nx * (y + ny * z);
                 if (MODE == SM_SETUP || MODE == SM_CLASSIFY) {
                     Stn sf = interior ? stencil15<true>(sa, c) : stencil15<false>(sa, c);
                     const uint32_t L = sf.mask, U = sf.valid & ~sf.mask;
@@ -232,26 +342,33 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
                         D.k[vbase + i] = 0;
                         F.g[i] = hv;
                         Stn sg = interior ? stencil15<true>(sb, c) : stencil15<false>(sb, c);
-                        check_vertex<EM>(D, q, smulti, sdl, fid, vbase, N, i, d, sg);
+                        req = request_mask(smulti, d, sg);
                     }
                 } else {
                     const uint32_t d = __ldg(&D.desc[vbase + i]);
                     Stn sg = interior ? stencil15<true>(sa, c) : stencil15<false>(sa, c);
-                    check_vertex<EM>(D, q, smulti, sdl, fid, vbase, N, i, d, sg);
+                    req = request_mask(smulti, d, sg);
                 }
             }
+            if (MODE != SM_CLASSIFY && req) tile_targets_add(tt, c, req);
             if (MODE == SM_SETUP) {
                 const uint32_t w = __ballot_sync(0xffffffffu, cp);
-                if (lane == 0 && y < ny && z < nz) D.cpwords[F.wbase + (z * ny + y) * F.tnx + tx] = w;
+                if (lane == 0 && y < ny && z < nz)
+                    D.cpwords[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = w;
             }
         }
-        if (MODE != SM_CLASSIFY) q_flush(q, D);
-        else __syncthreads();
+        __syncthreads();
+        if (MODE != SM_CLASSIFY) {
+            tile_targets_flush<EM>(tt, q, D, fid, vbase, N, x0, y0, z0, nx, ny);
+            __syncthreads();
+            if (q.n > QCAP - HALO_N) q_flush(q, D);  // uniform: q.n read after a barrier
+        }
         if (MODE == SM_SETUP && threadIdx.x == 0 && s_err) {
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
         }
     }
+    if (MODE != SM_CLASSIFY) q_flush(q, D);
 }
 
 // ------------------------------------------------------------ block scan helpers
@@ -318,36 +435,62 @@ __global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t *in, unsigned 
     if (threadIdx.x == 1023 && total) *total = sw[31];
 }
 
-// In-place exclusive scan of n uint32 values (sum < 2^32); one block of 1024.
+// In-place exclusive scan of n uint32 values (sum < 2^32); one block of 1024
+// threads walks the array in tiles of 4096 (each thread one uint4), so every
+// load and store is coalesced.
 __global__ void __launch_bounds__(1024) k_scan_inplace_u32(uint32_t *a, uint64_t n)
 {
     __shared__ uint32_t sw[32];
-    const uint64_t per = (n + 1023) / 1024;
-    const uint64_t b = threadIdx.x * per, e = min(n, b + per);
-    uint32_t s = 0;
-    for (uint64_t j = b; j < e; j++) s += a[j];
+    __shared__ uint32_t s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sw[warp] = x;
+    if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = sw[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+    for (uint64_t base = 0; base < n; base += 4096) {
+        const uint64_t j = base + 4ull * threadIdx.x;
+        uint32_t v[4];
+        if (j + 3 < n) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(a + j);
+            v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = (j + u < n) ? a[j + u] : 0u;
         }
-        sw[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = (warp ? sw[warp - 1] : 0) + x - s;
-    for (uint64_t j = b; j < e; j++) {
-        uint32_t v = a[j];
-        a[j] = run;
-        run += v;
+        const uint32_t tsum = v[0] + v[1] + v[2] + v[3];
+        uint32_t x = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sw[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = sw[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            sw[lane] = w;
+        }
+        __syncthreads();
+        uint32_t run = s_carry + (warp ? sw[warp - 1] : 0u) + x - tsum;
+        uint32_t out[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            out[u] = run;
+            run += v[u];
+        }
+        if (j + 3 < n) {
+            *reinterpret_cast<uint4 *>(a + j) = make_uint4(out[0], out[1], out[2], out[3]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (j + u < n) a[j + u] = out[u];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += sw[31];
+        __syncthreads();
     }
 }
 
@@ -451,14 +594,16 @@ __global__ void __launch_bounds__(CTA) k_sort_hist(Dev D, int pass, const uint32
     D.hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
+// last != 0: this is the final pass; also record each critical point's rank
+// within its field (cp_rank), which the frontier uses to find its CP pairs.
 __global__ void __launch_bounds__(CTA) k_sort_scatter(Dev D, int pass, const uint32_t *ksrc,
                                                       const unsigned long long *esrc, uint32_t *kdst,
-                                                      unsigned long long *edst)
+                                                      unsigned long long *edst, int last)
 {
     __shared__ uint32_t s_run[256];
     __shared__ uint32_t s_wc[WARPS][256];
     __shared__ uint32_t s_tot[256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     const unsigned long long count = D.ls->total_cp;
     const unsigned long long chunk = (count + gridDim.x - 1) / gridDim.x;
     const unsigned long long b = blockIdx.x * chunk, e = min(count, b + chunk);
@@ -497,22 +642,16 @@ __global__ void __launch_bounds__(CTA) k_sort_scatter(Dev D, int pass, const uin
             const uint32_t pos = s_run[d] + s_wc[warp][d] + rank;
             if (move_keys) kdst[pos] = key;
             edst[pos] = ent;
+            if (last) {
+                const uint32_t fid = (uint32_t)(ent >> LOCAL_BITS);
+                const FieldDesc &F = D.fields[fid];
+                D.cp_rank[F.vbase + (ent & LOCAL_MASK)] = (uint32_t)(pos - D.fst[fid].cp_base);
+                D.gs[pos] = F.g[ent & LOCAL_MASK];  // g == f_hat before the first edit
+            }
         }
         __syncthreads();
         s_run[threadIdx.x] += s_tot[threadIdx.x];
         __syncthreads();
-    }
-}
-
-__global__ void k_cp_rank(Dev D)
-{
-    const unsigned long long total = D.ls->total_cp;
-    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < total;
-         q += (unsigned long long)blockDim.x * gridDim.x) {
-        const unsigned long long e = D.o[q];
-        const uint32_t fid = (uint32_t)(e >> LOCAL_BITS);
-        const FieldDesc &F = D.fields[fid];
-        D.cp_rank[F.vbase + (e & LOCAL_MASK)] = (uint32_t)(q - D.fst[fid].cp_base);
     }
 }
 
@@ -530,6 +669,12 @@ __device__ __forceinline__ void warp_push(const Dev &D, bool has, unsigned long 
     if (has) D.req_list[base + __popc(m & lanemask_lt())] = e;
 }
 
+// Rule R3 on adjacent pairs (q, q+1) of the sorted critical points, reading
+// their current values from gs (kept in sorted order by k_apply); the sorted
+// entries are gathered only to resolve a tie by index or to name the target.
+// ALL: every pair (the first pass; pairs may straddle two fields).  LIST /
+// PINNED: pairs queued by k_apply, always inside one field; LIST also clears
+// each pair's queued bit.
 template <int PM>
 __global__ void __launch_bounds__(CTA) k_pairs(Dev D)
 {
@@ -550,114 +695,250 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D)
     for (unsigned long long base = (unsigned long long)blockIdx.x * CTA; base < count; base += stride) {
         const unsigned long long j = base + threadIdx.x;
         bool has = false;
-        unsigned long long e = 0;
+        unsigned long long a = 0;
         if (j < count) {
-            const unsigned long long q = list ? list[j] : j;
-            if (q + 1 < total) {
-                const unsigned long long a = D.o[q], b = D.o[q + 1];
-                if ((a >> LOCAL_BITS) == (b >> LOCAL_BITS)) {
-                    const uint32_t fid = (uint32_t)(a >> LOCAL_BITS);
-                    const FieldDesc &F = D.fields[fid];
-                    const uint64_t la = a & LOCAL_MASK, lb = b & LOCAL_MASK;
-                    const float ga = F.g[la], gb = F.g[lb];
-                    if (gb < ga || (gb == ga && lb < la)) {
-                        const uint64_t gid = F.vbase + la;
-                        const uint8_t kk = D.k[gid];
-                        const bool ok = PM == PM_PINNED ? (kk > F.N) : (kk <= F.N);
-                        if (ok) {
-                            const uint32_t bit = 1u << (gid & 31);
-                            uint32_t *w = &D.reqbits[gid >> 5];
-                            if (!(__ldcg(w) & bit) && !(atomicOr(w, bit) & bit)) {
-                                has = true;
-                                e = a;
-                            }
-                        }
-                    }
+            const unsigned long long q = list ? (unsigned long long)list[j] : j;
+            if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
+            const float ga = D.gs[q], gb = D.gs[q + 1];
+            bool viol = gb < ga;
+            if (PM == PM_ALL || gb == ga) {
+                a = D.o[q];
+                const unsigned long long b = D.o[q + 1];
+                if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
+                else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
+            } else if (viol) {
+                a = D.o[q];
+            }
+            if (viol) {
+                const FieldDesc &F = D.fields[a >> LOCAL_BITS];
+                const uint64_t gid = F.vbase + (a & LOCAL_MASK);
+                const uint8_t kk = D.k[gid];
+                if (PM == PM_PINNED ? (kk > F.N) : (kk <= F.N)) {
+                    const uint32_t bit = 1u << (gid & 31);
+                    uint32_t *w = &D.reqbits[gid >> 5];
+                    has = !(__ldcg(w) & bit) && !(atomicOr(w, bit) & bit);
                 }
             }
         }
-        warp_push(D, has, e);
+        warp_push(D, has, a);
     }
 }
 
 // ------------------------------------------------------------ apply (Sec. 3.3)
-__device__ __forceinline__ void mark_star_tiles(const Dev &D, const FieldDesc &F, uint64_t t, uint32_t *bits,
-                                                uint32_t *list, unsigned long long *count)
+// Field parameters the apply kernel needs, cached in registers per field id.
+struct ApplyField {
+    uint64_t vbase, n, tbase, wbase, max_iters, iterations, cp_base, ncp;
+    const float *f;
+    float *g;
+    float xi, delta;
+    uint32_t nx, ny, nz, tnx, tny, N, err;
+    FastDiv div_nx, div_ny;
+};
+
+__device__ __forceinline__ void load_apply_field(const Dev &D, uint32_t fid, ApplyField &A)
 {
-    const uint64_t nx = F.nx, ny = F.ny, nz = F.nz;
-    const int64_t x = (int64_t)(t % nx), y = (int64_t)((t / nx) % ny), z = (int64_t)(t / (nx * ny));
-    uint32_t seen[8];
-    int ns = 0;
-#pragma unroll 1
-    for (int r = 0; r < 15; r++) {
-        const int64_t X = x + rdx(r), Y = y + rdy(r), Z = z + rdz(r);
-        if (X < 0 || Y < 0 || Z < 0 || X >= (int64_t)nx || Y >= (int64_t)ny || Z >= (int64_t)nz) continue;
-        const uint32_t tile = (uint32_t)(F.tbase + (uint64_t)(X / TX) +
-                                         (uint64_t)F.tnx * ((uint64_t)(Y / TY) + (uint64_t)F.tny * (uint64_t)(Z / TZ)));
-        bool dup = false;
-        for (int s = 0; s < ns; s++) dup |= seen[s] == tile;
-        if (dup) continue;
-        if (ns < 8) seen[ns++] = tile;
-        mark_tile(bits, list, count, tile);
+    const FieldDesc &F = D.fields[fid];
+    A.vbase = F.vbase;
+    A.n = F.n;
+    A.tbase = F.tbase;
+    A.max_iters = F.max_iters;
+    A.f = F.f;
+    A.g = F.g;
+    A.xi = F.xi;
+    A.delta = F.delta;
+    A.nx = F.nx;
+    A.ny = F.ny;
+    A.nz = F.nz;
+    A.tnx = F.tnx;
+    A.tny = F.tny;
+    A.N = F.N;
+    A.div_nx = F.div_nx;
+    A.div_ny = F.div_ny;
+    A.wbase = F.wbase;
+    A.iterations = D.fst[fid].iterations;
+    A.err = D.fst[fid].err;
+    A.cp_base = D.fst[fid].cp_base;
+    A.ncp = D.fst[fid].ncp;
+}
+
+// Set the dirty bits of the closed star of (x, y, z): the seven grid rows it
+// touches, (dy, dz) in {(0,0), -(1,0), -(0,1), -(1,1), +(1,0), +(0,1), +(1,1)},
+// with x - 1 .. x + 1 in the centre row, x - 1 .. x below, x .. x + 1 above.
+__device__ __forceinline__ void mark_star_dirty(const ApplyField &A, uint32_t *dirty, uint32_t x, uint32_t y,
+                                                uint32_t z)
+{
+    const int rdy7[7] = {0, -1, 0, -1, 1, 0, 1};
+    const int rdz7[7] = {0, 0, -1, -1, 0, 1, 1};
+    const uint32_t w = x / 32, b = x % 32;
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        const int Y = (int)y + rdy7[k], Z = (int)z + rdz7[k];
+        if (Y < 0 || Z < 0 || Y >= (int)A.ny || Z >= (int)A.nz) continue;
+        const bool lo = k == 0 || k <= 3, hi = k == 0 || k >= 4;  // x-1 present / x+1 present
+        uint32_t *row = dirty + A.wbase + ((uint64_t)Z * A.ny + Y) * A.tnx;
+        uint32_t m = 1u << b;
+        if (hi && x + 1 < A.nx) {
+            if (b < 31) m |= 1u << (b + 1);
+            else atomicOr(&row[w + 1], 1u);
+        }
+        if (lo && x > 0) {
+            if (b > 0) m |= 1u << (b - 1);
+            else atomicOr(&row[w - 1], 0x80000000u);
+        }
+        atomicOr(&row[w], m);
     }
+}
+
+// Exclusive warp prefix of c; one atomicAdd per warp reserves the slots.
+// All 32 lanes must call it.
+__device__ __forceinline__ unsigned long long warp_reserve(uint32_t c, unsigned long long *counter)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (x - c);
+}
+
+// Mark the tiles holding the closed star of vertex (x, y, z).  The star's
+// negative offsets are the seven non-zero vectors of {0,-1}^3 and its positive
+// ones those of {0,1}^3, so the tiles it reaches beyond its own are, on each
+// side, the non-zero combinations of the tile faces the vertex lies on.
+__device__ __forceinline__ void mark_star_tiles(const ApplyField &A, uint32_t x, uint32_t y, uint32_t z,
+                                                uint32_t *bits, uint32_t *list, unsigned long long *count)
+{
+    const uint32_t own = (uint32_t)(A.tbase + x / TX + (uint64_t)A.tnx * (y / TY + (uint64_t)A.tny * (z / TZ)));
+    mark_tile(bits, list, count, own);
+    const uint32_t lo = ((x % TX) == 0 && x > 0 ? 1u : 0u) | ((y % TY) == 0 && y > 0 ? 2u : 0u) |
+                        ((z % TZ) == 0 && z > 0 ? 4u : 0u);
+    const uint32_t hi = ((x % TX) == TX - 1 && x + 1 < A.nx ? 1u : 0u) | ((y % TY) == TY - 1 && y + 1 < A.ny ? 2u : 0u) |
+                        ((z % TZ) == TZ - 1 && z + 1 < A.nz ? 4u : 0u);
+    const uint32_t sy = A.tnx, sz = A.tnx * A.tny;
+#pragma unroll 1
+    for (uint32_t m = lo; m; m = (m - 1) & lo)  // non-empty subsets of the low faces
+        mark_tile(bits, list, count, own - (m & 1u) - ((m >> 1) & 1u) * sy - ((m >> 2) & 1u) * sz);
+#pragma unroll 1
+    for (uint32_t m = hi; m; m = (m - 1) & hi)
+        mark_tile(bits, list, count, own + (m & 1u) + ((m >> 1) & 1u) * sy + ((m >> 2) & 1u) * sz);
 }
 
 __global__ void __launch_bounds__(CTA) k_apply(Dev D, int frontier)
 {
     const unsigned long long count = D.ls->req_count;
     const uint32_t nxt = D.ls->cur ^ 1u;
-    for (unsigned long long j = blockIdx.x * (unsigned long long)CTA + threadIdx.x; j < count;
-         j += (unsigned long long)gridDim.x * CTA) {
-        const unsigned long long e = D.req_list[j];
-        const uint32_t fid = (uint32_t)(e >> LOCAL_BITS);
-        const uint64_t t = e & LOCAL_MASK;
-        const FieldDesc &F = D.fields[fid];
-        FieldState *S = &D.fst[fid];
-        const uint64_t gid = F.vbase + t;
-        atomicAnd(&D.reqbits[gid >> 5], ~(1u << (gid & 31)));
-        if (S->err) continue;
-        if (S->iterations >= F.max_iters) {
-            atomicAdd(&S->capped, 1ull);
-            continue;
+    const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
+    uint32_t cached = 0xFFFFFFFFu, flagged = 0xFFFFFFFFu;
+    ApplyField A{};
+    // block-uniform loop: every lane of a warp takes part in the warp collectives below
+    for (unsigned long long base = (unsigned long long)blockIdx.x * CTA; base < count; base += stride) {
+        const unsigned long long j = base + threadIdx.x;
+        bool applied = false, cp = false, pinned = false;
+        uint32_t fid = 0xFFFFFFFFu;
+        unsigned long long q = 0, r = 0;
+        if (j < count) {
+            const unsigned long long e = D.req_list[j];
+            fid = (uint32_t)(e >> LOCAL_BITS);
+            const uint64_t t = e & LOCAL_MASK;
+            if (fid != cached) {
+                load_apply_field(D, fid, A);
+                cached = fid;
+            }
+            const uint64_t gid = A.vbase + t;
+            atomicAnd(&D.reqbits[gid >> 5], ~(1u << (gid & 31)));
+            if (!A.err) {
+                uint32_t kk = D.k[gid];
+                if (A.iterations >= A.max_iters) {
+                    // at the cap only requests to unpinned vertices are violations left to fix
+                    if (kk <= A.N) atomicAdd(&D.fst[fid].capped, 1ull);
+                } else {
+                    if (kk <= A.N) {  // pinned targets are requested but never change
+                        const float fl = __fsub_rn(A.f[t], A.xi);
+                        float gv;
+                        if (kk < A.N) {
+                            const float tt = __fsub_rn(A.g[t], A.delta);
+                            if (tt < fl) {
+                                gv = fl;
+                                kk = A.N + 1;
+                            } else {
+                                gv = tt;
+                                kk = kk + 1;
+                            }
+                        } else {
+                            gv = fl;
+                            kk = A.N + 1;
+                        }
+                        A.g[t] = gv;
+                        D.k[gid] = (uint8_t)kk;
+                        applied = true;
+                        pinned = kk == A.N + 1;
+                        if (frontier || pinned) {
+                            uint32_t x, y, z;
+                            if (A.n < (1ull << 32)) {
+                                const uint32_t t32 = (uint32_t)t, row = fdiv(t32, A.div_nx);
+                                x = t32 - row * A.nx;
+                                z = fdiv(row, A.div_ny);
+                                y = row - z * A.ny;
+                            } else {
+                                const uint64_t row = t / A.nx;
+                                x = (uint32_t)(t - row * A.nx);
+                                z = (uint32_t)(row / A.ny);
+                                y = (uint32_t)(row - (uint64_t)z * A.ny);
+                            }
+                            if (frontier) {
+                                mark_star_dirty(A, D.dirty, x, y, z);
+                                mark_star_tiles(A, x, y, z, D.tile_bits, D.tile_list[nxt], &D.ls->tile_count[nxt]);
+                            }
+                            if (pinned)
+                                mark_star_tiles(A, x, y, z, D.pin_tile_bits, D.pin_tile_list, &D.ls->pin_tile_count);
+                        }
+                        if (D.desc[gid] & D_CP) {
+                            r = D.cp_rank[gid];
+                            q = A.cp_base + r;
+                            D.gs[q] = gv;
+                            cp = frontier || pinned;
+                        }
+                    }
+                }
+            }
         }
-        const uint32_t N = F.N;
-        uint32_t kk = D.k[gid];
-        if (kk > N) continue;
-        const float fl = __fsub_rn(F.f[t], F.xi);
-        float gv;
-        if (kk < N) {
-            const float tt = __fsub_rn(F.g[t], F.delta);
-            if (tt < fl) {
-                gv = fl;
-                kk = N + 1;
-            } else {
-                gv = tt;
-                kk = kk + 1;
-            }
-        } else {
-            gv = fl;
-            kk = N + 1;
+        // "this field had an edit this pass": one store per warp and field
+        const uint32_t peers = __match_any_sync(0xffffffffu, applied ? fid : 0xFFFFFFFFu);
+        if (applied && (peers & lanemask_lt()) == 0 && flagged != fid) {
+            D.fst[fid].had_req = 1;
+            flagged = fid;
         }
-        F.g[t] = gv;
-        D.k[gid] = (uint8_t)kk;
-        S->had_req = 1;
-        const bool pinned = kk == N + 1;
-        if (frontier) mark_star_tiles(D, F, t, D.tile_bits, D.tile_list[nxt], &D.ls->tile_count[nxt]);
-        if (pinned) mark_star_tiles(D, F, t, D.pin_tile_bits, D.pin_tile_list, &D.ls->pin_tile_count);
-        if ((frontier || pinned) && (D.desc[gid] & D_CP)) {
-            const unsigned long long q = S->cp_base + D.cp_rank[gid];
-            const unsigned long long r = D.cp_rank[gid];
-            const int np = (r >= 1) ? 2 : 1;
-            if (frontier) {
-                const unsigned long long p = atomicAdd(&D.ls->pair_count[nxt], (unsigned long long)np);
-                D.pair_list[nxt][p] = (uint32_t)q;
-                if (np == 2) D.pair_list[nxt][p + 1] = (uint32_t)(q - 1);
+        // CP pairs (q-1, q) and (q, q+1) inside the field around an edited
+        // critical point: warp-aggregated appends; the frontier list is
+        // deduplicated through the pair bitmap
+        const bool has_lo = cp && r >= 1, has_hi = cp && r + 1 < A.ncp;
+        if (frontier && __any_sync(0xffffffffu, cp)) {
+            bool new_lo = false, new_hi = false;
+            if (has_hi) {
+                const uint32_t bit = 1u << (q & 31);
+                new_hi = !(__ldcg(&D.pairbits[q >> 5]) & bit) && !(atomicOr(&D.pairbits[q >> 5], bit) & bit);
             }
-            if (pinned) {
-                const unsigned long long p = atomicAdd(&D.ls->pin_pair_count, (unsigned long long)np);
-                D.pin_pair_list[p] = (uint32_t)q;
-                if (np == 2) D.pin_pair_list[p + 1] = (uint32_t)(q - 1);
+            if (has_lo) {
+                const unsigned long long p0 = q - 1;
+                const uint32_t bit = 1u << (p0 & 31);
+                new_lo = !(__ldcg(&D.pairbits[p0 >> 5]) & bit) && !(atomicOr(&D.pairbits[p0 >> 5], bit) & bit);
             }
+            const uint32_t np = (uint32_t)new_hi + (uint32_t)new_lo;
+            const unsigned long long p = warp_reserve(np, &D.ls->pair_count[nxt]);
+            if (new_hi) D.pair_list[nxt][p] = (uint32_t)q;
+            if (new_lo) D.pair_list[nxt][p + (new_hi ? 1 : 0)] = (uint32_t)(q - 1);
+        }
+        const uint32_t npp = pinned && cp ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
+        if (__any_sync(0xffffffffu, npp != 0)) {
+            const unsigned long long p = warp_reserve(npp, &D.ls->pin_pair_count);
+            if (pinned && has_hi) D.pin_pair_list[p] = (uint32_t)q;
+            if (pinned && has_lo) D.pin_pair_list[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
         }
     }
 }
@@ -687,6 +968,9 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
     if (threadIdx.x == 0) {
         LoopState *L = D.ls;
         const uint32_t c = L->cur;
+        L->sum_requests += L->req_count;
+        L->sum_tiles += L->tile_count[c];
+        L->sum_pairs += L->pair_count[c];
         L->tile_count[c] = 0;
         L->pair_count[c] = 0;
         L->cur = c ^ 1u;
@@ -890,15 +1174,15 @@ void launch_cp_sort(const Dev &D, cudaStream_t s)
         const int dst = src ^ 1;
         k_sort_hist<<<B, CTA, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src]);
         k_scan_inplace_u32<<<1, 1024, 0, s>>>(D.hist, (uint64_t)256 * B);
-        k_sort_scatter<<<B, CTA, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src], D.cp_key[dst], D.cp_ent[dst]);
+        k_sort_scatter<<<B, CTA, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src], D.cp_key[dst], D.cp_ent[dst],
+                                         p == P - 1);
         src = dst;
     }
-    k_cp_rank<<<sms() * 8, 256, 0, s>>>(D);
 }
 
 void launch_pairs_all(const Dev &D, cudaStream_t s) { k_pairs<PM_ALL><<<sms() * 8, CTA, 0, s>>>(D); }
-void launch_pairs_list(const Dev &D, cudaStream_t s) { k_pairs<PM_LIST><<<sms() * 4, CTA, 0, s>>>(D); }
-void launch_pairs_pinned(const Dev &D, cudaStream_t s) { k_pairs<PM_PINNED><<<sms() * 2, CTA, 0, s>>>(D); }
+void launch_pairs_list(const Dev &D, cudaStream_t s) { k_pairs<PM_LIST><<<sms() * 8, CTA, 0, s>>>(D); }
+void launch_pairs_pinned(const Dev &D, cudaStream_t s) { k_pairs<PM_PINNED><<<sms() * 4, CTA, 0, s>>>(D); }
 
 void launch_apply(const Dev &D, int frontier, cudaStream_t s)
 {
