@@ -50,10 +50,14 @@ __host__ __device__ constexpr int rank_of(int s) { return s < 7 ? s : s + 1; }
 // smem offset of rank r inside a halo tile
 __host__ __device__ constexpr int soff(int r) { return rdx(r) + HXP * rdy(r) + HXP * HY * rdz(r); }
 
-// Descriptor bits (per vertex of f)
+// Descriptor bits (per vertex): steepest up / down rank and lower-link mask of
+// f, saddle / critical flags of f, and in the top byte the vertex's edit count
+// k (0..N, N+1 = pinned at the lossless bound).
 constexpr uint32_t D_UP_SHIFT = 0, D_DN_SHIFT = 4, D_MASK_SHIFT = 8;
 constexpr uint32_t D_SADDLE = 1u << 22;
 constexpr uint32_t D_CP = 1u << 23;
+constexpr uint32_t D_K_SHIFT = 24;
+constexpr uint32_t D_F_MASK = 0x00FFFFFFu;
 
 // Field errors (FieldState::err bits)
 constexpr uint32_t ERR_NONFINITE = 1, ERR_BOUND = 2;
@@ -125,7 +129,7 @@ struct FieldState {
 };
 
 struct LoopState {
-    unsigned long long req_count;
+    unsigned long long apply_count;  // tiles holding requested vertices (this pass)
     unsigned long long tile_count[2];
     unsigned long long pair_count[2];
     unsigned long long pin_tile_count;
@@ -148,16 +152,16 @@ struct Dev {
     uint32_t nfields;
     uint32_t total_tiles;
     uint64_t total_v;   // arena vertices (padded)
-    uint64_t total_w;   // cp-bitmap words (padded)
-    uint8_t *k;
+    uint64_t total_w;   // row words (padded): one bit per vertex, one word per tile row
     uint32_t *desc;
     uint32_t *cp_rank;
-    uint32_t *reqbits;
-    uint32_t *cpwords;
-    uint32_t *dirty;     // vertices whose closed star changed last pass (cp-bitmap layout)
+    uint32_t *cpwords;   // critical points of f (row words)
+    uint32_t *reqw;      // vertices requested this pass (row words)
+    uint32_t *dirty;     // vertices whose closed star changed last pass (row words)
     float *gs;           // g of the critical points, in f's sorted order
     uint32_t *pairbits;  // CP pairs already queued for the next pass
-    unsigned long long *req_list;
+    uint32_t *apply_list;
+    uint32_t *apply_bits;
     uint32_t *tile_list[2];
     uint32_t *tile_bits;
     uint32_t *pin_tile_list;
@@ -170,7 +174,6 @@ struct Dev {
     const uint32_t *multi;  // 2^14-bit table: link subset has >= 2 components
     uint64_t cp_cap;
     uint64_t pair_cap;
-    uint64_t req_cap;
     // scratch for scans, histograms and block counts
     uint32_t *blk;
     unsigned long long *blk_off;

@@ -133,11 +133,9 @@ struct exactz_workspace {
     FieldState *d_fst = nullptr;
     LoopState *d_ls = nullptr;
     uint32_t *d_multi = nullptr;
-    uint8_t *k = nullptr;
-    uint32_t *desc = nullptr, *cp_rank = nullptr, *reqbits = nullptr, *cpwords = nullptr;
-    uint32_t *dirty = nullptr, *pairbits = nullptr;
+    uint32_t *desc = nullptr, *cp_rank = nullptr, *cpwords = nullptr, *reqw = nullptr;
+    uint32_t *dirty = nullptr, *pairbits = nullptr, *apply_list = nullptr, *apply_bits = nullptr;
     float *gs = nullptr;
-    unsigned long long *req_list = nullptr;
     uint32_t *tile_list[2] = {nullptr, nullptr}, *tile_bits = nullptr;
     uint32_t *pin_tile_list = nullptr, *pin_tile_bits = nullptr;
     uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_list = nullptr;
@@ -235,15 +233,15 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->d_fst, L.nfields);
     AL(ws->d_ls, 1);
     AL(ws->d_multi, 512);
-    AL(ws->k, V);
     AL(ws->desc, V);
     AL(ws->cp_rank, V);
-    AL(ws->reqbits, V / 32 + 1);
     AL(ws->cpwords, W);
+    AL(ws->reqw, W);
     AL(ws->dirty, W);
     AL(ws->gs, C);
     AL(ws->pairbits, C / 32 + 1);
-    AL(ws->req_list, C);
+    AL(ws->apply_list, T);
+    AL(ws->apply_bits, T / 32 + 1);
     AL(ws->tile_list[0], T);
     AL(ws->tile_list[1], T);
     AL(ws->tile_bits, T / 32 + 1);
@@ -261,9 +259,9 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->hist, 256ull * ws->sort_blocks);
 #undef AL
     CK(cudaMemcpy(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice));
-    CK(cudaMemset(ws->k, 0, V));
-    CK(cudaMemset(ws->reqbits, 0, (V / 32 + 1) * 4));
+    CK(cudaMemset(ws->desc, 0, V * 4));
     CK(cudaMemset(ws->cpwords, 0, W * 4));
+    CK(cudaMemset(ws->reqw, 0, W * 4));
     CK(cudaMemset(ws->dirty, 0, W * 4));
     CK(cudaMallocHost(&ws->h_fst, sizeof(FieldState) * L.nfields));
     CK(cudaMallocHost(&ws->h_ls, sizeof(LoopState)));
@@ -282,15 +280,15 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.total_tiles = L.total_tiles;
     D.total_v = L.total_v;
     D.total_w = L.total_w;
-    D.k = ws->k;
     D.desc = ws->desc;
     D.cp_rank = ws->cp_rank;
-    D.reqbits = ws->reqbits;
     D.cpwords = ws->cpwords;
+    D.reqw = ws->reqw;
     D.dirty = ws->dirty;
     D.gs = ws->gs;
     D.pairbits = ws->pairbits;
-    D.req_list = ws->req_list;
+    D.apply_list = ws->apply_list;
+    D.apply_bits = ws->apply_bits;
     D.tile_list[0] = ws->tile_list[0];
     D.tile_list[1] = ws->tile_list[1];
     D.tile_bits = ws->tile_bits;
@@ -307,7 +305,6 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.multi = ws->d_multi;
     D.cp_cap = ws->cap_real;
     D.pair_cap = 2 * ws->cap_real;
-    D.req_cap = ws->cap_real;
     D.blk = ws->blk;
     D.blk_off = ws->blk_off;
     D.hist = ws->hist;
@@ -447,9 +444,10 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         for (uint64_t x : v) hsh = (hsh ^ x) * 1099511628211ull;
     }
     if (hsh != ws->layout_hash) {
-        // a new layout: arena padding may hold another layout's vertices
-        CK(cudaMemsetAsync(ws->k, 0, L.total_v, s));
+        // a new layout: padding may hold another layout's vertices (edit counts, row bits)
+        CK(cudaMemsetAsync(ws->desc, 0, L.total_v * 4, s));
         CK(cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s));
+        CK(cudaMemsetAsync(ws->reqw, 0, L.total_w * 4, s));
         CK(cudaMemsetAsync(ws->dirty, 0, L.total_w * 4, s));
         ws->layout_hash = hsh;
     }
@@ -459,6 +457,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemsetAsync(ws->tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->pairbits, 0, (L.total_real / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->apply_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
     const Dev D = make_dev(ws, L);
     const int frontier = opt.mode != EXACTZ_MODE_PLAIN;
     const bool prof = opt.profile != 0;
@@ -793,9 +792,10 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
     const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
     ws->sort_blocks = (uint32_t)nsm * 8;
     bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
-              c.take(ws->d_ls, 1) && c.take(ws->k, V) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
-              c.take(ws->reqbits, V / 32 + 1) && c.take(ws->cpwords, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
-              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->req_list, C) &&
+              c.take(ws->d_ls, 1) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
+              c.take(ws->cpwords, W) && c.take(ws->reqw, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
+              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_list, T) &&
+              c.take(ws->apply_bits, T / 32 + 1) &&
               c.take(ws->tile_list[0], T) && c.take(ws->tile_list[1], T) && c.take(ws->tile_bits, T / 32 + 1) &&
               c.take(ws->pin_tile_list, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
               c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
@@ -850,8 +850,8 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     ws->h_ls = &g_noalloc_hls[dev];
     // the array keeps the previous call's contents: reset what must start at zero
     if (cudaMemcpyAsync(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(ws->k, 0, L.total_v, s) != cudaSuccess ||
-        cudaMemsetAsync(ws->reqbits, 0, (L.total_v / 32 + 1) * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->desc, 0, L.total_v * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->reqw, 0, L.total_w * 4, s) != cudaSuccess ||
         cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s) != cudaSuccess ||
         cudaMemsetAsync(ws->dirty, 0, L.total_w * 4, s) != cudaSuccess) {
         cudaGetLastError();

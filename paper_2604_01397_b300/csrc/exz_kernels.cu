@@ -30,88 +30,111 @@
 namespace exz {
 
 enum { SM_SETUP = 0, SM_CHECK_ALL = 1, SM_CHECK_LIST = 2, SM_PINNED = 3, SM_CLASSIFY = 4 };
-enum { EM_FIRST = 0, EM_NORMAL = 1, EM_PINNED = 2 };
-
-constexpr int QCAP = 2048;
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
-// ------------------------------------------------------------ emission
-// Requests leave a tile in two steps.  (1) While checking, a lane records each
-// target as its halo-cell index, deduplicated inside the tile by a shared bit
-// per halo cell.  (2) The block then claims the distinct targets in the
-// global request bitmap in one parallel round and queues the new ones; the
-// queue is flushed to the global request list when it is nearly full.
-struct EmitQ {
-    unsigned long long e[QCAP];
-    uint32_t n;
-    unsigned long long base;
-};
-
-__device__ __forceinline__ void q_push(EmitQ &q, const Dev &D, unsigned long long e)
-{
-    uint32_t p = atomicAdd(&q.n, 1u);
-    if (p < QCAP) {
-        q.e[p] = e;
-    } else {
-        unsigned long long gp = atomicAdd(&D.ls->req_count, 1ull);
-        D.req_list[gp] = e;
-    }
-}
-
-// All threads of the block must call this.
-__device__ __forceinline__ void q_flush(EmitQ &q, const Dev &D)
-{
-    __syncthreads();
-    uint32_t n = min(q.n, (uint32_t)QCAP);
-    if (threadIdx.x == 0 && n) q.base = atomicAdd(&D.ls->req_count, (unsigned long long)n);
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < n; j += CTA) D.req_list[q.base + j] = q.e[j];
-    __syncthreads();
-    if (threadIdx.x == 0) q.n = 0;
-    __syncthreads();
-}
-
-constexpr int TBW = (HALO_N + 31) / 32;  // words of the per-tile target bitmap
-
+// ------------------------------------------------------------ requests
+// A request is a bit in the row-word bitmap reqw (one 32-bit word per tile row,
+// bit = x mod 32); setting it twice is harmless, which deduplicates requests.
+// Every tile holding a requested vertex is queued once in the apply list.
+//
+// Inside the check kernel a tile first collects its targets as bits of its
+// halo rows in shared memory (34 cells per row: x0-1 .. x0+32), then commits
+// each halo row with at most three word ORs and queues the tiles they fall in.
 struct TileTargets {
-    uint32_t bits[TBW];
-    uint16_t cell[HALO_N];
-    uint32_t n;
+    unsigned long long row[HY * HZ];
+    uint32_t nb;  // 27-bit set of neighbouring tiles (ox, oy, oz in -1..1) holding targets
 };
 
-// Step (1): record the closed-star ranks in m of the vertex at halo cell c.
-__device__ __forceinline__ void tile_targets_add(TileTargets &T, int c, uint32_t m)
+// Record the closed-star ranks in m of the tile vertex (lx, ly, lz).
+__device__ __forceinline__ void tile_targets_add(TileTargets &T, int lx, int ly, int lz, uint32_t m)
 {
     while (m) {
         const int r = __ffs(m) - 1;
         m &= m - 1;
-        const int h = c + soff(r);
-        const uint32_t bit = 1u << (h & 31);
-        if (!(atomicOr(&T.bits[h >> 5], bit) & bit)) T.cell[atomicAdd(&T.n, 1u)] = (uint16_t)h;
+        const int row = (lz + 1 + rdz(r)) * HY + (ly + 1 + rdy(r));
+        atomicOr(&T.row[row], 1ull << (lx + 1 + rdx(r)));
     }
 }
 
-// Step (2), after a barrier: claim the targets in the request bitmap, queue
-// the new ones, reset the tile state.  EM_PINNED keeps only pinned targets.
-template <int EM>
-__device__ __forceinline__ void tile_targets_flush(TileTargets &T, EmitQ &q, const Dev &D, uint32_t fid,
-                                                   uint64_t vbase, uint32_t N, int x0, int y0, int z0,
-                                                   uint32_t nx, uint32_t ny)
+__device__ __forceinline__ int nb_index(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
+
+// Queue the tiles of a 27-bit neighbourhood mask around `tile`; thread j of
+// the block handles neighbour j, so the marks go out in parallel.
+__device__ __forceinline__ void mark_nb_tiles(uint32_t nb, uint32_t tile, uint32_t tnx, uint32_t tny, uint32_t *bits,
+                                              uint32_t *list, unsigned long long *count)
 {
-    const uint32_t n = T.n;
-    for (uint32_t j = threadIdx.x; j < n; j += CTA) {
-        const int h = T.cell[j];
-        const int hz = h / (HXP * HY), rem = h - hz * (HXP * HY), hy = rem / HXP, hx = rem - hy * HXP;
-        const uint64_t t = ((uint64_t)(z0 - 1 + hz) * ny + (uint64_t)(y0 - 1 + hy)) * nx + (uint64_t)(x0 - 1 + hx);
-        const uint64_t gid = vbase + t;
-        if (EM == EM_PINNED && D.k[gid] <= N) continue;
-        const uint32_t bit = 1u << (gid & 31);
-        if (!(atomicOr(&D.reqbits[gid >> 5], bit) & bit)) q_push(q, D, ((unsigned long long)fid << LOCAL_BITS) | t);
+    const int j = threadIdx.x;
+    if (j < 27 && ((nb >> j) & 1u)) {
+        const int ox = j % 3 - 1, oy = (j / 3) % 3 - 1, oz = j / 9 - 1;
+        mark_tile(bits, list, count, (uint32_t)((int64_t)tile + ox + (int64_t)tnx * (oy + (int64_t)tny * oz)));
     }
-    for (int w = threadIdx.x; w < TBW; w += CTA) T.bits[w] = 0;
+}
+
+// Commit the tile's targets (after a barrier); resets T.  PINNED keeps only
+// targets already at the lossless bound (the residual count).
+template <bool PINNED>
+__device__ __forceinline__ void tile_targets_commit(TileTargets &T, const Dev &D, const FieldDesc &F, uint32_t tile,
+                                                    uint32_t tx, int y0, int z0, uint32_t tnx, uint32_t tny)
+{
+    for (int row = threadIdx.x; row < HY * HZ; row += CTA) {
+        unsigned long long m = T.row[row];
+        if (!m) continue;
+        T.row[row] = 0;
+        const int hz = row / HY, hy = row - hz * HY;
+        const uint32_t Y = (uint32_t)(y0 - 1 + hy), Z = (uint32_t)(z0 - 1 + hz);
+        const uint64_t rw = F.wbase + ((uint64_t)Z * F.ny + Y) * tnx;  // word of tile column 0 in this row
+        if (PINNED) {  // drop targets that are not pinned
+            unsigned long long keep = 0, mm = m;
+            const uint64_t rb = ((uint64_t)Z * F.ny + Y) * F.nx;
+            while (mm) {
+                const int hx = __ffsll(mm) - 1;
+                mm &= mm - 1;
+                const uint64_t t = rb + (uint64_t)((int)(tx * TX) - 1 + hx);
+                if ((D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) keep |= 1ull << hx;
+            }
+            m = keep;
+            if (!m) continue;
+        }
+        const int oy = hy == 0 ? -1 : (hy == TY + 1 ? 1 : 0), oz = hz == 0 ? -1 : (hz == TZ + 1 ? 1 : 0);
+        uint32_t nb = 0;
+        if (m & 1ull) {
+            atomicOr(&D.reqw[rw + tx - 1], 0x80000000u);
+            nb |= 1u << nb_index(-1, oy, oz);
+        }
+        const uint32_t mid = (uint32_t)(m >> 1);
+        if (mid) {
+            atomicOr(&D.reqw[rw + tx], mid);
+            nb |= 1u << nb_index(0, oy, oz);
+        }
+        if ((m >> 33) & 1ull) {
+            atomicOr(&D.reqw[rw + tx + 1], 1u);
+            nb |= 1u << nb_index(1, oy, oz);
+        }
+        atomicOr(&T.nb, nb);
+    }
     __syncthreads();
-    if (threadIdx.x == 0) T.n = 0;
+    const uint32_t nb = T.nb;
+    mark_nb_tiles(nb, tile, tnx, tny, D.apply_bits, D.apply_list, &D.ls->apply_count);
+    __syncthreads();
+    if (threadIdx.x == 0) T.nb = 0;
+}
+
+// Request vertex t of field F from outside a tile (the CP-pair check).
+__device__ __forceinline__ void request_vertex(const Dev &D, const FieldDesc &F, uint64_t t)
+{
+    uint32_t x, row;
+    if (F.n < (1ull << 32)) {
+        row = fdiv((uint32_t)t, F.div_nx);
+        x = (uint32_t)t - row * F.nx;
+    } else {
+        row = (uint32_t)(t / F.nx);
+        x = (uint32_t)(t - (uint64_t)row * F.nx);
+    }
+    const uint32_t z = fdiv(row, F.div_ny), y = row - z * F.ny;
+    atomicOr(&D.reqw[F.wbase + (uint64_t)row * F.tnx + (x >> 5)], 1u << (x & 31));
+    const uint32_t tile = (uint32_t)(F.tbase + (x >> 5) + (uint64_t)F.tnx * (y / TY + (uint64_t)F.tny * (z / TZ)));
+    mark_tile(D.apply_bits, D.apply_list, &D.ls->apply_count, tile);
 }
 
 // ------------------------------------------------------------ stencil core
@@ -194,17 +217,15 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
     __shared__ float sa[HALO_N];
     __shared__ float sb[MODE == SM_SETUP ? HALO_N : 1];
     __shared__ uint32_t smulti[512];
-    __shared__ EmitQ q;
     __shared__ TileTargets tt;
     __shared__ uint32_t s_err;
     __shared__ uint32_t s_rw[ROWS];       // dirty row words of the tile (CHECK_LIST)
     __shared__ uint32_t s_pre[ROWS + 1];  // their prefix popcounts
 
     for (int j = threadIdx.x; j < 512; j += CTA) smulti[j] = D.multi[j];
-    for (int w = threadIdx.x; w < TBW; w += CTA) tt.bits[w] = 0;
+    for (int w = threadIdx.x; w < HY * HZ; w += CTA) tt.row[w] = 0;
     if (threadIdx.x == 0) {
-        q.n = 0;
-        tt.n = 0;
+        tt.nb = 0;
         s_err = 0;
     }
     unsigned long long count;
@@ -220,7 +241,6 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
         list = D.pin_tile_list;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int EM = MODE == SM_SETUP ? EM_FIRST : (MODE == SM_PINNED ? EM_PINNED : EM_NORMAL);
 
     for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
         const uint32_t tile = list ? list[it] : (uint32_t)it;
@@ -228,7 +248,6 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
         const FieldDesc &F = D.fields[fid];
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
         const uint64_t vbase = F.vbase;
-        const uint32_t N = F.N;
         const uint32_t lt = (uint32_t)(tile - F.tbase);
         const uint32_t tnx = F.tnx, tny = F.tny;
         const uint32_t rest = lt / tnx;
@@ -338,8 +357,7 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
                         if (!isfinite(fv) || !isfinite(hv)) e = ERR_NONFINITE;
                         else if (hv < __fsub_rn(fv, F.xi) || hv > __fadd_rn(fv, F.xi)) e = ERR_BOUND;
                         if (e) atomicOr(&s_err, e);
-                        D.desc[vbase + i] = d;
-                        D.k[vbase + i] = 0;
+                        D.desc[vbase + i] = d;  // edit count k = 0 in the top byte
                         F.g[i] = hv;
                         Stn sg = interior ? stencil15<true>(sb, c) : stencil15<false>(sb, c);
                         req = request_mask(smulti, d, sg);
@@ -350,7 +368,7 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
                     req = request_mask(smulti, d, sg);
                 }
             }
-            if (MODE != SM_CLASSIFY && req) tile_targets_add(tt, c, req);
+            if (MODE != SM_CLASSIFY && req) tile_targets_add(tt, lx, ly, lz, req);
             if (MODE == SM_SETUP) {
                 const uint32_t w = __ballot_sync(0xffffffffu, cp);
                 if (lane == 0 && y < ny && z < nz)
@@ -358,17 +376,12 @@ __global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint
             }
         }
         __syncthreads();
-        if (MODE != SM_CLASSIFY) {
-            tile_targets_flush<EM>(tt, q, D, fid, vbase, N, x0, y0, z0, nx, ny);
-            __syncthreads();
-            if (q.n > QCAP - HALO_N) q_flush(q, D);  // uniform: q.n read after a barrier
-        }
+        if (MODE != SM_CLASSIFY) tile_targets_commit<MODE == SM_PINNED>(tt, D, F, tile, tx, y0, z0, tnx, tny);
         if (MODE == SM_SETUP && threadIdx.x == 0 && s_err) {
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
         }
     }
-    if (MODE != SM_CLASSIFY) q_flush(q, D);
 }
 
 // ------------------------------------------------------------ block scan helpers
@@ -658,23 +671,12 @@ __global__ void __launch_bounds__(CTA) k_sort_scatter(Dev D, int pass, const uin
 // ------------------------------------------------------------ pair check (Sec. 4.3)
 enum { PM_ALL = 0, PM_LIST = 1, PM_PINNED = 2 };
 
-__device__ __forceinline__ void warp_push(const Dev &D, bool has, unsigned long long e)
-{
-    const uint32_t m = __ballot_sync(0xffffffffu, has);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(&D.ls->req_count, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (has) D.req_list[base + __popc(m & lanemask_lt())] = e;
-}
-
 // Rule R3 on adjacent pairs (q, q+1) of the sorted critical points, reading
-// their current values from gs (kept in sorted order by k_apply); the sorted
-// entries are gathered only to resolve a tie by index or to name the target.
-// ALL: every pair (the first pass; pairs may straddle two fields).  LIST /
-// PINNED: pairs queued by k_apply, always inside one field; LIST also clears
-// each pair's queued bit.
+// their current values from gs (kept in sorted order by the apply kernel); the
+// sorted entries are gathered only to resolve a tie by index or to name the
+// target.  ALL: every pair (the first pass; pairs may straddle two fields).
+// LIST / PINNED: pairs queued by the apply kernel, always inside one field;
+// LIST also clears each pair's queued bit.  PINNED keeps pinned targets only.
 template <int PM>
 __global__ void __launch_bounds__(CTA) k_pairs(Dev D)
 {
@@ -692,103 +694,29 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D)
         list = D.pin_pair_list;
     }
     const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * CTA; base < count; base += stride) {
-        const unsigned long long j = base + threadIdx.x;
-        bool has = false;
+    for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
+        const unsigned long long q = list ? (unsigned long long)list[j] : j;
+        if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
+        const float ga = D.gs[q], gb = D.gs[q + 1];
+        bool viol = gb < ga;
         unsigned long long a = 0;
-        if (j < count) {
-            const unsigned long long q = list ? (unsigned long long)list[j] : j;
-            if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
-            const float ga = D.gs[q], gb = D.gs[q + 1];
-            bool viol = gb < ga;
-            if (PM == PM_ALL || gb == ga) {
-                a = D.o[q];
-                const unsigned long long b = D.o[q + 1];
-                if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
-                else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
-            } else if (viol) {
-                a = D.o[q];
-            }
-            if (viol) {
-                const FieldDesc &F = D.fields[a >> LOCAL_BITS];
-                const uint64_t gid = F.vbase + (a & LOCAL_MASK);
-                const uint8_t kk = D.k[gid];
-                if (PM == PM_PINNED ? (kk > F.N) : (kk <= F.N)) {
-                    const uint32_t bit = 1u << (gid & 31);
-                    uint32_t *w = &D.reqbits[gid >> 5];
-                    has = !(__ldcg(w) & bit) && !(atomicOr(w, bit) & bit);
-                }
-            }
+        if (PM == PM_ALL || gb == ga) {
+            a = D.o[q];
+            const unsigned long long b = D.o[q + 1];
+            if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
+            else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
+        } else if (viol) {
+            a = D.o[q];
         }
-        warp_push(D, has, a);
+        if (viol) {
+            const FieldDesc &F = D.fields[a >> LOCAL_BITS];
+            const uint64_t t = a & LOCAL_MASK;
+            if (PM != PM_PINNED || (D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) request_vertex(D, F, t);
+        }
     }
 }
 
 // ------------------------------------------------------------ apply (Sec. 3.3)
-// Field parameters the apply kernel needs, cached in registers per field id.
-struct ApplyField {
-    uint64_t vbase, n, tbase, wbase, max_iters, iterations, cp_base, ncp;
-    const float *f;
-    float *g;
-    float xi, delta;
-    uint32_t nx, ny, nz, tnx, tny, N, err;
-    FastDiv div_nx, div_ny;
-};
-
-__device__ __forceinline__ void load_apply_field(const Dev &D, uint32_t fid, ApplyField &A)
-{
-    const FieldDesc &F = D.fields[fid];
-    A.vbase = F.vbase;
-    A.n = F.n;
-    A.tbase = F.tbase;
-    A.max_iters = F.max_iters;
-    A.f = F.f;
-    A.g = F.g;
-    A.xi = F.xi;
-    A.delta = F.delta;
-    A.nx = F.nx;
-    A.ny = F.ny;
-    A.nz = F.nz;
-    A.tnx = F.tnx;
-    A.tny = F.tny;
-    A.N = F.N;
-    A.div_nx = F.div_nx;
-    A.div_ny = F.div_ny;
-    A.wbase = F.wbase;
-    A.iterations = D.fst[fid].iterations;
-    A.err = D.fst[fid].err;
-    A.cp_base = D.fst[fid].cp_base;
-    A.ncp = D.fst[fid].ncp;
-}
-
-// Set the dirty bits of the closed star of (x, y, z): the seven grid rows it
-// touches, (dy, dz) in {(0,0), -(1,0), -(0,1), -(1,1), +(1,0), +(0,1), +(1,1)},
-// with x - 1 .. x + 1 in the centre row, x - 1 .. x below, x .. x + 1 above.
-__device__ __forceinline__ void mark_star_dirty(const ApplyField &A, uint32_t *dirty, uint32_t x, uint32_t y,
-                                                uint32_t z)
-{
-    const int rdy7[7] = {0, -1, 0, -1, 1, 0, 1};
-    const int rdz7[7] = {0, 0, -1, -1, 0, 1, 1};
-    const uint32_t w = x / 32, b = x % 32;
-#pragma unroll
-    for (int k = 0; k < 7; k++) {
-        const int Y = (int)y + rdy7[k], Z = (int)z + rdz7[k];
-        if (Y < 0 || Z < 0 || Y >= (int)A.ny || Z >= (int)A.nz) continue;
-        const bool lo = k == 0 || k <= 3, hi = k == 0 || k >= 4;  // x-1 present / x+1 present
-        uint32_t *row = dirty + A.wbase + ((uint64_t)Z * A.ny + Y) * A.tnx;
-        uint32_t m = 1u << b;
-        if (hi && x + 1 < A.nx) {
-            if (b < 31) m |= 1u << (b + 1);
-            else atomicOr(&row[w + 1], 1u);
-        }
-        if (lo && x > 0) {
-            if (b > 0) m |= 1u << (b - 1);
-            else atomicOr(&row[w - 1], 0x80000000u);
-        }
-        atomicOr(&row[w], m);
-    }
-}
-
 // Exclusive warp prefix of c; one atomicAdd per warp reserves the slots.
 // All 32 lanes must call it.
 __device__ __forceinline__ unsigned long long warp_reserve(uint32_t c, unsigned long long *counter)
@@ -807,140 +735,220 @@ __device__ __forceinline__ unsigned long long warp_reserve(uint32_t c, unsigned 
     return base + (x - c);
 }
 
-// Mark the tiles holding the closed star of vertex (x, y, z).  The star's
-// negative offsets are the seven non-zero vectors of {0,-1}^3 and its positive
-// ones those of {0,1}^3, so the tiles it reaches beyond its own are, on each
+// Queue the tiles holding the closed star of vertex (x, y, z) of tile `own`:
+// the star's negative offsets are the non-zero vectors of {0,-1}^3 and its
+// positive ones those of {0,1}^3, so the other tiles it reaches are, on each
 // side, the non-zero combinations of the tile faces the vertex lies on.
-__device__ __forceinline__ void mark_star_tiles(const ApplyField &A, uint32_t x, uint32_t y, uint32_t z,
-                                                uint32_t *bits, uint32_t *list, unsigned long long *count)
+__device__ __forceinline__ void mark_star_tiles(uint32_t own, uint32_t x, uint32_t y, uint32_t z, uint32_t nx,
+                                                uint32_t ny, uint32_t nz, uint32_t tnx, uint32_t tny, uint32_t *bits,
+                                                uint32_t *list, unsigned long long *count)
 {
-    const uint32_t own = (uint32_t)(A.tbase + x / TX + (uint64_t)A.tnx * (y / TY + (uint64_t)A.tny * (z / TZ)));
     mark_tile(bits, list, count, own);
     const uint32_t lo = ((x % TX) == 0 && x > 0 ? 1u : 0u) | ((y % TY) == 0 && y > 0 ? 2u : 0u) |
                         ((z % TZ) == 0 && z > 0 ? 4u : 0u);
-    const uint32_t hi = ((x % TX) == TX - 1 && x + 1 < A.nx ? 1u : 0u) | ((y % TY) == TY - 1 && y + 1 < A.ny ? 2u : 0u) |
-                        ((z % TZ) == TZ - 1 && z + 1 < A.nz ? 4u : 0u);
-    const uint32_t sy = A.tnx, sz = A.tnx * A.tny;
+    const uint32_t hi = ((x % TX) == TX - 1 && x + 1 < nx ? 1u : 0u) | ((y % TY) == TY - 1 && y + 1 < ny ? 2u : 0u) |
+                        ((z % TZ) == TZ - 1 && z + 1 < nz ? 4u : 0u);
+    const uint32_t sy = tnx, sz = tnx * tny;
 #pragma unroll 1
-    for (uint32_t m = lo; m; m = (m - 1) & lo)  // non-empty subsets of the low faces
+    for (uint32_t m = lo; m; m = (m - 1) & lo)
         mark_tile(bits, list, count, own - (m & 1u) - ((m >> 1) & 1u) * sy - ((m >> 2) & 1u) * sz);
 #pragma unroll 1
     for (uint32_t m = hi; m; m = (m - 1) & hi)
         mark_tile(bits, list, count, own + (m & 1u) + ((m >> 1) & 1u) * sy + ((m >> 2) & 1u) * sz);
 }
 
-__global__ void __launch_bounds__(CTA) k_apply(Dev D, int frontier)
+enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
+
+// One tile of the apply list per block iteration.  The tile's request words
+// are read (and cleared), the requested vertices compacted into a dense list
+// that all threads work through, and the changed vertices collected as row
+// bits in shared memory.
+//   PLAIN / FRONTIER: apply the bounded edit (Sec. 3.3) to each requested,
+//     unpinned vertex (at the iteration cap: count it instead), keep the CP
+//     values in gs, queue CP pairs and pinned neighbourhoods; FRONTIER also
+//     sets the next pass's dirty bits -- the closed stars of the changed
+//     vertices, by shifting each changed-row word into the seven star rows
+//     (0,0), -(1,0), -(0,1), -(1,1), +(1,0), +(0,1), +(1,1) (x-1..x+1 in the
+//     centre row, x-1..x below, x..x+1 above) -- and queues their tiles.
+//   COUNT: add the requested (pinned) vertices to the field's residual.
+template <int AM>
+__global__ void __launch_bounds__(CTA) k_apply_tiles(Dev D)
 {
-    const unsigned long long count = D.ls->req_count;
+    __shared__ uint32_t s_rw[ROWS], s_cw[ROWS], s_pre[ROWS + 1];
+    __shared__ uint32_t s_nb, s_cap;
+    const unsigned long long count = D.ls->apply_count;
     const uint32_t nxt = D.ls->cur ^ 1u;
-    const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
-    uint32_t cached = 0xFFFFFFFFu, flagged = 0xFFFFFFFFu;
-    ApplyField A{};
-    // block-uniform loop: every lane of a warp takes part in the warp collectives below
-    for (unsigned long long base = (unsigned long long)blockIdx.x * CTA; base < count; base += stride) {
-        const unsigned long long j = base + threadIdx.x;
-        bool applied = false, cp = false, pinned = false;
-        uint32_t fid = 0xFFFFFFFFu;
-        unsigned long long q = 0, r = 0;
-        if (j < count) {
-            const unsigned long long e = D.req_list[j];
-            fid = (uint32_t)(e >> LOCAL_BITS);
-            const uint64_t t = e & LOCAL_MASK;
-            if (fid != cached) {
-                load_apply_field(D, fid, A);
-                cached = fid;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long nreq = 0;
+    for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
+        const uint32_t tile = D.apply_list[it];
+        const uint32_t fid = field_of_tile(D, tile);
+        const FieldDesc &F = D.fields[fid];
+        FieldState *S = &D.fst[fid];
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny, N = F.N;
+        const uint32_t lt = (uint32_t)(tile - F.tbase);
+        const uint32_t rest = lt / tnx, tx = lt - rest * tnx, tz = rest / tny, ty = rest - tz * tny;
+        const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+        const uint64_t vbase = F.vbase, wbase = F.wbase;
+        if (threadIdx.x < ROWS) {
+            const uint32_t y = y0 + threadIdx.x % TY, z = z0 + threadIdx.x / TY;
+            uint32_t W = 0;
+            if (y < ny && z < nz) {
+                uint32_t *wp = D.reqw + wbase + ((uint64_t)z * ny + y) * tnx + tx;
+                W = *wp;
+                if (W) *wp = 0;
             }
-            const uint64_t gid = A.vbase + t;
-            atomicAnd(&D.reqbits[gid >> 5], ~(1u << (gid & 31)));
-            if (!A.err) {
-                uint32_t kk = D.k[gid];
-                if (A.iterations >= A.max_iters) {
-                    // at the cap only requests to unpinned vertices are violations left to fix
-                    if (kk <= A.N) atomicAdd(&D.fst[fid].capped, 1ull);
-                } else {
-                    if (kk <= A.N) {  // pinned targets are requested but never change
-                        const float fl = __fsub_rn(A.f[t], A.xi);
+            s_rw[threadIdx.x] = W;
+            s_cw[threadIdx.x] = 0;
+        }
+        if (threadIdx.x == 0) {
+            atomicAnd(&D.apply_bits[tile >> 5], ~(1u << (tile & 31)));
+            s_nb = 0;
+            s_cap = 0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t c = lane < ROWS ? __popc(s_rw[lane]) : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+                if (lane >= o) c += y;
+            }
+            if (lane < ROWS) s_pre[lane + 1] = c;
+            if (lane == 0) s_pre[0] = 0;
+        }
+        __syncthreads();
+        const int nvisit = (int)s_pre[ROWS];
+        if (threadIdx.x == 0) nreq += nvisit;
+        if (AM == AM_COUNT) {
+            if (threadIdx.x == 0 && nvisit) atomicAdd(&S->pinned_res, (unsigned long long)nvisit);
+            __syncthreads();
+            continue;
+        }
+        const bool err = S->err != 0, capped = S->iterations >= F.max_iters;
+        for (int base = 0; base < nvisit; base += CTA) {
+            const int k = base + threadIdx.x;
+            const bool sel = k < nvisit && !err;
+            bool applied = false, pinned = false, has_lo = false, has_hi = false;
+            unsigned long long q = 0;
+            uint32_t x = 0, y = 0, z = 0;
+            if (sel) {
+                int row = 0;
+#pragma unroll
+                for (int step = 8; step >= 1; step >>= 1)
+                    if (row + step <= ROWS - 1 && (int)s_pre[row + step] <= k) row += step;
+                const int lx = nth_set_bit(s_rw[row], k - (int)s_pre[row]);
+                x = x0 + lx;
+                y = y0 + row % TY;
+                z = z0 + row / TY;
+                const uint64_t t = ((uint64_t)z * ny + y) * nx + x;
+                const uint32_t d = D.desc[vbase + t];
+                uint32_t kk = d >> D_K_SHIFT;
+                if (kk <= N) {  // a pinned target stays as it is
+                    if (capped) {
+                        atomicAdd(&s_cap, 1u);
+                    } else {
+                        const float fl = __fsub_rn(F.f[t], F.xi);
                         float gv;
-                        if (kk < A.N) {
-                            const float tt = __fsub_rn(A.g[t], A.delta);
+                        if (kk < N) {
+                            const float tt = __fsub_rn(F.g[t], F.delta);
                             if (tt < fl) {
                                 gv = fl;
-                                kk = A.N + 1;
+                                kk = N + 1;
                             } else {
                                 gv = tt;
                                 kk = kk + 1;
                             }
                         } else {
                             gv = fl;
-                            kk = A.N + 1;
+                            kk = N + 1;
                         }
-                        A.g[t] = gv;
-                        D.k[gid] = (uint8_t)kk;
+                        F.g[t] = gv;
+                        D.desc[vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
                         applied = true;
-                        pinned = kk == A.N + 1;
-                        if (frontier || pinned) {
-                            uint32_t x, y, z;
-                            if (A.n < (1ull << 32)) {
-                                const uint32_t t32 = (uint32_t)t, row = fdiv(t32, A.div_nx);
-                                x = t32 - row * A.nx;
-                                z = fdiv(row, A.div_ny);
-                                y = row - z * A.ny;
-                            } else {
-                                const uint64_t row = t / A.nx;
-                                x = (uint32_t)(t - row * A.nx);
-                                z = (uint32_t)(row / A.ny);
-                                y = (uint32_t)(row - (uint64_t)z * A.ny);
-                            }
-                            if (frontier) {
-                                mark_star_dirty(A, D.dirty, x, y, z);
-                                mark_star_tiles(A, x, y, z, D.tile_bits, D.tile_list[nxt], &D.ls->tile_count[nxt]);
-                            }
-                            if (pinned)
-                                mark_star_tiles(A, x, y, z, D.pin_tile_bits, D.pin_tile_list, &D.ls->pin_tile_count);
-                        }
-                        if (D.desc[gid] & D_CP) {
-                            r = D.cp_rank[gid];
-                            q = A.cp_base + r;
+                        pinned = kk == N + 1;
+                        atomicOr(&s_cw[row], 1u << lx);
+                        if (d & D_CP) {  // value in sorted order; pairs inside the field
+                            const unsigned long long r = D.cp_rank[vbase + t];
+                            q = S->cp_base + r;
                             D.gs[q] = gv;
-                            cp = frontier || pinned;
+                            if (AM == AM_FRONTIER || pinned) {
+                                has_lo = r >= 1;
+                                has_hi = r + 1 < S->ncp;
+                            }
                         }
                     }
                 }
             }
-        }
-        // "this field had an edit this pass": one store per warp and field
-        const uint32_t peers = __match_any_sync(0xffffffffu, applied ? fid : 0xFFFFFFFFu);
-        if (applied && (peers & lanemask_lt()) == 0 && flagged != fid) {
-            D.fst[fid].had_req = 1;
-            flagged = fid;
-        }
-        // CP pairs (q-1, q) and (q, q+1) inside the field around an edited
-        // critical point: warp-aggregated appends; the frontier list is
-        // deduplicated through the pair bitmap
-        const bool has_lo = cp && r >= 1, has_hi = cp && r + 1 < A.ncp;
-        if (frontier && __any_sync(0xffffffffu, cp)) {
-            bool new_lo = false, new_hi = false;
-            if (has_hi) {
-                const uint32_t bit = 1u << (q & 31);
-                new_hi = !(__ldcg(&D.pairbits[q >> 5]) & bit) && !(atomicOr(&D.pairbits[q >> 5], bit) & bit);
+            if (AM == AM_FRONTIER && __any_sync(0xffffffffu, has_lo || has_hi)) {
+                bool new_lo = false, new_hi = false;
+                if (has_hi) {
+                    const uint32_t bit = 1u << (q & 31);
+                    new_hi = !(atomicOr(&D.pairbits[q >> 5], bit) & bit);
+                }
+                if (has_lo) {
+                    const unsigned long long p0 = q - 1;
+                    const uint32_t bit = 1u << (p0 & 31);
+                    new_lo = !(atomicOr(&D.pairbits[p0 >> 5], bit) & bit);
+                }
+                const unsigned long long p = warp_reserve((uint32_t)new_hi + (uint32_t)new_lo, &D.ls->pair_count[nxt]);
+                if (new_hi) D.pair_list[nxt][p] = (uint32_t)q;
+                if (new_lo) D.pair_list[nxt][p + (new_hi ? 1 : 0)] = (uint32_t)(q - 1);
             }
-            if (has_lo) {
-                const unsigned long long p0 = q - 1;
-                const uint32_t bit = 1u << (p0 & 31);
-                new_lo = !(__ldcg(&D.pairbits[p0 >> 5]) & bit) && !(atomicOr(&D.pairbits[p0 >> 5], bit) & bit);
+            const uint32_t npp = pinned ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
+            if (__any_sync(0xffffffffu, npp != 0)) {
+                const unsigned long long p = warp_reserve(npp, &D.ls->pin_pair_count);
+                if (pinned && has_hi) D.pin_pair_list[p] = (uint32_t)q;
+                if (pinned && has_lo) D.pin_pair_list[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
             }
-            const uint32_t np = (uint32_t)new_hi + (uint32_t)new_lo;
-            const unsigned long long p = warp_reserve(np, &D.ls->pair_count[nxt]);
-            if (new_hi) D.pair_list[nxt][p] = (uint32_t)q;
-            if (new_lo) D.pair_list[nxt][p + (new_hi ? 1 : 0)] = (uint32_t)(q - 1);
+            if (pinned)  // the residual check revisits the closed stars of pinned vertices
+                mark_star_tiles(tile, x, y, z, nx, ny, nz, tnx, tny, D.pin_tile_bits, D.pin_tile_list,
+                                &D.ls->pin_tile_count);
+            (void)applied;
         }
-        const uint32_t npp = pinned && cp ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
-        if (__any_sync(0xffffffffu, npp != 0)) {
-            const unsigned long long p = warp_reserve(npp, &D.ls->pin_pair_count);
-            if (pinned && has_hi) D.pin_pair_list[p] = (uint32_t)q;
-            if (pinned && has_lo) D.pin_pair_list[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_cap) atomicAdd(&S->capped, (unsigned long long)s_cap);
+            bool any = false;
+            for (int r = 0; r < ROWS; r++) any |= s_cw[r] != 0;
+            if (any && !S->had_req) S->had_req = 1;
         }
+        if (AM == AM_FRONTIER) {
+            // dirty bits: thread (row, star row k) for row < ROWS, k < 7
+            const int row = threadIdx.x / 7, k = threadIdx.x - row * 7;
+            if (row < ROWS && s_cw[row]) {
+                const uint32_t C = s_cw[row];
+                const uint32_t y = y0 + row % TY, z = z0 + row / TY;
+                const int dy = (k == 1 || k == 3) ? -1 : ((k == 4 || k == 6) ? 1 : 0);
+                const int dz = (k == 2 || k == 3) ? -1 : ((k == 5 || k == 6) ? 1 : 0);
+                const int Y = (int)y + dy, Z = (int)z + dz;
+                if (Y >= 0 && Z >= 0 && Y < (int)ny && Z < (int)nz) {
+                    const bool lo = k <= 3, hi = k == 0 || k >= 4;
+                    uint32_t m = C;
+                    if (lo) m |= C >> 1;
+                    if (hi) m |= C << 1;
+                    const uint64_t wi = wbase + ((uint64_t)Z * ny + (uint64_t)Y) * tnx + tx;
+                    const int oy = Y < (int)y0 ? -1 : (Y >= (int)(y0 + TY) ? 1 : 0);
+                    const int oz = Z < (int)z0 ? -1 : (Z >= (int)(z0 + TZ) ? 1 : 0);
+                    uint32_t nb = 1u << nb_index(0, oy, oz);
+                    atomicOr(&D.dirty[wi], m);
+                    if (lo && (C & 1u) && tx > 0) {
+                        atomicOr(&D.dirty[wi - 1], 0x80000000u);
+                        nb |= 1u << nb_index(-1, oy, oz);
+                    }
+                    if (hi && (C >> 31) && tx + 1 < tnx) {
+                        atomicOr(&D.dirty[wi + 1], 1u);
+                        nb |= 1u << nb_index(1, oy, oz);
+                    }
+                    atomicOr(&s_nb, nb);
+                }
+            }
+            __syncthreads();
+            mark_nb_tiles(s_nb, tile, tnx, tny, D.tile_bits, D.tile_list[nxt], &D.ls->tile_count[nxt]);
+        }
+        __syncthreads();
     }
+    if (AM != AM_COUNT && threadIdx.x == 0 && nreq) atomicAdd(&D.ls->sum_requests, nreq);
 }
 
 // ------------------------------------------------------------ bookkeeping
@@ -968,13 +976,12 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
     if (threadIdx.x == 0) {
         LoopState *L = D.ls;
         const uint32_t c = L->cur;
-        L->sum_requests += L->req_count;
         L->sum_tiles += L->tile_count[c];
         L->sum_pairs += L->pair_count[c];
         L->tile_count[c] = 0;
         L->pair_count[c] = 0;
         L->cur = c ^ 1u;
-        L->req_count = 0;
+        L->apply_count = 0;
         L->pass += 1;
         L->any_active = s_any;
         if (use_graph) cudaGraphSetConditional(h, s_any ? 1u : 0u);
@@ -996,20 +1003,7 @@ __global__ void k_loop_flag(Dev D, cudaGraphConditionalHandle h, int use_graph)
     }
 }
 
-// ------------------------------------------------------------ residual / status
-__global__ void __launch_bounds__(CTA) k_finish(Dev D)
-{
-    const unsigned long long count = D.ls->req_count;
-    for (unsigned long long j = blockIdx.x * (unsigned long long)CTA + threadIdx.x; j < count;
-         j += (unsigned long long)gridDim.x * CTA) {
-        const unsigned long long e = D.req_list[j];
-        const uint32_t fid = (uint32_t)(e >> LOCAL_BITS);
-        const uint64_t gid = D.fields[fid].vbase + (e & LOCAL_MASK);
-        atomicAnd(&D.reqbits[gid >> 5], ~(1u << (gid & 31)));
-        atomicAdd(&D.fst[fid].pinned_res, 1ull);
-    }
-}
-
+// ------------------------------------------------------------ status
 __global__ void k_status(Dev D)
 {
     for (uint32_t f = threadIdx.x + blockIdx.x * blockDim.x; f < D.nfields; f += blockDim.x * gridDim.x) {
@@ -1019,7 +1013,7 @@ __global__ void k_status(Dev D)
         else if (S->capped) S->status = ST_ITER_LIMIT;
         else S->status = (S->pinned_res ? ST_STUCK : ST_CONVERGED);
     }
-    if (threadIdx.x == 0 && blockIdx.x == 0) D.ls->req_count = 0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) D.ls->apply_count = 0;
 }
 
 // ------------------------------------------------------------ edit list
@@ -1046,18 +1040,16 @@ __global__ void __launch_bounds__(CTA) k_edit_count(Dev D)
     const uint32_t N = D.fields[fid].N;
     const uint64_t b = v0 + threadIdx.x * EPT;
     uint32_t c = 0, l = 0;
-    const uint4 *kp = reinterpret_cast<const uint4 *>(D.k + b);
-    for (int j = 0; j < EPT / 16; j++) {
-        const uint4 w = kp[j];
+    const uint4 *dp = reinterpret_cast<const uint4 *>(D.desc + b);
+#pragma unroll
+    for (int j = 0; j < EPT / 4; j++) {
+        const uint4 w = dp[j];
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-#pragma unroll
-            for (int s = 0; s < 4; s++) {
-                const uint32_t kk = (ws[u] >> (8 * s)) & 255u;
-                c += kk != 0;
-                l += kk == N + 1;
-            }
+            const uint32_t kk = ws[u] >> D_K_SHIFT;
+            c += kk != 0;
+            l += kk == N + 1;
         }
     }
     __syncthreads();
@@ -1080,15 +1072,27 @@ __global__ void __launch_bounds__(CTA) k_edit_write(Dev D)
     if (!F.edits) return;
     const uint32_t N = F.N;
     const uint64_t b = v0 + threadIdx.x * EPT;
+    uint32_t kks[EPT];
     uint32_t c = 0;
-    for (int j = 0; j < EPT; j++) c += D.k[b + j] != 0;
+    const uint4 *dp = reinterpret_cast<const uint4 *>(D.desc + b);
+#pragma unroll
+    for (int j = 0; j < EPT / 4; j++) {
+        const uint4 w = dp[j];
+        kks[4 * j + 0] = w.x >> D_K_SHIFT;
+        kks[4 * j + 1] = w.y >> D_K_SHIFT;
+        kks[4 * j + 2] = w.z >> D_K_SHIFT;
+        kks[4 * j + 3] = w.w >> D_K_SHIFT;
+    }
+#pragma unroll
+    for (int j = 0; j < EPT; j++) c += kks[j] != 0;
     uint32_t ex;
     block_excl_scan(c, ex, sw);
     const unsigned long long fbase = D.blk_off[F.vbase / VBLOCK];
     unsigned long long pos = D.blk_off[blockIdx.x] + ex - fbase;
     if (!c) return;
+#pragma unroll
     for (int j = 0; j < EPT; j++) {
-        const uint32_t kk = D.k[b + j];
+        const uint32_t kk = kks[j];
         if (!kk) continue;
         if (pos < F.edits_cap) {
             const uint64_t t = b + j - F.vbase;
@@ -1186,7 +1190,8 @@ void launch_pairs_pinned(const Dev &D, cudaStream_t s) { k_pairs<PM_PINNED><<<sm
 
 void launch_apply(const Dev &D, int frontier, cudaStream_t s)
 {
-    k_apply<<<sms() * 8, CTA, 0, s>>>(D, frontier);
+    if (frontier) k_apply_tiles<AM_FRONTIER><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
+    else k_apply_tiles<AM_PLAIN><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
 }
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s)
 {
@@ -1198,7 +1203,7 @@ void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph,
 }
 void launch_finish(const Dev &D, cudaStream_t s)
 {
-    k_finish<<<sms() * 2, CTA, 0, s>>>(D);
+    k_apply_tiles<AM_COUNT><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
     k_status<<<(D.nfields + 255) / 256, 256, 0, s>>>(D);
 }
 void launch_edit_list(const Dev &D, int write, cudaStream_t s)
