@@ -31,6 +31,12 @@ namespace exz {
 
 enum { SM_SETUP = 0, SM_CHECK_ALL = 1, SM_CHECK_LIST = 2, SM_PINNED = 3, SM_CLASSIFY = 4 };
 
+// Block-size assumptions of the kernels below.
+static_assert(TX == 32, "one row word (and one warp) per tile row");
+static_assert(CTA % 32 == 0 && ROWS <= 32, "tile-row prefix sums run in one warp");
+static_assert(CTA >= 7 * ROWS && CTA >= 27, "dirty dilation: one thread per (row, star row); 27 neighbour tiles");
+static_assert(WBLOCK % CTA == 0 && VBLOCK % (4 * CTA) == 0, "compaction and edit-list blocks");
+
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
 // ------------------------------------------------------------ requests
@@ -212,7 +218,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
 // staged in shared memory (NaN outside the domain), then every vertex (SETUP,
 // CHECK_ALL, PINNED, CLASSIFY) or every dirty vertex (CHECK_LIST) is checked.
 template <int MODE>
-__global__ void __launch_bounds__(CTA) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out)
+__global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out)
 {
     __shared__ float sa[HALO_N];
     __shared__ float sb[MODE == SM_SETUP ? HALO_N : 1];
@@ -582,6 +588,9 @@ __global__ void k_cp_ncp(Dev D)
 }
 
 // ------------------------------------------------------------ radix sort (stable LSD)
+// The sort kernels run RADIX threads per block: thread d owns digit d.
+constexpr int RADIX = 256;
+constexpr int SWARPS = RADIX / 32;
 // Pass p < 4: digit p of the 32-bit value key; pass p >= 4: digit p-4 of the field id.
 __device__ __forceinline__ uint32_t sort_digit(int pass, uint32_t key, unsigned long long ent)
 {
@@ -589,8 +598,8 @@ __device__ __forceinline__ uint32_t sort_digit(int pass, uint32_t key, unsigned 
     return (uint32_t)(ent >> (LOCAL_BITS + 8 * (pass - 4))) & 255u;
 }
 
-__global__ void __launch_bounds__(CTA) k_sort_hist(Dev D, int pass, const uint32_t *ksrc,
-                                                   const unsigned long long *esrc)
+__global__ void __launch_bounds__(RADIX) k_sort_hist(Dev D, int pass, const uint32_t *ksrc,
+                                                     const unsigned long long *esrc)
 {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
@@ -598,7 +607,7 @@ __global__ void __launch_bounds__(CTA) k_sort_hist(Dev D, int pass, const uint32
     const unsigned long long count = D.ls->total_cp;
     const unsigned long long chunk = (count + gridDim.x - 1) / gridDim.x;
     const unsigned long long b = blockIdx.x * chunk, e = min(count, b + chunk);
-    for (unsigned long long j = b + threadIdx.x; j < e; j += CTA) {
+    for (unsigned long long j = b + threadIdx.x; j < e; j += RADIX) {
         const uint32_t key = pass < 4 ? ksrc[j] : 0u;
         const unsigned long long ent = pass < 4 ? 0ull : esrc[j];
         atomicAdd(&h[sort_digit(pass, key, ent)], 1u);
@@ -609,22 +618,22 @@ __global__ void __launch_bounds__(CTA) k_sort_hist(Dev D, int pass, const uint32
 
 // last != 0: this is the final pass; also record each critical point's rank
 // within its field (cp_rank), which the frontier uses to find its CP pairs.
-__global__ void __launch_bounds__(CTA) k_sort_scatter(Dev D, int pass, const uint32_t *ksrc,
-                                                      const unsigned long long *esrc, uint32_t *kdst,
-                                                      unsigned long long *edst, int last)
+__global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const uint32_t *ksrc,
+                                                        const unsigned long long *esrc, uint32_t *kdst,
+                                                        unsigned long long *edst, int last)
 {
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_wc[WARPS][256];
-    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_run[RADIX];
+    __shared__ uint32_t s_wc[SWARPS][RADIX];
+    __shared__ uint32_t s_tot[RADIX];
     const int warp = threadIdx.x >> 5;
     const unsigned long long count = D.ls->total_cp;
     const unsigned long long chunk = (count + gridDim.x - 1) / gridDim.x;
     const unsigned long long b = blockIdx.x * chunk, e = min(count, b + chunk);
     s_run[threadIdx.x] = D.hist[threadIdx.x * gridDim.x + blockIdx.x];
     const bool move_keys = pass < 3;  // keys are not needed after the last value pass
-    for (unsigned long long base = b; base < e; base += CTA) {
+    for (unsigned long long base = b; base < e; base += RADIX) {
 #pragma unroll
-        for (int w = 0; w < WARPS; w++) s_wc[w][threadIdx.x] = 0;
+        for (int w = 0; w < SWARPS; w++) s_wc[w][threadIdx.x] = 0;
         __syncthreads();
         const unsigned long long j = base + threadIdx.x;
         const bool valid = j < e;
@@ -643,7 +652,7 @@ __global__ void __launch_bounds__(CTA) k_sort_scatter(Dev D, int pass, const uin
         {
             uint32_t s = 0;
 #pragma unroll
-            for (int w = 0; w < WARPS; w++) {
+            for (int w = 0; w < SWARPS; w++) {
                 const uint32_t t = s_wc[w][threadIdx.x];
                 s_wc[w][threadIdx.x] = s;
                 s += t;
@@ -772,7 +781,7 @@ enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
 //     centre row, x-1..x below, x..x+1 above) -- and queues their tiles.
 //   COUNT: add the requested (pinned) vertices to the field's residual.
 template <int AM>
-__global__ void __launch_bounds__(CTA) k_apply_tiles(Dev D)
+__global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
 {
     __shared__ uint32_t s_rw[ROWS], s_cw[ROWS], s_pre[ROWS + 1];
     __shared__ uint32_t s_nb, s_cap;
@@ -1176,9 +1185,9 @@ void launch_cp_sort(const Dev &D, cudaStream_t s)
     int src = 0;
     for (int p = 0; p < P; p++) {
         const int dst = src ^ 1;
-        k_sort_hist<<<B, CTA, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src]);
-        k_scan_inplace_u32<<<1, 1024, 0, s>>>(D.hist, (uint64_t)256 * B);
-        k_sort_scatter<<<B, CTA, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src], D.cp_key[dst], D.cp_ent[dst],
+        k_sort_hist<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src]);
+        k_scan_inplace_u32<<<1, 1024, 0, s>>>(D.hist, (uint64_t)RADIX * B);
+        k_sort_scatter<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src], D.cp_key[dst], D.cp_ent[dst],
                                          p == P - 1);
         src = dst;
     }
