@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--fields", type=int, default=256, help="field count of the batched workload")
     return p.parse_args()
 
 
@@ -374,10 +375,99 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- many fields
+def run_batched(a):
+    """256 uneven fields corrected in one run (one launch per stage per pass over
+    all fields, CUDA-graph loop) against the same fields one call at a time."""
+    import torch
+
+    import paper_2604_01397_b300 as ez
+    import synth
+
+    specs = synth.batched_specs(count=a.fields)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    fs, fhs, xis = [], [], []
+    for sp in specs:
+        f, fh, xi = synth.make_case(sp["kind"], sp["dims"], sp["seed"], sp["rel"], sp["fhat"],
+                                    n_bumps=sp["n_bumps"], sigma=sp["sigma"], device=dev)
+        fs.append(f)
+        fhs.append(fh)
+        xis.append(xi)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    dims = [sp["dims"] for sp in specs]
+    n_total = sum(f.numel() for f in fs)
+    ws = ez.Workspace(dims)
+    gs = [torch.empty_like(f) for f in fs]
+    caps = [min(f.numel(), 1 << 22) for f in fs]
+    ebufs = [torch.empty((c, 16), dtype=torch.uint8, device=dev) for c in caps]
+    stream = torch.cuda.current_stream()
+
+    def batched(mode="graph"):
+        return ws.correct(fs, fhs, xis, mode=mode, g_out=gs, edit_bufs=ebufs)
+
+    for _ in range(max(3, a.warmup)):
+        rs = batched()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index, enabled=not a.no_clocks)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for _ in range(a.steps):
+        rs = batched()
+        launches += ws.stats()["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    st = ws.stats()
+
+    # the same fields one call at a time, each with its own workspace (made beforehand)
+    per = [ez.Workspace([d]) for d in dims]
+    g1 = [torch.empty_like(f) for f in fs]
+    loop_ms = {}
+    same = True
+    for mode in ("graph", "plain"):
+        for i in range(len(fs)):  # warm-up: graphs captured, caches primed
+            per[i].correct([fs[i]], [fhs[i]], [xis[i]], mode=mode, g_out=[g1[i]], edit_bufs=[ebufs[i]])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(len(fs)):
+            r1 = per[i].correct([fs[i]], [fhs[i]], [xis[i]], mode=mode, g_out=[g1[i]], edit_bufs=[ebufs[i]])[0]
+            same &= r1["iterations"] == rs[i]["iterations"] and r1["status"] == rs[i]["status"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms[mode] = e0.elapsed_time(e1)
+        same &= all(torch.equal(g1[i].view(torch.int32), gs[i].view(torch.int32)) for i in range(len(fs)))
+    for w in per:
+        w.close()
+    value = 4.0 * n_total / (ms / 1e3) / 1e9
+    iters = [r["iterations"] for r in rs]
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": max(3, a.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(fs)} fields, axes U{{32..256}}, Gaussian bumps (volume/4096, sigma~U[2,8]) "
+                                   f"+ N(0,0.01), seeds 1000+j, xi 1e-3/1e-4 alternating, f_hat = f + U(-xi,xi)",
+                       "vertices": n_total, "mode": "graph, all fields in one run", "parallelism": "replicas x1"},
+            "gpu_launches": launches, "clocks": clk,
+            "extras": {"per_field_graph_ms": loop_ms["graph"], "per_field_plain_ms": loop_ms["plain"],
+                       "speedup_vs_per_field_graph": loop_ms["graph"] / ms,
+                       "speedup_vs_per_field_plain": loop_ms["plain"] / ms,
+                       "per_field_plain_gbs": 4.0 * n_total / (loop_ms["plain"] / 1e3) / 1e9,
+                       "same_results": bool(same), "passes": st["passes"], "max_iterations": max(iters),
+                       "mean_iterations": statistics.mean(iters), "generation_s": gen_s,
+                       "workspace_gib": ws.nbytes / 2 ** 30}}
+    print(json.dumps(line), flush=True)
+    ws.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched":
+        run_batched(a)
     else:
         run_ours(a)
 
