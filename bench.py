@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--fields", type=int, default=256, help="field count of the batched workload")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     return p.parse_args()
 
 
@@ -266,6 +267,8 @@ def run_ours(a):
     def step(mode=a.mode, profile=True):
         return ws.correct([f], [fh], [xi], mode=mode, g_out=[g], edit_bufs=[ebuf], profile=profile)[0]
 
+    tuning = ws.autotune([f], [fh], [xi], repeats=2) if not a.no_autotune else ws.tuning()
+
     for _ in range(max(3, a.warmup)):
         r = step()
     if dist:
@@ -366,7 +369,7 @@ def run_ours(a):
             "warmup": max(3, a.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(c), "mode": a.mode, "l2": "inputs larger than L2 (4n bytes per field)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tuning": tuning},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * 1,
             "clocks": clk, "extras": extras}
     print(json.dumps(line), flush=True)
@@ -406,6 +409,8 @@ def run_batched(a):
 
     def batched(mode="graph"):
         return ws.correct(fs, fhs, xis, mode=mode, g_out=gs, edit_bufs=ebufs)
+
+    tuning = ws.autotune(fs, fhs, xis, repeats=1) if not a.no_autotune else ws.tuning()
 
     for _ in range(max(3, a.warmup)):
         rs = batched()
@@ -449,7 +454,8 @@ def run_batched(a):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(fs)} fields, axes U{{32..256}}, Gaussian bumps (volume/4096, sigma~U[2,8]) "
                                    f"+ N(0,0.01), seeds 1000+j, xi 1e-3/1e-4 alternating, f_hat = f + U(-xi,xi)",
-                       "vertices": n_total, "mode": "graph, all fields in one run", "parallelism": "replicas x1"},
+                       "vertices": n_total, "mode": "graph, all fields in one run", "parallelism": "replicas x1",
+                       "tuning": tuning},
             "gpu_launches": launches, "clocks": clk,
             "extras": {"per_field_graph_ms": loop_ms["graph"], "per_field_plain_ms": loop_ms["plain"],
                        "speedup_vs_per_field_graph": loop_ms["graph"] / ms,

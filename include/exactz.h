@@ -162,6 +162,35 @@ typedef struct {
 
 int exactz_ws_stats(const exactz_workspace *ws, exactz_stats *out);
 
+/* ---- launch-schedule autotuning (the paper has no counterpart) ---- */
+
+/* The per-pass kernels' launch schedule on a workspace: resident blocks per SM
+ * of the tile-check, tile-apply and CP-pair kernels, and whether each block
+ * takes a contiguous chunk of the tile list (1) or every grid-th tile (0).
+ * Defaults: 16, 16, 8, 0.  The schedule never changes any result. */
+typedef struct {
+    uint32_t stencil_blocks_per_sm;
+    uint32_t apply_blocks_per_sm;
+    uint32_t pairs_blocks_per_sm;
+    uint32_t chunked_schedule;
+    float best_ms; /* exactz_ws_autotune: time of the best schedule (ms) */
+} exactz_tuning;
+
+int exactz_ws_get_tuning(const exactz_workspace *ws, exactz_tuning *out);
+/* Values out of range (blocks per SM outside 1..64, chunked_schedule > 1)
+ * return EXACTZ_EINVAL. */
+int exactz_ws_set_tuning(exactz_workspace *ws, const exactz_tuning *t);
+
+/* Pick the schedule for these fields by timing whole corrections on
+ * cuda_stream (coordinate descent over the four knobs, best of `repeats`
+ * runs, 0 = 2).  The fields are device arrays as for exactz_ws_correct; the
+ * call allocates scratch outputs for the trial runs and frees them.  The
+ * chosen schedule stays with the workspace and is written to *out. */
+int exactz_ws_autotune(exactz_workspace *ws, uint32_t nfields, const float *const *f,
+                       const float *const *fhat, const exactz_dims *d, const float *xi,
+                       const exactz_opts *opts, void *cuda_stream, uint32_t repeats,
+                       exactz_tuning *out);
+
 /* ---- inspection of the set-up stage (Sec. 3.2, Sec. 4.3) ---- */
 
 /* Per-vertex descriptor of field h (device arrays of n entries):

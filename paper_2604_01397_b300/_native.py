@@ -54,13 +54,20 @@ class Stats(ctypes.Structure):
                 ("stage_ms", ctypes.c_float * 8)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("stencil_blocks_per_sm", ctypes.c_uint32), ("apply_blocks_per_sm", ctypes.c_uint32),
+                ("pairs_blocks_per_sm", ctypes.c_uint32), ("chunked_schedule", ctypes.c_uint32),
+                ("best_ms", ctypes.c_float)]
+
+
 STAGES = ["setup", "compact", "sort", "first_pass", "loop", "finish", "edit_list", "total"]
 
 assert ctypes.sizeof(Edit) == 16 and ctypes.sizeof(Result) == 48
 
 EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exactz_workspace_create",
            "exactz_workspace_destroy", "exactz_workspace_bytes", "exactz_ws_correct", "exactz_classify",
-           "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc"]
+           "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc",
+           "exactz_ws_get_tuning", "exactz_ws_set_tuning", "exactz_ws_autotune"]
 
 _lib = None
 
@@ -94,6 +101,14 @@ def lib():
                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Opts), PP, PP,
                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), P, ctypes.c_int]
     L.exactz_ws_correct.restype = ctypes.c_int
+    L.exactz_ws_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    L.exactz_ws_get_tuning.restype = ctypes.c_int
+    L.exactz_ws_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    L.exactz_ws_set_tuning.restype = ctypes.c_int
+    L.exactz_ws_autotune.argtypes = [P, ctypes.c_uint32, PP, PP, ctypes.POINTER(Dims),
+                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Opts), P, ctypes.c_uint32,
+                                     ctypes.POINTER(Tuning)]
+    L.exactz_ws_autotune.restype = ctypes.c_int
     L.exactz_ws_stats.argtypes = [P, ctypes.POINTER(Stats)]
     L.exactz_ws_stats.restype = ctypes.c_int
     L.exactz_classify.argtypes = [P, Dims, P, P, P]

@@ -110,6 +110,33 @@ class Workspace:
                     sum_tiles=int(st.sum_tiles), sum_pairs=int(st.sum_pairs),
                     stage_ms={k: float(v) for k, v in zip(N.STAGES, st.stage_ms)})
 
+    def tuning(self) -> dict:
+        t = N.Tuning()
+        N.lib().exactz_ws_get_tuning(self._h, ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in N.Tuning._fields_}
+
+    def set_tuning(self, stencil_blocks_per_sm=16, apply_blocks_per_sm=16, pairs_blocks_per_sm=8,
+                   chunked_schedule=0):
+        t = N.Tuning(stencil_blocks_per_sm, apply_blocks_per_sm, pairs_blocks_per_sm, chunked_schedule, 0.0)
+        rc = N.lib().exactz_ws_set_tuning(self._h, ctypes.byref(t))
+        if rc != N.EXACTZ_OK:
+            raise ExactzError(rc, "exactz_ws_set_tuning")
+
+    def autotune(self, fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "graph", repeats: int = 2,
+                 stream=None) -> dict:
+        """Pick the launch schedule for these fields by timing whole corrections."""
+        nf = len(fs)
+        dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
+        t = N.Tuning()
+        o = make_opts(N_steps, mode, 1_000_000, False)
+        rc = N.lib().exactz_ws_autotune(
+            self._h, nf, N.ptr_array([x.data_ptr() for x in fs]), N.ptr_array([x.data_ptr() for x in fhats]),
+            (N.Dims * nf)(*[N.Dims(*d) for d in dl]), (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis]),
+            ctypes.byref(o), ctypes.c_void_p(_stream(stream)), int(repeats), ctypes.byref(t))
+        if rc != N.EXACTZ_OK:
+            raise ExactzError(rc, "exactz_ws_autotune")
+        return {k: getattr(t, k) for k, _ in N.Tuning._fields_}
+
     @property
     def nbytes(self) -> int:
         return int(N.lib().exactz_workspace_bytes(self._h))

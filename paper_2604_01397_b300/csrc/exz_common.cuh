@@ -144,6 +144,13 @@ struct LoopState {
     uint32_t overflow;
 };
 
+// Launch schedule of the per-pass kernels (chosen by the autotuner): blocks per
+// SM of the tile-check, tile-apply and CP-pair kernels, and whether a block
+// takes a contiguous chunk of the tile list (1) or every gridDim-th tile (0).
+struct Tuning {
+    uint32_t stencil_bps = 16, apply_bps = 16, pairs_bps = 8, chunked = 0;
+};
+
 // All device pointers of one workspace, passed to kernels by value.
 struct Dev {
     const FieldDesc *fields;
@@ -179,7 +186,24 @@ struct Dev {
     unsigned long long *blk_off;
     uint32_t *hist;
     uint32_t sort_blocks;
+    Tuning tun;
 };
+
+// Tiles [beg, end) with stride `step` of a list of `count` tiles handled by this block.
+__device__ __forceinline__ void tile_range(const Dev &D, unsigned long long count, unsigned long long &beg,
+                                           unsigned long long &end, unsigned long long &step)
+{
+    if (D.tun.chunked) {
+        const unsigned long long c = (count + gridDim.x - 1) / gridDim.x;
+        beg = blockIdx.x * c;
+        end = min(count, beg + c);
+        step = 1;
+    } else {
+        beg = blockIdx.x;
+        end = count;
+        step = gridDim.x;
+    }
+}
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t field_of_tile(const Dev &D, uint32_t tile)

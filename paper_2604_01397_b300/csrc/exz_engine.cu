@@ -162,6 +162,7 @@ struct exactz_workspace {
     uint64_t layout_hash = 0;  // dims of the previous run (padding must hold k = 0, no CP bits)
     exactz_stats stats{};
     cudaEvent_t ev[9] = {};
+    Tuning tun;
 
     std::mutex mu;
 };
@@ -309,13 +310,17 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.blk_off = ws->blk_off;
     D.hist = ws->hist;
     D.sort_blocks = ws->sort_blocks;
+    D.tun = ws->tun;
     return D;
 }
 
 // Graph: [loop-flag kernel] -> while (flag) { check, pairs, apply, bookkeeping }.
 int ensure_graph(exactz_workspace *ws, const Dev &D)
 {
-    const uint64_t key[5] = {D.nfields, D.total_tiles, D.total_v, D.total_w, (uint64_t)(uintptr_t)D.o};
+    const uint64_t key[5] = {D.nfields, D.total_tiles, D.total_v, D.total_w,
+                             (uint64_t)(uintptr_t)D.o ^ ((uint64_t)D.tun.stencil_bps << 48) ^
+                                 ((uint64_t)D.tun.apply_bps << 40) ^ ((uint64_t)D.tun.pairs_bps << 32) ^
+                                 ((uint64_t)D.tun.chunked << 56)};
     if (ws->gexec && std::memcmp(key, ws->gkey, sizeof(key)) == 0) return EXACTZ_OK;
     if (ws->gexec) {
         cudaGraphExecDestroy(ws->gexec);
@@ -622,6 +627,111 @@ int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const
     std::lock_guard<std::mutex> lk(ws->mu);
     return run(ws, nfields, f, fhat, d, xi, opts, g_out, edits_out, edits_cap, res,
                static_cast<cudaStream_t>(cuda_stream), host_buffers);
+}
+
+int exactz_ws_get_tuning(const exactz_workspace *ws, exactz_tuning *out)
+{
+    if (!ws || !out) return EXACTZ_EINVAL;
+    out->stencil_blocks_per_sm = ws->tun.stencil_bps;
+    out->apply_blocks_per_sm = ws->tun.apply_bps;
+    out->pairs_blocks_per_sm = ws->tun.pairs_bps;
+    out->chunked_schedule = ws->tun.chunked;
+    out->best_ms = 0.f;
+    return EXACTZ_OK;
+}
+
+int exactz_ws_set_tuning(exactz_workspace *ws, const exactz_tuning *t)
+{
+    if (!ws || !t) return EXACTZ_EINVAL;
+    if (t->stencil_blocks_per_sm < 1 || t->stencil_blocks_per_sm > 64 || t->apply_blocks_per_sm < 1 ||
+        t->apply_blocks_per_sm > 64 || t->pairs_blocks_per_sm < 1 || t->pairs_blocks_per_sm > 64 ||
+        t->chunked_schedule > 1)
+        return EXACTZ_EINVAL;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    ws->tun.stencil_bps = t->stencil_blocks_per_sm;
+    ws->tun.apply_bps = t->apply_blocks_per_sm;
+    ws->tun.pairs_bps = t->pairs_blocks_per_sm;
+    ws->tun.chunked = t->chunked_schedule;
+    return EXACTZ_OK;
+}
+
+// Coordinate descent over the launch schedule: each knob in turn takes every
+// candidate value with the others fixed, and keeps the one whose whole
+// correction of these fields ran fastest (CUDA events on the caller's stream,
+// best of `repeats`).  The result never depends on the schedule.
+int exactz_ws_autotune(exactz_workspace *ws, uint32_t nfields, const float *const *f, const float *const *fhat,
+                       const exactz_dims *d, const float *xi, const exactz_opts *opts, void *cuda_stream,
+                       uint32_t repeats, exactz_tuning *out)
+{
+    if (!ws || !out) return EXACTZ_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<float *> gtmp(nfields, nullptr);
+    std::vector<exactz_result> res(nfields);
+    int rc = EXACTZ_OK;
+    for (uint32_t i = 0; i < nfields && !rc; i++) {
+        if (!d) { rc = EXACTZ_EINVAL; break; }
+        const uint64_t n = (uint64_t)d[i].nx * d[i].ny * d[i].nz;
+        if (cudaMalloc(&gtmp[i], n * 4) != cudaSuccess) rc = EXACTZ_ENOMEM;
+    }
+    exactz_opts o;
+    exactz_default_opts(&o);
+    if (opts) o = *opts;
+    o.want_edit_list = 0;
+    o.profile = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = EXACTZ_ENODEV;
+    auto time_one = [&](float &ms) -> int {
+        ms = 1e30f;
+        for (uint32_t r = 0; r < (repeats ? repeats : 2); r++) {
+            cudaEventRecord(e0, s);
+            int c = exactz_ws_correct(ws, nfields, f, fhat, d, xi, &o, gtmp.data(), nullptr, nullptr, res.data(),
+                                      cuda_stream, 0);
+            cudaEventRecord(e1, s);
+            if (c != EXACTZ_OK && c != EXACTZ_ECAP) return c;
+            if (cudaEventSynchronize(e1) != cudaSuccess) return EXACTZ_ENODEV;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        return EXACTZ_OK;
+    };
+    float best = 0.f;
+    if (!rc) rc = time_one(best);  // also warms the graph and caches
+    if (!rc) rc = time_one(best);
+    static const uint32_t bps[] = {4, 8, 16, 32};
+    static const uint32_t pbps[] = {2, 4, 8, 16};
+    for (int knob = 0; knob < 4 && !rc; knob++) {
+        const int nc = knob == 3 ? 2 : 4;
+        Tuning keep = ws->tun;
+        for (int c = 0; c < nc && !rc; c++) {
+            Tuning cand = keep;
+            if (knob == 0) cand.stencil_bps = bps[c];
+            else if (knob == 1) cand.apply_bps = bps[c];
+            else if (knob == 2) cand.pairs_bps = pbps[c];
+            else cand.chunked = (uint32_t)c;
+            if (std::memcmp(&cand, &keep, sizeof(Tuning)) == 0) continue;
+            {
+                std::lock_guard<std::mutex> lk(ws->mu);
+                ws->tun = cand;
+            }
+            float t = 0.f;
+            rc = time_one(t);
+            if (!rc && t < best) {
+                best = t;
+                keep = cand;
+            }
+        }
+        std::lock_guard<std::mutex> lk(ws->mu);
+        ws->tun = keep;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (float *p : gtmp)
+        if (p) cudaFree(p);
+    if (rc) return rc;
+    exactz_ws_get_tuning(ws, out);
+    out->best_ms = best;
+    return EXACTZ_OK;
 }
 
 int exactz_correct_batch(uint32_t nfields, const float *const *f, const float *const *fhat, const exactz_dims *d,

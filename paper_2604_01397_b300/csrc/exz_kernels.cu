@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
+    unsigned long long it0, it1, its;
+    tile_range(D, count, it0, it1, its);
+    for (unsigned long long it = it0; it < it1; it += its) {
         const uint32_t tile = list ? list[it] : (uint32_t)it;
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
@@ -789,7 +791,9 @@ __global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
     const uint32_t nxt = D.ls->cur ^ 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long nreq = 0;
-    for (unsigned long long it = blockIdx.x; it < count; it += gridDim.x) {
+    unsigned long long it0, it1, its;
+    tile_range(D, count, it0, it1, its);
+    for (unsigned long long it = it0; it < it1; it += its) {
         const uint32_t tile = D.apply_list[it];
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
@@ -1145,11 +1149,11 @@ void launch_setup(const Dev &D, cudaStream_t s)
 }
 void launch_check_all(const Dev &D, cudaStream_t s)
 {
-    k_stencil<SM_CHECK_ALL><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr);
+    k_stencil<SM_CHECK_ALL><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(D, nullptr, nullptr);
 }
 void launch_check_list(const Dev &D, cudaStream_t s)
 {
-    k_stencil<SM_CHECK_LIST><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr);
+    k_stencil<SM_CHECK_LIST><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(D, nullptr, nullptr);
 }
 void launch_check_pinned(const Dev &D, cudaStream_t s)
 {
@@ -1194,13 +1198,13 @@ void launch_cp_sort(const Dev &D, cudaStream_t s)
 }
 
 void launch_pairs_all(const Dev &D, cudaStream_t s) { k_pairs<PM_ALL><<<sms() * 8, CTA, 0, s>>>(D); }
-void launch_pairs_list(const Dev &D, cudaStream_t s) { k_pairs<PM_LIST><<<sms() * 8, CTA, 0, s>>>(D); }
+void launch_pairs_list(const Dev &D, cudaStream_t s) { k_pairs<PM_LIST><<<sms() * D.tun.pairs_bps, CTA, 0, s>>>(D); }
 void launch_pairs_pinned(const Dev &D, cudaStream_t s) { k_pairs<PM_PINNED><<<sms() * 4, CTA, 0, s>>>(D); }
 
 void launch_apply(const Dev &D, int frontier, cudaStream_t s)
 {
-    if (frontier) k_apply_tiles<AM_FRONTIER><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
-    else k_apply_tiles<AM_PLAIN><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
+    if (frontier) k_apply_tiles<AM_FRONTIER><<<grid_for(D.total_tiles, 1, D.tun.apply_bps), CTA, 0, s>>>(D);
+    else k_apply_tiles<AM_PLAIN><<<grid_for(D.total_tiles, 1, D.tun.apply_bps), CTA, 0, s>>>(D);
 }
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s)
 {

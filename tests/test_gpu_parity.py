@@ -204,3 +204,30 @@ def test_workspace_reuse_and_host_buffers():
             assert_same(rh, ref, f.size)
     finally:
         ws.close()
+
+
+def test_launch_schedule_never_changes_results():
+    import paper_2604_01397_b300 as ez
+
+    specs = [((40, 36, 30), 5, "uniform", 1e-2), ((33, 5, 7), 11, "uniform", 3e-2), ((64, 8, 8), 12, "quantised", 1e-2)]
+    cases = [_case(*sp) for sp in specs]
+    fs = [to_dev(c[0], sp[0]) for c, sp in zip(cases, specs)]
+    fhs = [to_dev(c[1], sp[0]) for c, sp in zip(cases, specs)]
+    xis = [c[2] for c in cases]
+    refs = [oracle_run(c[0], c[1], c[2], sp[0]) for c, sp in zip(cases, specs)]
+    ws = ez.Workspace([sp[0] for sp in specs])
+    try:
+        for sched in [(4, 4, 2, 0), (32, 8, 16, 1), (16, 32, 4, 1)]:
+            ws.set_tuning(*sched)
+            for mode in MODES:
+                for r, ref, c in zip(ws.correct(fs, fhs, xis, mode=mode), refs, cases):
+                    assert_same(r, ref, c[0].size)
+        t = ws.autotune(fs, fhs, xis, repeats=1)
+        assert t["stencil_blocks_per_sm"] in (4, 8, 16, 32) and t["chunked_schedule"] in (0, 1)
+        assert t["best_ms"] > 0 and ws.tuning()["apply_blocks_per_sm"] == t["apply_blocks_per_sm"]
+        for r, ref, c in zip(ws.correct(fs, fhs, xis), refs, cases):
+            assert_same(r, ref, c[0].size)
+        with pytest.raises(ez.ExactzError):
+            ws.set_tuning(0, 16, 8, 0)
+    finally:
+        ws.close()
