@@ -105,6 +105,8 @@ struct FieldDesc {
     uint64_t max_iters;
     struct EditRec *edits;  // output edit list (device), may be null
     uint64_t edits_cap;
+    uint32_t *pin_tiles;    // tiles around this field's pinned vertices (capacity: its tile count)
+    uint32_t *pin_pairs;    // CP pairs next to its pinned critical points (capacity: 2 n)
     FastDiv div_nx, div_ny;  // x = t mod nx, row = t / nx, z = row / ny (fields below 2^32 vertices)
 };
 
@@ -125,6 +127,8 @@ struct FieldState {
     unsigned long long pinned_res;  // pinned vertices still requested at exit
     unsigned long long n_edits;
     unsigned long long n_lossless;
+    unsigned long long pin_tile_count;
+    unsigned long long pin_pair_count;
     uint32_t had_req, done, err, status;
 };
 
@@ -132,8 +136,6 @@ struct LoopState {
     unsigned long long apply_count;  // tiles holding requested vertices (this pass)
     unsigned long long tile_count[2];
     unsigned long long pair_count[2];
-    unsigned long long pin_tile_count;
-    unsigned long long pin_pair_count;
     unsigned long long total_cp;
     unsigned long long sum_requests;  // requests applied or skipped, over all passes
     unsigned long long sum_tiles;     // tiles checked by frontier passes
@@ -171,10 +173,8 @@ struct Dev {
     uint32_t *apply_bits;
     uint32_t *tile_list[2];
     uint32_t *tile_bits;
-    uint32_t *pin_tile_list;
     uint32_t *pin_tile_bits;
     uint32_t *pair_list[2];
-    uint32_t *pin_pair_list;
     uint32_t *cp_key[2];
     unsigned long long *cp_ent[2];
     unsigned long long *o;  // sorted critical points (aliases one of cp_ent)
@@ -187,6 +187,24 @@ struct Dev {
     uint32_t *hist;
     uint32_t sort_blocks;
     Tuning tun;
+};
+
+// Fields set up together: tiles [tile0, tile1), compaction blocks
+// [wblk0, wblk0 + nwblk) of the row-word bitmap, fields [fid0, fid1), and the
+// critical points placed from position cp0 on, their number in *cp_count.
+struct SetupRange {
+    uint32_t tile0, tile1;
+    uint64_t wblk0, nwblk;
+    uint32_t fid0, fid1;
+    uint64_t cp0;
+    unsigned long long *cp_count;
+};
+
+// Fields finished together: ids fids[0..n), arena blocks [vblk0, vblk0 + nvblk).
+struct FieldSet {
+    const uint32_t *fids;
+    uint32_t n;
+    uint64_t vblk0, nvblk;
 };
 
 // Tiles [beg, end) with stride `step` of a list of `count` tiles handled by this block.

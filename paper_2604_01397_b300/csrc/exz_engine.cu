@@ -77,6 +77,7 @@ struct Layout {
     uint64_t total_v = 0, total_w = 0, total_real = 0;
     uint32_t total_tiles = 0;
     std::vector<FieldDesc> fd;
+    std::vector<uint64_t> cpc;  // per field: sum of the vertex counts before it (CP capacity offset)
 };
 
 int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
@@ -84,6 +85,7 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
     if (nf == 0 || nf >= (1u << 24) || !d) return EXACTZ_EINVAL;
     L.nfields = nf;
     L.fd.assign(nf, FieldDesc{});
+    L.cpc.assign(nf, 0);
     uint64_t v = 0, w = 0, t = 0, real = 0;
     for (uint32_t i = 0; i < nf; i++) {
         const uint64_t nx = d[i].nx, ny = d[i].ny, nz = d[i].nz;
@@ -108,6 +110,7 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
         w = round_up(w, WBLOCK);
         F.wbase = w;
         w += ny * nz * F.tnx;
+        L.cpc[i] = real;
         real += n;
     }
     if (t >= (1ull << 32) || real >= (1ull << 32)) return EXACTZ_EINVAL;
@@ -137,8 +140,9 @@ struct exactz_workspace {
     uint32_t *dirty = nullptr, *pairbits = nullptr, *apply_list = nullptr, *apply_bits = nullptr;
     float *gs = nullptr;
     uint32_t *tile_list[2] = {nullptr, nullptr}, *tile_bits = nullptr;
-    uint32_t *pin_tile_list = nullptr, *pin_tile_bits = nullptr;
-    uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_list = nullptr;
+    uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
+    uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_arena = nullptr;
+    uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
     uint32_t *blk = nullptr;
@@ -246,11 +250,12 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->tile_list[0], T);
     AL(ws->tile_list[1], T);
     AL(ws->tile_bits, T / 32 + 1);
-    AL(ws->pin_tile_list, T);
+    AL(ws->pin_tile_arena, T);
     AL(ws->pin_tile_bits, T / 32 + 1);
     AL(ws->pair_list[0], 2 * C);
     AL(ws->pair_list[1], 2 * C);
-    AL(ws->pin_pair_list, 2 * C);
+    AL(ws->pin_pair_arena, 2 * C);
+    AL(ws->fids, L.nfields);
     AL(ws->cp_key[0], C);
     AL(ws->cp_key[1], C);
     AL(ws->cp_ent[0], C);
@@ -261,6 +266,11 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
 #undef AL
     CK(cudaMemcpy(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice));
     CK(cudaMemset(ws->desc, 0, V * 4));
+    {
+        std::vector<uint32_t> ids(L.nfields);
+        for (uint32_t i = 0; i < L.nfields; i++) ids[i] = i;
+        CK(cudaMemcpy(ws->fids, ids.data(), 4ull * L.nfields, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemset(ws->cpwords, 0, W * 4));
     CK(cudaMemset(ws->reqw, 0, W * 4));
     CK(cudaMemset(ws->dirty, 0, W * 4));
@@ -293,16 +303,14 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.tile_list[0] = ws->tile_list[0];
     D.tile_list[1] = ws->tile_list[1];
     D.tile_bits = ws->tile_bits;
-    D.pin_tile_list = ws->pin_tile_list;
     D.pin_tile_bits = ws->pin_tile_bits;
     D.pair_list[0] = ws->pair_list[0];
     D.pair_list[1] = ws->pair_list[1];
-    D.pin_pair_list = ws->pin_pair_list;
     D.cp_key[0] = ws->cp_key[0];
     D.cp_key[1] = ws->cp_key[1];
     D.cp_ent[0] = ws->cp_ent[0];
     D.cp_ent[1] = ws->cp_ent[1];
-    D.o = ws->cp_ent[sort_passes(L.nfields) & 1];
+    D.o = ws->cp_ent[sort_passes(0, L.nfields) & 1];
     D.multi = ws->d_multi;
     D.cp_cap = ws->cap_real;
     D.pair_cap = 2 * ws->cap_real;
@@ -426,6 +434,8 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         F.xi = xi[i];
         F.delta = xi[i] / (float)opt.N;  // binary32 division, Sec. 3.3
         F.max_iters = opt.max_iters;
+        F.pin_tiles = ws->pin_tile_arena + F.tbase;
+        F.pin_pairs = ws->pin_pair_arena + 2 * L.cpc[i];
         const bool has_edits = opt.want_edit_list && edits_out && edits_out[i] && caps && caps[i] > 0;
         F.edits_cap = has_edits ? caps[i] : 0;
         if (host) {
@@ -469,18 +479,20 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     auto mark = [&](int i) {
         if (prof) cudaEventRecord(ws->ev[i], s);
     };
-    const uint64_t P = (uint64_t)sort_passes(nf);
+    const uint64_t P = (uint64_t)sort_passes(0, nf);
+    const SetupRange R{0, L.total_tiles, 0, L.total_w / WBLOCK, 0, nf, 0, &ws->d_ls->total_cp};
+    const FieldSet FS{ws->fids, nf, 0, L.total_v / VBLOCK};
     uint64_t launches = 0;
 
     // set-up and the first pass
     mark(0);
-    launch_setup(D, s);
+    launch_setup(D, R, s);
     mark(1);
-    launch_cp_compact(D, s);
+    launch_cp_compact(D, R, s);
     mark(2);
-    launch_cp_sort(D, s);
+    launch_cp_sort(D, R, s);
     mark(3);
-    launch_pairs_all(D, s);
+    launch_pairs_all(D, R, s);
     launch_apply(D, frontier, s);
     launch_book(D, 0, 0, s);
     mark(4);
@@ -498,7 +510,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
             if (!ws->h_ls->any_active) break;
             if (opt.mode == EXACTZ_MODE_PLAIN) {
                 launch_check_all(D, s);
-                launch_pairs_all(D, s);
+                launch_pairs_all(D, R, s);
                 launch_apply(D, 0, s);
             } else {
                 launch_check_list(D, s);
@@ -512,11 +524,11 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     }
     mark(5);
     // residual violations on pinned vertices, status, edit list
-    launch_check_pinned(D, s);
-    launch_pairs_pinned(D, s);
-    launch_finish(D, s);
+    launch_check_pinned(D, FS, s);
+    launch_pairs_pinned(D, FS, s);
+    launch_finish(D, FS, s);
     mark(6);
-    launch_edit_list(D, opt.want_edit_list ? 1 : 0, s);
+    launch_edit_list(D, FS, opt.want_edit_list ? 1 : 0, s);
     mark(7);
     launches += 4 + (opt.want_edit_list ? 3 : 1);
     CK(cudaGetLastError());
@@ -807,13 +819,16 @@ int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t
         F.N = 5;
         F.xi = 1.0f;
         F.delta = 0.2f;
+        F.pin_tiles = ws->pin_tile_arena;
+        F.pin_pairs = ws->pin_pair_arena;
         const Dev D = make_dev(ws, L);
+        const SetupRange R{0, L.total_tiles, 0, L.total_w / WBLOCK, 0, 1, 0, &ws->d_ls->total_cp};
         cudaMemcpyAsync(ws->d_fields, L.fd.data(), sizeof(FieldDesc), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(ws->d_fst, 0, sizeof(FieldState), s);
         cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s);
-        launch_setup(D, s);
-        launch_cp_compact(D, s);
-        launch_cp_sort(D, s);
+        launch_setup(D, R, s);
+        launch_cp_compact(D, R, s);
+        launch_cp_sort(D, R, s);
         cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(ws->h_fst, ws->d_fst, sizeof(FieldState), cudaMemcpyDeviceToHost, s);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = EXACTZ_ENODEV;
@@ -907,9 +922,10 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
               c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_list, T) &&
               c.take(ws->apply_bits, T / 32 + 1) &&
               c.take(ws->tile_list[0], T) && c.take(ws->tile_list[1], T) && c.take(ws->tile_bits, T / 32 + 1) &&
-              c.take(ws->pin_tile_list, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
+              c.take(ws->pin_tile_arena, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
               c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
-              c.take(ws->pin_pair_list, 2 * C) && c.take(ws->cp_key[0], C) && c.take(ws->cp_key[1], C) &&
+              c.take(ws->pin_pair_arena, 2 * C) && c.take(ws->fids, L.nfields) && c.take(ws->cp_key[0], C) &&
+              c.take(ws->cp_key[1], C) &&
               c.take(ws->cp_ent[0], C) && c.take(ws->cp_ent[1], C) && c.take(ws->blk, nblk) &&
               c.take(ws->blk_off, nblk) && c.take(ws->hist, 256ull * ws->sort_blocks);
     if (!ok) return false;
@@ -959,7 +975,9 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     ws->h_fst = &g_noalloc_hfst[dev];
     ws->h_ls = &g_noalloc_hls[dev];
     // the array keeps the previous call's contents: reset what must start at zero
+    static const uint32_t zero_fid = 0;
     if (cudaMemcpyAsync(ws->d_multi, g_multi_host, sizeof(g_multi_host), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws->fids, &zero_fid, sizeof(zero_fid), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(ws->desc, 0, L.total_v * 4, s) != cudaSuccess ||
         cudaMemsetAsync(ws->reqw, 0, L.total_w * 4, s) != cudaSuccess ||
         cudaMemsetAsync(ws->cpwords, 0, L.total_w * 4, s) != cudaSuccess ||

@@ -217,8 +217,11 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
 // One tile per block iteration: the tile's values plus a one-vertex halo are
 // staged in shared memory (NaN outside the domain), then every vertex (SETUP,
 // CHECK_ALL, PINNED, CLASSIFY) or every dirty vertex (CHECK_LIST) is checked.
+// Tiles come from [t0, t1) (SETUP, CHECK_ALL, CLASSIFY), the current frontier
+// list (CHECK_LIST), or the pinned-tile lists of fields fids[0..nf) (PINNED).
 template <int MODE>
-__global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out)
+__global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
+                                                    uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
     __shared__ float sa[HALO_N];
     __shared__ float sb[MODE == SM_SETUP ? HALO_N : 1];
@@ -234,24 +237,25 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
         tt.nb = 0;
         s_err = 0;
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nouter = MODE == SM_PINNED ? nf : 1u;
+    for (uint32_t fi = 0; fi < nouter; fi++) {
     unsigned long long count;
     const uint32_t *list = nullptr;
     if (MODE == SM_SETUP || MODE == SM_CHECK_ALL || MODE == SM_CLASSIFY) {
-        count = D.total_tiles;
+        count = t1 - t0;
     } else if (MODE == SM_CHECK_LIST) {
         uint32_t c = D.ls->cur;
         count = D.ls->tile_count[c];
         list = D.tile_list[c];
     } else {
-        count = D.ls->pin_tile_count;
-        list = D.pin_tile_list;
+        count = D.fst[fids[fi]].pin_tile_count;
+        list = D.fields[fids[fi]].pin_tiles;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
     unsigned long long it0, it1, its;
     tile_range(D, count, it0, it1, its);
     for (unsigned long long it = it0; it < it1; it += its) {
-        const uint32_t tile = list ? list[it] : (uint32_t)it;
+        const uint32_t tile = list ? list[it] : t0 + (uint32_t)it;
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
@@ -389,6 +393,7 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
         }
+    }
     }
 }
 
@@ -529,10 +534,10 @@ __device__ __forceinline__ uint32_t field_of_word(const Dev &D, uint64_t w)
     return lo;
 }
 
-__global__ void __launch_bounds__(CTA) k_cp_count(Dev D)
+__global__ void __launch_bounds__(CTA) k_cp_count(Dev D, uint64_t wblk0)
 {
     __shared__ uint32_t sw[WARPS];
-    const uint64_t w0 = (uint64_t)blockIdx.x * WBLOCK + threadIdx.x * WPT;
+    const uint64_t w0 = (wblk0 + blockIdx.x) * WBLOCK + threadIdx.x * WPT;
     uint32_t c = 0;
 #pragma unroll
     for (int j = 0; j < WPT; j++) c += __popc(D.cpwords[w0 + j]);
@@ -541,10 +546,10 @@ __global__ void __launch_bounds__(CTA) k_cp_count(Dev D)
     if (threadIdx.x == 0) D.blk[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(CTA) k_cp_write(Dev D)
+__global__ void __launch_bounds__(CTA) k_cp_write(Dev D, uint64_t wblk0, uint64_t cp0)
 {
     __shared__ uint32_t sw[WARPS];
-    const uint64_t blk0 = (uint64_t)blockIdx.x * WBLOCK;
+    const uint64_t blk0 = (wblk0 + blockIdx.x) * WBLOCK;
     const uint32_t fid = field_of_word(D, blk0);
     const FieldDesc &F = D.fields[fid];
     const uint64_t w0 = blk0 + threadIdx.x * WPT;
@@ -557,8 +562,8 @@ __global__ void __launch_bounds__(CTA) k_cp_write(Dev D)
     }
     uint32_t ex;
     block_excl_scan(c, ex, sw);
-    unsigned long long pos = D.blk_off[blockIdx.x] + ex;
-    if (blk0 == F.wbase && threadIdx.x == 0) D.fst[fid].cp_base = D.blk_off[blockIdx.x];
+    unsigned long long pos = cp0 + D.blk_off[blockIdx.x] + ex;
+    if (blk0 == F.wbase && threadIdx.x == 0) D.fst[fid].cp_base = cp0 + D.blk_off[blockIdx.x];
     const uint64_t ny = F.ny;
 #pragma unroll
     for (int j = 0; j < WPT; j++) {
@@ -579,12 +584,12 @@ __global__ void __launch_bounds__(CTA) k_cp_write(Dev D)
     }
 }
 
-__global__ void k_cp_ncp(Dev D)
+__global__ void k_cp_ncp(Dev D, SetupRange R)
 {
-    const unsigned long long total = D.ls->total_cp;
-    for (uint32_t f = threadIdx.x + blockIdx.x * blockDim.x; f < D.nfields; f += blockDim.x * gridDim.x) {
+    const unsigned long long end = R.cp0 + *R.cp_count;
+    for (uint32_t f = R.fid0 + threadIdx.x + blockIdx.x * blockDim.x; f < R.fid1; f += blockDim.x * gridDim.x) {
         const unsigned long long b = D.fst[f].cp_base;
-        const unsigned long long e = (f + 1 < D.nfields) ? D.fst[f + 1].cp_base : total;
+        const unsigned long long e = (f + 1 < R.fid1) ? D.fst[f + 1].cp_base : end;
         D.fst[f].ncp = e - b;
     }
 }
@@ -601,12 +606,12 @@ __device__ __forceinline__ uint32_t sort_digit(int pass, uint32_t key, unsigned 
 }
 
 __global__ void __launch_bounds__(RADIX) k_sort_hist(Dev D, int pass, const uint32_t *ksrc,
-                                                     const unsigned long long *esrc)
+                                                     const unsigned long long *esrc, const unsigned long long *countp)
 {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const unsigned long long count = D.ls->total_cp;
+    const unsigned long long count = *countp;
     const unsigned long long chunk = (count + gridDim.x - 1) / gridDim.x;
     const unsigned long long b = blockIdx.x * chunk, e = min(count, b + chunk);
     for (unsigned long long j = b + threadIdx.x; j < e; j += RADIX) {
@@ -622,13 +627,14 @@ __global__ void __launch_bounds__(RADIX) k_sort_hist(Dev D, int pass, const uint
 // within its field (cp_rank), which the frontier uses to find its CP pairs.
 __global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const uint32_t *ksrc,
                                                         const unsigned long long *esrc, uint32_t *kdst,
-                                                        unsigned long long *edst, int last)
+                                                        unsigned long long *edst, int last,
+                                                        const unsigned long long *countp, uint64_t cp0)
 {
     __shared__ uint32_t s_run[RADIX];
     __shared__ uint32_t s_wc[SWARPS][RADIX];
     __shared__ uint32_t s_tot[RADIX];
     const int warp = threadIdx.x >> 5;
-    const unsigned long long count = D.ls->total_cp;
+    const unsigned long long count = *countp;
     const unsigned long long chunk = (count + gridDim.x - 1) / gridDim.x;
     const unsigned long long b = blockIdx.x * chunk, e = min(count, b + chunk);
     s_run[threadIdx.x] = D.hist[threadIdx.x * gridDim.x + blockIdx.x];
@@ -669,8 +675,8 @@ __global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const u
             if (last) {
                 const uint32_t fid = (uint32_t)(ent >> LOCAL_BITS);
                 const FieldDesc &F = D.fields[fid];
-                D.cp_rank[F.vbase + (ent & LOCAL_MASK)] = (uint32_t)(pos - D.fst[fid].cp_base);
-                D.gs[pos] = F.g[ent & LOCAL_MASK];  // g == f_hat before the first edit
+                D.cp_rank[F.vbase + (ent & LOCAL_MASK)] = (uint32_t)(cp0 + pos - D.fst[fid].cp_base);
+                D.gs[cp0 + pos] = F.g[ent & LOCAL_MASK];  // g == f_hat before the first edit
             }
         }
         __syncthreads();
@@ -688,25 +694,30 @@ enum { PM_ALL = 0, PM_LIST = 1, PM_PINNED = 2 };
 // target.  ALL: every pair (the first pass; pairs may straddle two fields).
 // LIST / PINNED: pairs queued by the apply kernel, always inside one field;
 // LIST also clears each pair's queued bit.  PINNED keeps pinned targets only.
+// ALL covers the CP segment [cp0, cp0 + *countp); PINNED the pinned-pair lists
+// of fields fids[0..nf).
 template <int PM>
-__global__ void __launch_bounds__(CTA) k_pairs(Dev D)
+__global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsigned long long *countp,
+                                               const uint32_t *fids, uint32_t nf)
 {
-    const unsigned long long total = D.ls->total_cp;
+    const uint32_t nouter = PM == PM_PINNED ? nf : 1u;
+    for (uint32_t fi = 0; fi < nouter; fi++) {
     unsigned long long count;
     const uint32_t *list = nullptr;
     if (PM == PM_ALL) {
+        const unsigned long long total = *countp;
         count = total ? total - 1 : 0;
     } else if (PM == PM_LIST) {
         const uint32_t c = D.ls->cur;
         count = D.ls->pair_count[c];
         list = D.pair_list[c];
     } else {
-        count = D.ls->pin_pair_count;
-        list = D.pin_pair_list;
+        count = D.fst[fids[fi]].pin_pair_count;
+        list = D.fields[fids[fi]].pin_pairs;
     }
     const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
     for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
-        const unsigned long long q = list ? (unsigned long long)list[j] : j;
+        const unsigned long long q = list ? (unsigned long long)list[j] : cp0 + j;
         if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
         const float ga = D.gs[q], gb = D.gs[q + 1];
         bool viol = gb < ga;
@@ -724,6 +735,7 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D)
             const uint64_t t = a & LOCAL_MASK;
             if (PM != PM_PINNED || (D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) request_vertex(D, F, t);
         }
+    }
     }
 }
 
@@ -910,13 +922,13 @@ __global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
             }
             const uint32_t npp = pinned ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
             if (__any_sync(0xffffffffu, npp != 0)) {
-                const unsigned long long p = warp_reserve(npp, &D.ls->pin_pair_count);
-                if (pinned && has_hi) D.pin_pair_list[p] = (uint32_t)q;
-                if (pinned && has_lo) D.pin_pair_list[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
+                const unsigned long long p = warp_reserve(npp, &S->pin_pair_count);
+                if (pinned && has_hi) F.pin_pairs[p] = (uint32_t)q;
+                if (pinned && has_lo) F.pin_pairs[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
             }
             if (pinned)  // the residual check revisits the closed stars of pinned vertices
-                mark_star_tiles(tile, x, y, z, nx, ny, nz, tnx, tny, D.pin_tile_bits, D.pin_tile_list,
-                                &D.ls->pin_tile_count);
+                mark_star_tiles(tile, x, y, z, nx, ny, nz, tnx, tny, D.pin_tile_bits, F.pin_tiles,
+                                &S->pin_tile_count);
             (void)applied;
         }
         __syncthreads();
@@ -1017,10 +1029,10 @@ __global__ void k_loop_flag(Dev D, cudaGraphConditionalHandle h, int use_graph)
 }
 
 // ------------------------------------------------------------ status
-__global__ void k_status(Dev D)
+__global__ void k_status(Dev D, FieldSet FS)
 {
-    for (uint32_t f = threadIdx.x + blockIdx.x * blockDim.x; f < D.nfields; f += blockDim.x * gridDim.x) {
-        FieldState *S = &D.fst[f];
+    for (uint32_t j = threadIdx.x + blockIdx.x * blockDim.x; j < FS.n; j += blockDim.x * gridDim.x) {
+        FieldState *S = &D.fst[FS.fids[j]];
         if (S->err & ERR_NONFINITE) S->status = (uint32_t)-2;
         else if (S->err & ERR_BOUND) S->status = (uint32_t)-3;
         else if (S->capped) S->status = ST_ITER_LIMIT;
@@ -1043,12 +1055,12 @@ __device__ __forceinline__ uint32_t field_of_vertex(const Dev &D, uint64_t v)
     return lo;
 }
 
-__global__ void __launch_bounds__(CTA) k_edit_count(Dev D)
+__global__ void __launch_bounds__(CTA) k_edit_count(Dev D, uint64_t vblk0)
 {
     __shared__ uint32_t sw[WARPS];
     __shared__ uint32_t s_lossless;
     if (threadIdx.x == 0) s_lossless = 0;
-    const uint64_t v0 = (uint64_t)blockIdx.x * VBLOCK;
+    const uint64_t v0 = (vblk0 + blockIdx.x) * VBLOCK;
     const uint32_t fid = field_of_vertex(D, v0);
     const uint32_t N = D.fields[fid].N;
     const uint64_t b = v0 + threadIdx.x * EPT;
@@ -1076,10 +1088,10 @@ __global__ void __launch_bounds__(CTA) k_edit_count(Dev D)
     }
 }
 
-__global__ void __launch_bounds__(CTA) k_edit_write(Dev D)
+__global__ void __launch_bounds__(CTA) k_edit_write(Dev D, uint64_t vblk0)
 {
     __shared__ uint32_t sw[WARPS];
-    const uint64_t v0 = (uint64_t)blockIdx.x * VBLOCK;
+    const uint64_t v0 = (vblk0 + blockIdx.x) * VBLOCK;
     const uint32_t fid = field_of_vertex(D, v0);
     const FieldDesc &F = D.fields[fid];
     if (!F.edits) return;
@@ -1100,7 +1112,7 @@ __global__ void __launch_bounds__(CTA) k_edit_write(Dev D)
     for (int j = 0; j < EPT; j++) c += kks[j] != 0;
     uint32_t ex;
     block_excl_scan(c, ex, sw);
-    const unsigned long long fbase = D.blk_off[F.vbase / VBLOCK];
+    const unsigned long long fbase = D.blk_off[F.vbase / VBLOCK - vblk0];
     unsigned long long pos = D.blk_off[blockIdx.x] + ex - fbase;
     if (!c) return;
 #pragma unroll
@@ -1143,63 +1155,82 @@ static unsigned grid_for(uint64_t items, int per_block, int cap_mult)
     return (unsigned)g;
 }
 
-void launch_setup(const Dev &D, cudaStream_t s)
+void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
-    k_stencil<SM_SETUP><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr);
+    k_stencil<SM_SETUP><<<grid_for(R.tile1 - R.tile0, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr, R.tile0, R.tile1,
+                                                                          nullptr, 0);
 }
 void launch_check_all(const Dev &D, cudaStream_t s)
 {
-    k_stencil<SM_CHECK_ALL><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(D, nullptr, nullptr);
+    k_stencil<SM_CHECK_ALL><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(
+        D, nullptr, nullptr, 0, D.total_tiles, nullptr, 0);
 }
 void launch_check_list(const Dev &D, cudaStream_t s)
 {
-    k_stencil<SM_CHECK_LIST><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(D, nullptr, nullptr);
+    k_stencil<SM_CHECK_LIST><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(
+        D, nullptr, nullptr, 0, 0, nullptr, 0);
 }
-void launch_check_pinned(const Dev &D, cudaStream_t s)
+void launch_check_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s)
 {
-    k_stencil<SM_PINNED><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr);
+    k_stencil<SM_PINNED><<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, nullptr, nullptr, 0, 0, FS.fids, FS.n);
 }
 void launch_classify(const Dev &D, uint32_t *desc_out, uint8_t *type_out, cudaStream_t s)
 {
-    k_stencil<SM_CLASSIFY><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, desc_out, type_out);
+    k_stencil<SM_CLASSIFY><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, desc_out, type_out, 0, D.total_tiles,
+                                                                         nullptr, 0);
 }
 
-void launch_cp_compact(const Dev &D, cudaStream_t s)
+void launch_cp_compact(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
-    const uint64_t nb = D.total_w / WBLOCK;
-    k_cp_count<<<(unsigned)nb, CTA, 0, s>>>(D);
-    k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, nb, &D.ls->total_cp);
-    k_cp_write<<<(unsigned)nb, CTA, 0, s>>>(D);
-    k_cp_ncp<<<(D.nfields + 255) / 256, 256, 0, s>>>(D);
+    const unsigned nb = (unsigned)R.nwblk;
+    k_cp_count<<<nb, CTA, 0, s>>>(D, R.wblk0);
+    k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, R.nwblk, R.cp_count);
+    k_cp_write<<<nb, CTA, 0, s>>>(D, R.wblk0, R.cp0);
+    k_cp_ncp<<<(R.fid1 - R.fid0 + 255) / 256, 256, 0, s>>>(D, R);
 }
 
-int sort_passes(uint32_t nfields)
+// LSD passes of one sort: four 8-bit digits of the value key, then the digits
+// of the field id when the range holds more than one field.
+int sort_passes(uint32_t fid0, uint32_t fid1)
 {
     int p = 4;
-    if (nfields > 1) p += 1;
-    if (nfields > 256) p += 1;
-    if (nfields > 65536) p += 1;
+    if (fid1 - fid0 > 1) {
+        const uint32_t top = fid1 - 1;
+        p += 1;
+        if (top > 255) p += 1;
+        if (top > 65535) p += 1;
+    }
     return p;
 }
 
-void launch_cp_sort(const Dev &D, cudaStream_t s)
+void launch_cp_sort(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
-    const int P = sort_passes(D.nfields);
+    const int P = sort_passes(R.fid0, R.fid1);
     const unsigned B = D.sort_blocks;
     int src = 0;
     for (int p = 0; p < P; p++) {
         const int dst = src ^ 1;
-        k_sort_hist<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src]);
+        k_sort_hist<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src] + R.cp0, D.cp_ent[src] + R.cp0, R.cp_count);
         k_scan_inplace_u32<<<1, 1024, 0, s>>>(D.hist, (uint64_t)RADIX * B);
-        k_sort_scatter<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src], D.cp_ent[src], D.cp_key[dst], D.cp_ent[dst],
-                                         p == P - 1);
+        k_sort_scatter<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src] + R.cp0, D.cp_ent[src] + R.cp0,
+                                           D.cp_key[dst] + R.cp0, D.cp_ent[dst] + R.cp0, p == P - 1, R.cp_count,
+                                           R.cp0);
         src = dst;
     }
 }
 
-void launch_pairs_all(const Dev &D, cudaStream_t s) { k_pairs<PM_ALL><<<sms() * 8, CTA, 0, s>>>(D); }
-void launch_pairs_list(const Dev &D, cudaStream_t s) { k_pairs<PM_LIST><<<sms() * D.tun.pairs_bps, CTA, 0, s>>>(D); }
-void launch_pairs_pinned(const Dev &D, cudaStream_t s) { k_pairs<PM_PINNED><<<sms() * 4, CTA, 0, s>>>(D); }
+void launch_pairs_all(const Dev &D, const SetupRange &R, cudaStream_t s)
+{
+    k_pairs<PM_ALL><<<sms() * 8, CTA, 0, s>>>(D, R.cp0, R.cp_count, nullptr, 0);
+}
+void launch_pairs_list(const Dev &D, cudaStream_t s)
+{
+    k_pairs<PM_LIST><<<sms() * D.tun.pairs_bps, CTA, 0, s>>>(D, 0, nullptr, nullptr, 0);
+}
+void launch_pairs_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s)
+{
+    k_pairs<PM_PINNED><<<sms() * 4, CTA, 0, s>>>(D, 0, nullptr, FS.fids, FS.n);
+}
 
 void launch_apply(const Dev &D, int frontier, cudaStream_t s)
 {
@@ -1214,18 +1245,18 @@ void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph,
 {
     k_loop_flag<<<1, 256, 0, s>>>(D, h, use_graph);
 }
-void launch_finish(const Dev &D, cudaStream_t s)
+void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s)
 {
     k_apply_tiles<AM_COUNT><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
-    k_status<<<(D.nfields + 255) / 256, 256, 0, s>>>(D);
+    k_status<<<(FS.n + 255) / 256, 256, 0, s>>>(D, FS);
 }
-void launch_edit_list(const Dev &D, int write, cudaStream_t s)
+void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s)
 {
-    const uint64_t nb = D.total_v / VBLOCK;
-    k_edit_count<<<(unsigned)nb, CTA, 0, s>>>(D);
+    const unsigned nb = (unsigned)FS.nvblk;
+    k_edit_count<<<nb, CTA, 0, s>>>(D, FS.vblk0);
     if (write) {
-        k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, nb, nullptr);
-        k_edit_write<<<(unsigned)nb, CTA, 0, s>>>(D);
+        k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, FS.nvblk, nullptr);
+        k_edit_write<<<nb, CTA, 0, s>>>(D, FS.vblk0);
     }
 }
 

@@ -6,21 +6,21 @@
 
 namespace exz {
 
-void launch_setup(const Dev &D, cudaStream_t s);
+void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s);
 void launch_check_all(const Dev &D, cudaStream_t s);
 void launch_check_list(const Dev &D, cudaStream_t s);
-void launch_check_pinned(const Dev &D, cudaStream_t s);
+void launch_check_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s);
 void launch_classify(const Dev &D, uint32_t *desc_out, uint8_t *type_out, cudaStream_t s);
-void launch_cp_compact(const Dev &D, cudaStream_t s);
-void launch_cp_sort(const Dev &D, cudaStream_t s);
-int sort_passes(uint32_t nfields);
-void launch_pairs_all(const Dev &D, cudaStream_t s);
+void launch_cp_compact(const Dev &D, const SetupRange &R, cudaStream_t s);
+void launch_cp_sort(const Dev &D, const SetupRange &R, cudaStream_t s);
+int sort_passes(uint32_t fid0, uint32_t fid1);
+void launch_pairs_all(const Dev &D, const SetupRange &R, cudaStream_t s);
 void launch_pairs_list(const Dev &D, cudaStream_t s);
-void launch_pairs_pinned(const Dev &D, cudaStream_t s);
+void launch_pairs_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s);
 void launch_apply(const Dev &D, int frontier, cudaStream_t s);
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);
 void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);
-void launch_finish(const Dev &D, cudaStream_t s);
-void launch_edit_list(const Dev &D, int write, cudaStream_t s);
+void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s);
+void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s);
 
 }  // namespace exz
