@@ -17,7 +17,7 @@ bounded crop of the same workload on the host cores, and the SM clocks
 sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload bumps512|bumps64|octave1024|batched] [--size S]
+                  [--workload bumps512|bumps64|octave1024|batched|serving] [--size S]
 
 With N > 1 (torchrun) every rank corrects its own replica of the workload
 (no data-path collective; a barrier and a max-reduction of the step time only).
@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--fields", type=int, default=256, help="field count of the batched workload")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
+    p.add_argument("--rates", default="50,200,800", help="serving workload: Poisson arrival rates (1/s)")
+    p.add_argument("--duration", type=float, default=10.0, help="serving workload: arrival window per rate (s)")
+    p.add_argument("--budget-gb", type=float, default=120.0, help="serving workload: HBM budget (GB)")
     return p.parse_args()
 
 
@@ -468,12 +471,185 @@ def run_batched(a):
     ws.close()
 
 
+# ---------------------------------------------------------------- serving
+POOL = {64: 8, 128: 6, 256: 4, 512: 2}  # distinct pre-generated fields per cube side
+QMAX = 128                              # outstanding requests before arrivals are shed
+
+
+def _percentile(xs, q):
+    if not xs:
+        return None
+    return float(np.percentile(np.asarray(xs), q))
+
+
+def _fifo(arrivals, service):
+    """A single FIFO worker (the per-request path) on the same arrivals, with
+    the same shedding rule as the server run: latencies, kept flags, end time."""
+    lat, kept, free_at, ends = [], [], 0.0, []
+    for t, s in zip(arrivals, service):
+        ends = [e for e in ends if e > t]
+        if len(ends) >= QMAX:
+            kept.append(False)
+            continue
+        free_at = max(t, free_at) + s
+        ends.append(free_at)
+        lat.append(free_at - t)
+        kept.append(True)
+    return lat, kept, free_at
+
+
+def run_serving(a):
+    """Poisson request streams served by the continuous-batching server, with
+    host buffers (copies in and out inside every latency), against the plain
+    per-request path on the same arrivals."""
+    import torch
+
+    import paper_2604_01397_b300 as ez
+    import synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rates = [float(x) for x in a.rates.split(",") if x]
+    streams = {lam: synth.serving_requests(lam, a.duration) for lam in rates}
+    # pool: the first POOL[side] requests of each side in the densest stream give the fields
+    t0 = time.perf_counter()
+    pool = {side: [] for side in POOL}
+    for sp in streams[max(rates)] + synth.serving_requests(max(rates), 60.0):
+        side = sp["dims"][0]
+        if len(pool[side]) >= POOL[side]:
+            continue
+        f, fh, xi = synth.make_case(sp["kind"], sp["dims"], sp["seed"], sp["rel"], sp["fhat"],
+                                    n_bumps=sp["n_bumps"], sigma=sp["sigma"], device=dev)
+        pool[side].append(dict(f=f.reshape(-1).cpu().pin_memory(), fh=fh.reshape(-1).cpu().pin_memory(),
+                               xi=xi, dims=sp["dims"], kind=sp["kind"], rel=sp["rel"]))
+        del f, fh
+        if all(len(pool[s]) >= POOL[s] for s in POOL):
+            break
+    gen_s = time.perf_counter() - t0
+    # output rings (results of in-flight requests may share a ring slot: only timing is read here)
+    rings = {side: [(torch.empty(side ** 3, dtype=torch.float32, pin_memory=True),
+                     torch.empty((side ** 3 // 4, 16), dtype=torch.uint8, pin_memory=True))
+                    for _ in range(2 if side >= 512 else 4)] for side in POOL}
+    budget = int(min(a.budget_gb * 1e9, torch.cuda.mem_get_info()[0] - 24e9))
+
+    def entry(sp):
+        side = sp["dims"][0]
+        return pool[side][sp["seed"] % len(pool[side])]
+
+    # the plain per-request path: one exactz_ws_correct per request, host buffers, plain loop
+    ws = ez.Workspace([(512, 512, 512)])
+    service = {}
+    for side in POOL:
+        for j, e in enumerate(pool[side]):
+            g, eb = rings[side][0]
+            kw = dict(dims=[e["dims"]], mode="plain", g_out=[g], edit_bufs=[eb], host_buffers=True)
+            ws.correct([e["f"]], [e["fh"]], [e["xi"]], **kw)  # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ref = ws.correct([e["f"]], [e["fh"]], [e["xi"]], **kw)[0]
+            torch.cuda.synchronize()
+            service[(side, j)] = time.perf_counter() - t
+            e["ref_iterations"], e["ref_status"] = ref["iterations"], ref["status"]
+    ws.close()
+
+    per_rate = []
+    launches = 0
+    clocks = Clocks(dev.index, enabled=not a.no_clocks)
+    for lam in rates:
+        reqs = streams[lam]
+        srv = ez.Server(budget_bytes=budget, max_fields=64, N_steps=5)
+        # warm the server once (first-use costs outside the stream)
+        e = pool[64][0]
+        srv.wait(srv.submit(e["f"], e["fh"], e["xi"], dims=e["dims"], g_out=rings[64][0][0],
+                            edit_buf=rings[64][0][1]), decode=False)
+        base_passes, base_launches = srv.stats()["passes"], srv.stats()["kernel_launches"]
+        out = {}
+        lat, shed, bytes_done, same, h2d, d2h = [], 0, 0, True, 0, 0
+        ring_i = {side: 0 for side in POOL}
+        i = 0
+        t_start = time.perf_counter()
+        last_done = t_start
+        while i < len(reqs) or out:
+            now = time.perf_counter() - t_start
+            while i < len(reqs) and reqs[i]["t"] <= now:
+                sp = reqs[i]
+                i += 1
+                if len(out) >= QMAX:
+                    shed += 1
+                    continue
+                side = sp["dims"][0]
+                e = entry(sp)
+                g, eb = rings[side][ring_i[side] % len(rings[side])]
+                ring_i[side] += 1
+                tk = srv.submit(e["f"], e["fh"], e["xi"], dims=e["dims"], g_out=g, edit_buf=eb)
+                out[tk] = (sp["t"], time.perf_counter() - t_start, e, g)
+            progressed = False
+            for tk in list(out):
+                r = srv.poll(tk, decode=False)
+                if r is None:
+                    continue
+                progressed = True
+                t_arr, t_sub, e, g = out.pop(tk)
+                # latency from the arrival instant: generator lag + submission to results in host memory
+                lat.append((t_sub - t_arr) + r["latency_s"])
+                n = e["f"].numel()
+                bytes_done += 4 * n
+                h2d += 8 * n
+                d2h += 4 * n + 16 * min(r["n_edits"], r["edits"].shape[0])
+                same &= r["iterations"] == e["ref_iterations"] and r["status"] == e["ref_status"]
+                last_done = time.perf_counter()
+            if not progressed:
+                time.sleep(0.0002)
+        wall = last_done - t_start
+        st = srv.stats()
+        launches += st["kernel_launches"] - base_launches
+        srv.close()
+        arr = [r["t"] for r in reqs]
+        svc = [service[(r["dims"][0], r["seed"] % len(pool[r["dims"][0]]))] for r in reqs]
+        plat, kept, pend = _fifo(arr, svc)
+        pbytes = sum(4 * r["dims"][0] ** 3 for r, ok in zip(reqs, kept) if ok)
+        pshed = kept.count(False)
+        per_rate.append({
+            "rate_per_s": lam, "requests": len(reqs), "completed": len(lat), "shed": shed,
+            "offered_gbs": sum(4 * r["dims"][0] ** 3 for r in reqs) / a.duration / 1e9,
+            "gbs": bytes_done / wall / 1e9, "p50_ms": _percentile(lat, 50) * 1e3, "p99_ms": _percentile(lat, 99) * 1e3,
+            "passes": st["passes"] - base_passes, "max_resident": st["max_resident"],
+            "h2d_bytes_per_request": h2d / max(1, len(lat)), "d2h_bytes_per_request": d2h / max(1, len(lat)),
+            "same_counts_as_per_request": bool(same),
+            "per_request_plain": {"gbs": pbytes / max(pend, 1e-9) / 1e9, "shed": pshed,
+                                  "p50_ms": _percentile(plat, 50) * 1e3, "p99_ms": _percentile(plat, 99) * 1e3},
+        })
+    clk = clocks.stop()
+    best = max(per_rate, key=lambda r: r["gbs"])
+    knee = max([r["rate_per_s"] for r in per_rate if r["shed"] == 0 and r["completed"] == r["requests"]
+                and r["gbs"] >= 0.9 * r["offered_gbs"]], default=None)
+    line = {"metric": METRIC, "value": best["gbs"], "unit": "GB/s", "n_gpus": 1, "steps": len(rates),
+            "warmup": 1, "ms_per_step": a.duration * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Poisson request streams, cubes 64/128/256/512 (p .4/.3/.2/.1), bumps or 3-octave "
+                                   "noise 50/50, xi 1e-3/1e-4 of range, f_hat by 2xi-quantisation, request seed 1e6+r; "
+                                   f"each request draws its field from a pool of {POOL} pre-generated fields",
+                       "rates_per_s": rates, "window_s": a.duration, "budget_bytes": budget, "max_fields": 64,
+                       "shed_above_outstanding": QMAX, "l2": "inputs larger than L2 (the 512^3 fields)",
+                       "latency": "arrival to g and edit list in pinned host memory",
+                       "per_request_path": "exactz_ws_correct, host buffers, plain loop; service time measured per "
+                                           "pool field, FIFO queue simulated on the same arrivals"},
+            "e2e": {"value": best["gbs"], "unit": "GB/s", "h2d_bytes_per_step": best["h2d_bytes_per_request"],
+                    "d2h_bytes_per_step": best["d2h_bytes_per_request"],
+                    "step": "one request (the value is already host to host)"},
+            "gpu_launches": launches, "clocks": clk, "knee_rate_per_s": knee, "per_rate": per_rate,
+            "extras": {"generation_s": gen_s, "service_s": {f"{k[0]}^3#{k[1]}": v for k, v in service.items()}}}
+    print(json.dumps(line), flush=True)
+
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batched":
         run_batched(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
         run_ours(a)
 

@@ -240,6 +240,69 @@ int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, flo
                            const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
                            uint64_t edits_cap, exactz_result *res, void *cuda_stream);
 
+/* ---- request server with continuous batching (the paper has no counterpart) ---- */
+
+/* A server corrects fields submitted one at a time from HOST memory.  It owns
+ * one device arena planned from budget_bytes (about 1/8 for edit records, the
+ * rest at 76 bytes per resident vertex) and a host thread that runs the passes
+ * of Algorithm 1 over every resident field at once.  At each pass boundary it
+ * admits queued requests in submission order while a field slot and arena room
+ * are free (a request that does not fit waits; later ones wait behind it),
+ * and retires fields whose loop ended: their residual check, status and edit
+ * list are computed, g and the edit list are copied into the caller's host
+ * buffers, and the room is freed.  Every field runs the passes of
+ * EXACTZ_MODE_FRONTIER; its result is bit-identical to exactz_correct's for
+ * the same input and options, whatever else is resident. */
+typedef struct exactz_server exactz_server;
+
+typedef struct {
+    uint64_t budget_bytes; /* device memory for the arena (>= 64 MiB) */
+    uint32_t max_fields;   /* resident fields at most (1..4096) */
+    uint32_t reserved;
+    exactz_opts opts;      /* N, max_iters, want_edit_list for every request (N = 0: defaults); mode ignored */
+} exactz_server_config;
+
+typedef struct {
+    uint64_t submitted, completed;
+    uint64_t passes;            /* passes the server ran */
+    uint64_t resident, queued;  /* now */
+    uint64_t max_resident;      /* most fields in one pass */
+    uint64_t admitted_vertices; /* sum of admitted fields' vertices */
+    uint64_t capacity_vertices; /* largest admissible field, in vertices */
+    uint64_t device_bytes;      /* device memory held */
+    uint64_t kernel_launches;   /* kernels launched so far */
+    double busy_s;              /* host time spent in passes */
+    int32_t error;              /* 0, or the CUDA failure that stopped the server (EXACTZ_ENODEV) */
+    int32_t reserved;
+} exactz_server_info;
+
+/* Returns NULL without a device, on a bad configuration or when the arena
+ * cannot be allocated.  The server uses the calling thread's current device. */
+exactz_server *exactz_server_create(const exactz_server_config *cfg);
+
+/* Queue one field.  f, fhat: HOST arrays of n floats; g_out: HOST array of n
+ * floats; edits_out: HOST array of edits_cap records, or NULL.  The buffers
+ * must stay valid and untouched until the request's result is taken (poll or
+ * wait returned 1); page-locked buffers copy fastest.  *ticket identifies the
+ * request.  Returns EXACTZ_EINVAL (bad dims, xi, pointers, or the server has
+ * stopped), EXACTZ_ESIZE (larger than an empty arena holds) or EXACTZ_OK.
+ * Invalid values (NaN, out of bound) are reported in the result's status. */
+int exactz_server_submit(exactz_server *s, const float *f, const float *fhat, exactz_dims d, float xi,
+                         float *g_out, exactz_edit *edits_out, uint64_t edits_cap, uint64_t *ticket);
+
+/* 1: done -- *res (status < 0 for invalid input; n_edits > edits_cap means
+ * the list was truncated) and *latency_s (submission to results in host
+ * memory) are filled and the ticket is released.  0: not yet (wait: timed
+ * out; timeout_s < 0 waits without limit).  EXACTZ_EINVAL: unknown ticket;
+ * EXACTZ_ENODEV: the server stopped on a CUDA failure. */
+int exactz_server_poll(exactz_server *s, uint64_t ticket, exactz_result *res, double *latency_s);
+int exactz_server_wait(exactz_server *s, uint64_t ticket, double timeout_s, exactz_result *res,
+                       double *latency_s);
+int exactz_server_stats(exactz_server *s, exactz_server_info *out);
+/* Finishes every submitted request, then frees the server.  Results not yet
+ * taken are discarded (their host buffers hold them). */
+void exactz_server_destroy(exactz_server *s);
+
 /* Library build / device information (host string, static storage). */
 const char *exactz_version(void);
 

@@ -10,6 +10,7 @@ from .api import (  # noqa: F401
     MODES,
     STATUS,
     ExactzError,
+    Server,
     Workspace,
     classify,
     correct,

@@ -60,6 +60,19 @@ class Tuning(ctypes.Structure):
                 ("best_ms", ctypes.c_float)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_fields", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("opts", Opts)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("passes", ctypes.c_uint64),
+                ("resident", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("max_resident", ctypes.c_uint64),
+                ("admitted_vertices", ctypes.c_uint64), ("capacity_vertices", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64), ("busy_s", ctypes.c_double), ("error", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 STAGES = ["setup", "compact", "sort", "first_pass", "loop", "finish", "edit_list", "total"]
 
 assert ctypes.sizeof(Edit) == 16 and ctypes.sizeof(Result) == 48
@@ -67,7 +80,9 @@ assert ctypes.sizeof(Edit) == 16 and ctypes.sizeof(Result) == 48
 EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exactz_workspace_create",
            "exactz_workspace_destroy", "exactz_workspace_bytes", "exactz_ws_correct", "exactz_classify",
            "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc",
-           "exactz_ws_get_tuning", "exactz_ws_set_tuning", "exactz_ws_autotune"]
+           "exactz_ws_get_tuning", "exactz_ws_set_tuning", "exactz_ws_autotune", "exactz_server_create",
+           "exactz_server_submit", "exactz_server_poll", "exactz_server_wait", "exactz_server_stats",
+           "exactz_server_destroy"]
 
 _lib = None
 
@@ -118,6 +133,20 @@ def lib():
     L.exactz_correct_noalloc.argtypes = [P, P, Dims, ctypes.c_float, ctypes.POINTER(Opts), P, P,
                                          ctypes.c_uint64, ctypes.POINTER(Result), P]
     L.exactz_correct_noalloc.restype = ctypes.c_int
+    L.exactz_server_create.argtypes = [ctypes.POINTER(ServerConfig)]
+    L.exactz_server_create.restype = P
+    L.exactz_server_submit.argtypes = [P, P, P, Dims, ctypes.c_float, P, P, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    L.exactz_server_submit.restype = ctypes.c_int
+    L.exactz_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_double)]
+    L.exactz_server_poll.restype = ctypes.c_int
+    L.exactz_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result),
+                                     ctypes.POINTER(ctypes.c_double)]
+    L.exactz_server_wait.restype = ctypes.c_int
+    L.exactz_server_stats.argtypes = [P, ctypes.POINTER(ServerInfo)]
+    L.exactz_server_stats.restype = ctypes.c_int
+    L.exactz_server_destroy.argtypes = [P]
+    L.exactz_server_destroy.restype = None
     L.exactz_version.argtypes = []
     L.exactz_version.restype = ctypes.c_char_p
     _lib = L

@@ -313,3 +313,108 @@ def correct_noalloc(f: torch.Tensor, fhat: torch.Tensor, xi: float, g_out: torch
     if edit_buf is not None:
         out["edits"] = decode_edits(edit_buf, out["n_edits"])
     return out
+
+
+class Server:
+    """Request server with continuous batching (exactz_server_*).
+
+    Fields are submitted from host memory (float32 CPU tensors, ideally pinned)
+    and corrected on the current CUDA device together with whatever else is
+    resident; each result equals correct(..., mode="frontier") for the same
+    input.  submit() returns a ticket; wait()/poll() return the result dict
+    (g and the edit list as CPU tensors, latency_s from submission to results
+    in host memory) once it is ready.
+    """
+
+    def __init__(self, budget_bytes: int, max_fields: int = 64, N_steps: int = 5,
+                 max_iters: int = 1_000_000, edits: bool = True):
+        cfg = N.ServerConfig()
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.max_fields = int(max_fields)
+        cfg.opts = make_opts(N_steps, "frontier", max_iters, edits)
+        self._h = N.lib().exactz_server_create(ctypes.byref(cfg))
+        if not self._h:
+            raise ExactzError(N.EXACTZ_ENOMEM, "exactz_server_create")
+        self.edits = bool(edits)
+        self._live = {}
+
+    def submit(self, f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, edits_cap=None,
+               g_out: Optional[torch.Tensor] = None, edit_buf: Optional[torch.Tensor] = None) -> int:
+        """Queue one field; g_out / edit_buf (a (cap, 16) uint8 host tensor) are
+        allocated here unless given."""
+        _check(f, "f", host=True)
+        _check(fhat, "fhat", host=True)
+        d = dims_of(f, dims)
+        g = torch.empty(f.shape, dtype=torch.float32, pin_memory=f.is_pinned()) if g_out is None else g_out
+        _check(g, "g_out", host=True)
+        if g.numel() < f.numel():
+            raise ValueError("g_out is smaller than the field")
+        if not self.edits:
+            buf, cap = None, 0
+        elif edit_buf is not None:
+            if edit_buf.is_cuda or edit_buf.dtype != torch.uint8 or edit_buf.dim() != 2 or edit_buf.shape[1] != 16:
+                raise ValueError("edit_buf must be a (cap, 16) uint8 host tensor")
+            buf, cap = edit_buf, int(edit_buf.shape[0])
+        else:
+            cap = default_edits_cap(f.numel()) if edits_cap is None else int(edits_cap)
+            buf = torch.empty((cap, 16), dtype=torch.uint8, pin_memory=f.is_pinned()) if cap else None
+        t = ctypes.c_uint64()
+        rc = N.lib().exactz_server_submit(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(fhat.data_ptr()),
+                                          N.Dims(*d), ctypes.c_float(float(np.float32(xi))),
+                                          ctypes.c_void_p(g.data_ptr()),
+                                          ctypes.c_void_p(buf.data_ptr() if buf is not None else 0), cap,
+                                          ctypes.byref(t))
+        if rc != N.EXACTZ_OK:
+            raise ExactzError(rc, "exactz_server_submit")
+        # the buffers must outlive the request: keep them until its result is taken
+        self._live[t.value] = (f, fhat, g, buf, cap)
+        return int(t.value)
+
+    def _finish(self, ticket: int, res: N.Result, lat: ctypes.c_double, decode: bool) -> dict:
+        f, fhat, g, buf, cap = self._live.pop(ticket)
+        out = _result_dict(res)
+        out["g"] = g
+        out["latency_s"] = float(lat.value)
+        if buf is not None:
+            out["edits_truncated"] = out["n_edits"] > cap
+            out["edits"] = decode_edits(buf, out["n_edits"]) if decode else buf
+        return out
+
+    def poll(self, ticket: int, decode: bool = True) -> Optional[dict]:
+        """The result if ready (else None); decode=False leaves the edit records raw."""
+        res, lat = N.Result(), ctypes.c_double()
+        rc = N.lib().exactz_server_poll(self._h, int(ticket), ctypes.byref(res), ctypes.byref(lat))
+        if rc < 0:
+            raise ExactzError(rc, "exactz_server_poll")
+        return self._finish(ticket, res, lat, decode) if rc == 1 else None
+
+    def wait(self, ticket: int, timeout_s: float = -1.0, decode: bool = True) -> Optional[dict]:
+        res, lat = N.Result(), ctypes.c_double()
+        rc = N.lib().exactz_server_wait(self._h, int(ticket), float(timeout_s), ctypes.byref(res),
+                                        ctypes.byref(lat))
+        if rc < 0:
+            raise ExactzError(rc, "exactz_server_wait")
+        return self._finish(ticket, res, lat, decode) if rc == 1 else None
+
+    def stats(self) -> dict:
+        st = N.ServerInfo()
+        N.lib().exactz_server_stats(self._h, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in N.ServerInfo._fields_ if k != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().exactz_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

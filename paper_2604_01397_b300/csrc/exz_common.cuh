@@ -187,6 +187,7 @@ struct Dev {
     uint32_t *hist;
     uint32_t sort_blocks;
     Tuning tun;
+    const uint32_t *tile_field;  // field slot of each tile when fields are placed freely (else null)
 };
 
 // Fields set up together: tiles [tile0, tile1), compaction blocks
@@ -205,6 +206,7 @@ struct FieldSet {
     const uint32_t *fids;
     uint32_t n;
     uint64_t vblk0, nvblk;
+    uint32_t fid0, fid1;  // the arena blocks belong to fields [fid0, fid1), placed in order
 };
 
 // Tiles [beg, end) with stride `step` of a list of `count` tiles handled by this block.
@@ -226,6 +228,7 @@ __device__ __forceinline__ void tile_range(const Dev &D, unsigned long long coun
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t field_of_tile(const Dev &D, uint32_t tile)
 {
+    if (D.tile_field) return D.tile_field[tile];
     uint32_t lo = 0, hi = D.nfields - 1;
     while (lo < hi) {
         uint32_t mid = (lo + hi + 1) >> 1;

@@ -481,7 +481,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     };
     const uint64_t P = (uint64_t)sort_passes(0, nf);
     const SetupRange R{0, L.total_tiles, 0, L.total_w / WBLOCK, 0, nf, 0, &ws->d_ls->total_cp};
-    const FieldSet FS{ws->fids, nf, 0, L.total_v / VBLOCK};
+    const FieldSet FS{ws->fids, nf, 0, L.total_v / VBLOCK, 0, nf};
     uint64_t launches = 0;
 
     // set-up and the first pass
@@ -588,6 +588,12 @@ int check_device()
 }
 
 }  // namespace
+
+const uint32_t *exz::host_multi_table()
+{
+    std::call_once(g_multi_once, build_multi_table);
+    return g_multi_host;
+}
 
 // ---------------------------------------------------------------- C ABI
 extern "C" {

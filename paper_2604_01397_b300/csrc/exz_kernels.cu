@@ -523,9 +523,9 @@ __global__ void __launch_bounds__(1024) k_scan_inplace_u32(uint32_t *a, uint64_t
 // ------------------------------------------------------------ CP compaction
 constexpr int WPT = WBLOCK / CTA;  // cp-bitmap words per thread
 
-__device__ __forceinline__ uint32_t field_of_word(const Dev &D, uint64_t w)
+__device__ __forceinline__ uint32_t field_of_word(const Dev &D, uint64_t w, uint32_t lo, uint32_t hi)
 {
-    uint32_t lo = 0, hi = D.nfields - 1;
+    hi -= 1;
     while (lo < hi) {
         uint32_t mid = (lo + hi + 1) >> 1;
         if (D.fields[mid].wbase <= w) lo = mid;
@@ -546,11 +546,12 @@ __global__ void __launch_bounds__(CTA) k_cp_count(Dev D, uint64_t wblk0)
     if (threadIdx.x == 0) D.blk[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(CTA) k_cp_write(Dev D, uint64_t wblk0, uint64_t cp0)
+__global__ void __launch_bounds__(CTA) k_cp_write(Dev D, SetupRange R)
 {
+    const uint64_t wblk0 = R.wblk0, cp0 = R.cp0;
     __shared__ uint32_t sw[WARPS];
     const uint64_t blk0 = (wblk0 + blockIdx.x) * WBLOCK;
-    const uint32_t fid = field_of_word(D, blk0);
+    const uint32_t fid = field_of_word(D, blk0, R.fid0, R.fid1);
     const FieldDesc &F = D.fields[fid];
     const uint64_t w0 = blk0 + threadIdx.x * WPT;
     uint32_t words[WPT];
@@ -1044,9 +1045,9 @@ __global__ void k_status(Dev D, FieldSet FS)
 // ------------------------------------------------------------ edit list
 constexpr int EPT = VBLOCK / CTA;  // arena vertices per thread
 
-__device__ __forceinline__ uint32_t field_of_vertex(const Dev &D, uint64_t v)
+__device__ __forceinline__ uint32_t field_of_vertex(const Dev &D, uint64_t v, uint32_t lo, uint32_t hi)
 {
-    uint32_t lo = 0, hi = D.nfields - 1;
+    hi -= 1;
     while (lo < hi) {
         uint32_t mid = (lo + hi + 1) >> 1;
         if (D.fields[mid].vbase <= v) lo = mid;
@@ -1055,13 +1056,14 @@ __device__ __forceinline__ uint32_t field_of_vertex(const Dev &D, uint64_t v)
     return lo;
 }
 
-__global__ void __launch_bounds__(CTA) k_edit_count(Dev D, uint64_t vblk0)
+__global__ void __launch_bounds__(CTA) k_edit_count(Dev D, FieldSet FS)
 {
+    const uint64_t vblk0 = FS.vblk0;
     __shared__ uint32_t sw[WARPS];
     __shared__ uint32_t s_lossless;
     if (threadIdx.x == 0) s_lossless = 0;
     const uint64_t v0 = (vblk0 + blockIdx.x) * VBLOCK;
-    const uint32_t fid = field_of_vertex(D, v0);
+    const uint32_t fid = field_of_vertex(D, v0, FS.fid0, FS.fid1);
     const uint32_t N = D.fields[fid].N;
     const uint64_t b = v0 + threadIdx.x * EPT;
     uint32_t c = 0, l = 0;
@@ -1088,11 +1090,12 @@ __global__ void __launch_bounds__(CTA) k_edit_count(Dev D, uint64_t vblk0)
     }
 }
 
-__global__ void __launch_bounds__(CTA) k_edit_write(Dev D, uint64_t vblk0)
+__global__ void __launch_bounds__(CTA) k_edit_write(Dev D, FieldSet FS)
 {
+    const uint64_t vblk0 = FS.vblk0;
     __shared__ uint32_t sw[WARPS];
     const uint64_t v0 = (vblk0 + blockIdx.x) * VBLOCK;
-    const uint32_t fid = field_of_vertex(D, v0);
+    const uint32_t fid = field_of_vertex(D, v0, FS.fid0, FS.fid1);
     const FieldDesc &F = D.fields[fid];
     if (!F.edits) return;
     const uint32_t N = F.N;
@@ -1155,6 +1158,19 @@ static unsigned grid_for(uint64_t items, int per_block, int cap_mult)
     return (unsigned)g;
 }
 
+__global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+void launch_fill_u32(uint32_t *p, uint32_t v, uint64_t n, cudaStream_t s)
+{
+    if (n) k_fill_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(p, v, n);
+}
+
+int device_sms() { return sms(); }
+
 void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
     k_stencil<SM_SETUP><<<grid_for(R.tile1 - R.tile0, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr, R.tile0, R.tile1,
@@ -1185,7 +1201,7 @@ void launch_cp_compact(const Dev &D, const SetupRange &R, cudaStream_t s)
     const unsigned nb = (unsigned)R.nwblk;
     k_cp_count<<<nb, CTA, 0, s>>>(D, R.wblk0);
     k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, R.nwblk, R.cp_count);
-    k_cp_write<<<nb, CTA, 0, s>>>(D, R.wblk0, R.cp0);
+    k_cp_write<<<nb, CTA, 0, s>>>(D, R);
     k_cp_ncp<<<(R.fid1 - R.fid0 + 255) / 256, 256, 0, s>>>(D, R);
 }
 
@@ -1253,10 +1269,10 @@ void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s)
 void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s)
 {
     const unsigned nb = (unsigned)FS.nvblk;
-    k_edit_count<<<nb, CTA, 0, s>>>(D, FS.vblk0);
+    k_edit_count<<<nb, CTA, 0, s>>>(D, FS);
     if (write) {
         k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, FS.nvblk, nullptr);
-        k_edit_write<<<nb, CTA, 0, s>>>(D, FS.vblk0);
+        k_edit_write<<<nb, CTA, 0, s>>>(D, FS);
     }
 }
 

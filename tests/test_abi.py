@@ -72,3 +72,31 @@ def test_oracle_and_library_share_no_code():
     for fn in ("api.py", "_native.py", "__init__.py"):
         src = open(os.path.join(ROOT, "paper_2604_01397_b300", fn)).read()
         assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    # compile a C program against include/exactz.h and compare every struct's
+    # size and field offsets with the ctypes mirror used by the binding
+    import subprocess
+
+    import paper_2604_01397_b300._native as N
+
+    structs = {"exactz_dims": N.Dims, "exactz_opts": N.Opts, "exactz_edit": N.Edit, "exactz_result": N.Result,
+               "exactz_stats": N.Stats, "exactz_tuning": N.Tuning, "exactz_server_config": N.ServerConfig,
+               "exactz_server_info": N.ServerInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "exactz.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
