@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bumps512")
     p.add_argument("--size", type=int, default=0, help="override the cube side (profiling runs)")
+    p.add_argument("--rel", type=float, default=0.0, help="override xi / range of the workload")
     p.add_argument("--mode", default="graph", choices=["graph", "frontier", "plain"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -67,7 +68,7 @@ def parse():
 
 
 # ---------------------------------------------------------------- workloads
-def workload_spec(name: str, size: int = 0):
+def workload_spec(name: str, size: int = 0, rel: float = 0.0):
     from synth.fields import CONFIGS
 
     if name == "bumps512":
@@ -84,6 +85,9 @@ def workload_spec(name: str, size: int = 0):
         if c["kind"] == "bumps":  # same bump density
             c["n_bumps"] = max(1, round(c["n_bumps"] * size ** 3 / vol))
         c["name"] = f"{name}@{size}"
+    if rel:
+        c["rel"] = rel
+        c["name"] = f"{c['name']}/rel{rel:g}"
     return c
 
 
@@ -214,7 +218,7 @@ def run_reference(a):
         return
     import torch
 
-    c = workload_spec(a.workload, a.size)
+    c = workload_spec(a.workload, a.size, a.rel)
     f, fh, xi = make_fields(c, "cpu")
     f, fh = f.numpy(), fh.numpy()
     budget = max(2.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
@@ -256,7 +260,7 @@ def run_ours(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
-    c = workload_spec(a.workload, a.size)
+    c = workload_spec(a.workload, a.size, a.rel)
     f, fh, xi = make_fields(c, dev)
     torch.cuda.synchronize()
     n = f.numel()

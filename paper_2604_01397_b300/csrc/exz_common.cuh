@@ -133,8 +133,6 @@ struct FieldState {
 };
 
 struct LoopState {
-    unsigned long long apply_count;  // tiles holding requested vertices (this pass)
-    unsigned long long tile_count[2];
     unsigned long long pair_count[2];
     unsigned long long total_cp;
     unsigned long long sum_requests;  // requests applied or skipped, over all passes
@@ -147,8 +145,9 @@ struct LoopState {
 };
 
 // Launch schedule of the per-pass kernels (chosen by the autotuner): blocks per
-// SM of the tile-check, tile-apply and CP-pair kernels, and whether a block
-// takes a contiguous chunk of the tile list (1) or every gridDim-th tile (0).
+// SM of the tile-check, tile-apply and CP-pair kernels, and whether a block (or
+// warp) takes a contiguous chunk of the tile bitmap's words (1) or every
+// grid-th word (0).
 struct Tuning {
     uint32_t stencil_bps = 16, apply_bps = 16, pairs_bps = 8, chunked = 0;
 };
@@ -169,10 +168,8 @@ struct Dev {
     uint32_t *dirty;     // vertices whose closed star changed last pass (row words)
     float *gs;           // g of the critical points, in f's sorted order
     uint32_t *pairbits;  // CP pairs already queued for the next pass
-    uint32_t *apply_list;
-    uint32_t *apply_bits;
-    uint32_t *tile_list[2];
-    uint32_t *tile_bits;
+    uint32_t *apply_bits;  // tiles holding requested vertices (read and cleared by the apply kernel)
+    uint32_t *tile_bits;   // tiles to check next pass (read and cleared by the check kernel)
     uint32_t *pin_tile_bits;
     uint32_t *pair_list[2];
     uint32_t *cp_key[2];
@@ -225,6 +222,26 @@ __device__ __forceinline__ void tile_range(const Dev &D, unsigned long long coun
     }
 }
 
+// Words [beg, end) with stride `step` of a tile bitmap handled by worker `w` of
+// `nworkers` (a block or a warp).
+__device__ __forceinline__ void word_range(const Dev &D, uint32_t nwords, uint32_t w, uint32_t nworkers,
+                                           uint32_t &beg, uint32_t &end, uint32_t &step)
+{
+    if (D.tun.chunked) {
+        const uint32_t c = (nwords + nworkers - 1) / nworkers;
+        beg = min(nwords, w * c);
+        end = min(nwords, beg + c);
+        step = 1;
+    } else {
+        beg = w;
+        end = nwords;
+        step = nworkers;
+    }
+}
+
+// Number of words of the tile bitmaps.
+__device__ __forceinline__ uint32_t tile_words(const Dev &D) { return (D.total_tiles + 31u) / 32u; }
+
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t field_of_tile(const Dev &D, uint32_t tile)
 {
@@ -274,6 +291,26 @@ __device__ __forceinline__ void mark_tile(uint32_t *bits, uint32_t *list, unsign
         unsigned long long p = atomicAdd(count, 1ull);
         list[p] = tile;
     }
+}
+
+// Warp-wide tile marking: each lane with `want` marks `tile` in the bitmap, and
+// the lanes that set a bit first append their tiles to the list with a single
+// counter update for the whole warp.  All 32 lanes must call it.
+__device__ __forceinline__ void warp_mark_tiles(bool want, uint32_t tile, uint32_t *bits, uint32_t *list,
+                                                unsigned long long *count)
+{
+    bool fresh = false;
+    if (want) {
+        const uint32_t bit = 1u << (tile & 31);
+        if (!(__ldcg(&bits[tile >> 5]) & bit)) fresh = !(atomicOr(&bits[tile >> 5], bit) & bit);
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, fresh);
+    if (!b) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(b) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (fresh) list[base + __popc(b & ((1u << lane) - 1u))] = tile;
 }
 
 }  // namespace exz

@@ -137,9 +137,9 @@ struct exactz_workspace {
     LoopState *d_ls = nullptr;
     uint32_t *d_multi = nullptr;
     uint32_t *desc = nullptr, *cp_rank = nullptr, *cpwords = nullptr, *reqw = nullptr;
-    uint32_t *dirty = nullptr, *pairbits = nullptr, *apply_list = nullptr, *apply_bits = nullptr;
+    uint32_t *dirty = nullptr, *pairbits = nullptr, *apply_bits = nullptr;
     float *gs = nullptr;
-    uint32_t *tile_list[2] = {nullptr, nullptr}, *tile_bits = nullptr;
+    uint32_t *tile_bits = nullptr;
     uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
     uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_arena = nullptr;
     uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
@@ -245,10 +245,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->dirty, W);
     AL(ws->gs, C);
     AL(ws->pairbits, C / 32 + 1);
-    AL(ws->apply_list, T);
     AL(ws->apply_bits, T / 32 + 1);
-    AL(ws->tile_list[0], T);
-    AL(ws->tile_list[1], T);
     AL(ws->tile_bits, T / 32 + 1);
     AL(ws->pin_tile_arena, T);
     AL(ws->pin_tile_bits, T / 32 + 1);
@@ -298,10 +295,7 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.dirty = ws->dirty;
     D.gs = ws->gs;
     D.pairbits = ws->pairbits;
-    D.apply_list = ws->apply_list;
     D.apply_bits = ws->apply_bits;
-    D.tile_list[0] = ws->tile_list[0];
-    D.tile_list[1] = ws->tile_list[1];
     D.tile_bits = ws->tile_bits;
     D.pin_tile_bits = ws->pin_tile_bits;
     D.pair_list[0] = ws->pair_list[0];
@@ -925,9 +919,8 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
     bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
               c.take(ws->d_ls, 1) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
               c.take(ws->cpwords, W) && c.take(ws->reqw, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
-              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_list, T) &&
-              c.take(ws->apply_bits, T / 32 + 1) &&
-              c.take(ws->tile_list[0], T) && c.take(ws->tile_list[1], T) && c.take(ws->tile_bits, T / 32 + 1) &&
+              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_bits, T / 32 + 1) &&
+              c.take(ws->tile_bits, T / 32 + 1) &&
               c.take(ws->pin_tile_arena, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
               c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
               c.take(ws->pin_pair_arena, 2 * C) && c.take(ws->fids, L.nfields) && c.take(ws->cp_key[0], C) &&

@@ -34,7 +34,10 @@ enum { SM_SETUP = 0, SM_CHECK_ALL = 1, SM_CHECK_LIST = 2, SM_PINNED = 3, SM_CLAS
 // Block-size assumptions of the kernels below.
 static_assert(TX == 32, "one row word (and one warp) per tile row");
 static_assert(CTA % 32 == 0 && ROWS <= 32, "tile-row prefix sums run in one warp");
-static_assert(CTA >= 7 * ROWS && CTA >= 27, "dirty dilation: one thread per (row, star row); 27 neighbour tiles");
+// The tile-stencil kernel runs smaller blocks than the others, so that more
+// tiles are in flight per SM (its time goes mostly to memory latency per tile).
+constexpr int SCTA = 128, STWARPS = SCTA / 32;
+static_assert(SCTA % 32 == 0 && SCTA >= 32 && SCTA >= ROWS, "stencil blocks: whole warps, one thread per tile row");
 static_assert(WBLOCK % CTA == 0 && VBLOCK % (4 * CTA) == 0, "compaction and edit-list blocks");
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
@@ -65,15 +68,16 @@ __device__ __forceinline__ void tile_targets_add(TileTargets &T, int lx, int ly,
 
 __device__ __forceinline__ int nb_index(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
-// Queue the tiles of a 27-bit neighbourhood mask around `tile`; thread j of
-// the block handles neighbour j, so the marks go out in parallel.
-__device__ __forceinline__ void mark_nb_tiles(uint32_t nb, uint32_t tile, uint32_t tnx, uint32_t tny, uint32_t *bits,
-                                              uint32_t *list, unsigned long long *count)
+// Mark the tiles of a 27-bit neighbourhood mask around `tile` in a tile
+// bitmap; lane j of the calling warp handles neighbour j.
+__device__ __forceinline__ void warp_mark_nb_tiles(uint32_t nb, uint32_t tile, uint32_t tnx, uint32_t tny,
+                                                   uint32_t *bits)
 {
-    const int j = threadIdx.x;
+    const int j = threadIdx.x & 31;
     if (j < 27 && ((nb >> j) & 1u)) {
         const int ox = j % 3 - 1, oy = (j / 3) % 3 - 1, oz = j / 9 - 1;
-        mark_tile(bits, list, count, (uint32_t)((int64_t)tile + ox + (int64_t)tnx * (oy + (int64_t)tny * oz)));
+        const uint32_t t = (uint32_t)((int64_t)tile + ox + (int64_t)tnx * (oy + (int64_t)tny * oz));
+        atomicOr(&bits[t >> 5], 1u << (t & 31));
     }
 }
 
@@ -83,7 +87,7 @@ template <bool PINNED>
 __device__ __forceinline__ void tile_targets_commit(TileTargets &T, const Dev &D, const FieldDesc &F, uint32_t tile,
                                                     uint32_t tx, int y0, int z0, uint32_t tnx, uint32_t tny)
 {
-    for (int row = threadIdx.x; row < HY * HZ; row += CTA) {
+    for (int row = threadIdx.x; row < HY * HZ; row += blockDim.x) {
         unsigned long long m = T.row[row];
         if (!m) continue;
         T.row[row] = 0;
@@ -121,13 +125,14 @@ __device__ __forceinline__ void tile_targets_commit(TileTargets &T, const Dev &D
     }
     __syncthreads();
     const uint32_t nb = T.nb;
-    mark_nb_tiles(nb, tile, tnx, tny, D.apply_bits, D.apply_list, &D.ls->apply_count);
+    if (threadIdx.x < 32) warp_mark_nb_tiles(nb, tile, tnx, tny, D.apply_bits);
     __syncthreads();
     if (threadIdx.x == 0) T.nb = 0;
 }
 
-// Request vertex t of field F from outside a tile (the CP-pair check).
-__device__ __forceinline__ void request_vertex(const Dev &D, const FieldDesc &F, uint64_t t)
+// Request vertex t of field F from outside a tile (the CP-pair check): set its
+// request bit and return its tile, which the caller queues (warp_mark_tiles).
+__device__ __forceinline__ uint32_t request_vertex(const Dev &D, const FieldDesc &F, uint64_t t)
 {
     uint32_t x, row;
     if (F.n < (1ull << 32)) {
@@ -139,8 +144,7 @@ __device__ __forceinline__ void request_vertex(const Dev &D, const FieldDesc &F,
     }
     const uint32_t z = fdiv(row, F.div_ny), y = row - z * F.ny;
     atomicOr(&D.reqw[F.wbase + (uint64_t)row * F.tnx + (x >> 5)], 1u << (x & 31));
-    const uint32_t tile = (uint32_t)(F.tbase + (x >> 5) + (uint64_t)F.tnx * (y / TY + (uint64_t)F.tny * (z / TZ)));
-    mark_tile(D.apply_bits, D.apply_list, &D.ls->apply_count, tile);
+    return (uint32_t)(F.tbase + (x >> 5) + (uint64_t)F.tnx * (y / TY + (uint64_t)F.tny * (z / TZ)));
 }
 
 // ------------------------------------------------------------ stencil core
@@ -220,7 +224,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
 // Tiles come from [t0, t1) (SETUP, CHECK_ALL, CLASSIFY), the current frontier
 // list (CHECK_LIST), or the pinned-tile lists of fields fids[0..nf) (PINNED).
 template <int MODE>
-__global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
+__global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
                                                     uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
     __shared__ float sa[HALO_N];
@@ -231,31 +235,14 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
     __shared__ uint32_t s_rw[ROWS];       // dirty row words of the tile (CHECK_LIST)
     __shared__ uint32_t s_pre[ROWS + 1];  // their prefix popcounts
 
-    for (int j = threadIdx.x; j < 512; j += CTA) smulti[j] = D.multi[j];
-    for (int w = threadIdx.x; w < HY * HZ; w += CTA) tt.row[w] = 0;
+    for (int j = threadIdx.x; j < 512; j += SCTA) smulti[j] = D.multi[j];
+    for (int w = threadIdx.x; w < HY * HZ; w += SCTA) tt.row[w] = 0;
     if (threadIdx.x == 0) {
         tt.nb = 0;
         s_err = 0;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t nouter = MODE == SM_PINNED ? nf : 1u;
-    for (uint32_t fi = 0; fi < nouter; fi++) {
-    unsigned long long count;
-    const uint32_t *list = nullptr;
-    if (MODE == SM_SETUP || MODE == SM_CHECK_ALL || MODE == SM_CLASSIFY) {
-        count = t1 - t0;
-    } else if (MODE == SM_CHECK_LIST) {
-        uint32_t c = D.ls->cur;
-        count = D.ls->tile_count[c];
-        list = D.tile_list[c];
-    } else {
-        count = D.fst[fids[fi]].pin_tile_count;
-        list = D.fields[fids[fi]].pin_tiles;
-    }
-    unsigned long long it0, it1, its;
-    tile_range(D, count, it0, it1, its);
-    for (unsigned long long it = it0; it < it1; it += its) {
-        const uint32_t tile = list ? list[it] : t0 + (uint32_t)it;
+    auto do_tile = [&](const uint32_t tile) {
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
@@ -266,8 +253,6 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
         const uint32_t tx = lt - rest * tnx;
         const uint32_t tz = rest / tny, ty = rest - tz * tny;
         const int x0 = (int)(tx * TX), y0 = (int)(ty * TY), z0 = (int)(tz * TZ);
-        if (MODE == SM_CHECK_LIST && threadIdx.x == 0)
-            atomicAnd(&D.tile_bits[tile >> 5], ~(1u << (tile & 31)));
         if (MODE == SM_CHECK_LIST && threadIdx.x < ROWS) {
             // take (and clear) the dirty bits of this tile's rows
             const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
@@ -284,7 +269,7 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
         const float *A = (MODE == SM_SETUP || MODE == SM_CLASSIFY) ? F.f : F.g;
         const float *B = F.fhat;
         const float qnan = __int_as_float(0x7fc00000);
-        for (int row = warp; row < HY * HZ; row += WARPS) {
+        for (int row = warp; row < HY * HZ; row += STWARPS) {
             const int hz = row / HY, hy = row - hz * HY;
             const int Y = y0 - 1 + hy, Z = z0 - 1 + hz;
             const bool rin = Y >= 0 && Z >= 0 && Y < (int)ny && Z < (int)nz;
@@ -320,7 +305,7 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
         // vertices of this tile to visit: all rows (one warp per row) or the dirty list
         const int nvisit = MODE == SM_CHECK_LIST ? (int)s_pre[ROWS] : ROWS * TX;
         for (int base = (MODE == SM_CHECK_LIST ? 0 : warp * TX); base < nvisit;
-             base += (MODE == SM_CHECK_LIST ? CTA : WARPS * TX)) {
+             base += (MODE == SM_CHECK_LIST ? SCTA : STWARPS * TX)) {
             int lx, ly, lz;
             bool sel = true;
             if (MODE == SM_CHECK_LIST) {
@@ -393,7 +378,46 @@ __global__ void __launch_bounds__(CTA, 8) k_stencil(Dev D, uint32_t *desc_out, u
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
         }
-    }
+    };
+
+    if (MODE == SM_CHECK_LIST) {
+        // the tiles of the set bits of tile_bits, a word at a time (read and cleared by thread 0)
+        __shared__ uint32_t s_word[2];
+        unsigned long long nt = 0;
+        uint32_t wb, we, wst;
+        word_range(D, tile_words(D), blockIdx.x, gridDim.x, wb, we, wst);
+        uint32_t par = 0;
+        for (uint32_t w = wb; w < we; w += wst, par ^= 1u) {
+            if (threadIdx.x == 0) {
+                const uint32_t v = D.tile_bits[w];
+                if (v) D.tile_bits[w] = 0;
+                s_word[par] = v;
+            }
+            __syncthreads();
+            uint32_t word = s_word[par];  // s_word[par] is rewritten two words later, after another barrier
+            nt += __popc(word);
+            while (word) {
+                const uint32_t tile = w * 32u + (uint32_t)(__ffs(word) - 1);
+                word &= word - 1;
+                do_tile(tile);
+            }
+        }
+        if (threadIdx.x == 0 && nt) atomicAdd(&D.ls->sum_tiles, nt);
+    } else {
+        const uint32_t nouter = MODE == SM_PINNED ? nf : 1u;
+        for (uint32_t fi = 0; fi < nouter; fi++) {
+            unsigned long long count;
+            const uint32_t *list = nullptr;
+            if (MODE == SM_PINNED) {
+                count = D.fst[fids[fi]].pin_tile_count;
+                list = D.fields[fids[fi]].pin_tiles;
+            } else {
+                count = t1 - t0;
+            }
+            unsigned long long it0, it1, its;
+            tile_range(D, count, it0, it1, its);
+            for (unsigned long long it = it0; it < it1; it += its) do_tile(list ? list[it] : t0 + (uint32_t)it);
+        }
     }
 }
 
@@ -716,26 +740,36 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
         count = D.fst[fids[fi]].pin_pair_count;
         list = D.fields[fids[fi]].pin_pairs;
     }
+    // warp-uniform trip counts: the request's tile is queued by the whole warp
     const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
-    for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
-        const unsigned long long q = list ? (unsigned long long)list[j] : cp0 + j;
-        if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
-        const float ga = D.gs[q], gb = D.gs[q + 1];
-        bool viol = gb < ga;
-        unsigned long long a = 0;
-        if (PM == PM_ALL || gb == ga) {
-            a = D.o[q];
-            const unsigned long long b = D.o[q + 1];
-            if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
-            else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
-        } else if (viol) {
-            a = D.o[q];
+    for (unsigned long long j0 = (unsigned long long)blockIdx.x * CTA + (threadIdx.x & ~31u); j0 < count;
+         j0 += stride) {
+        const unsigned long long j = j0 + (threadIdx.x & 31);
+        bool viol = false;
+        uint32_t tile = 0;
+        if (j < count) {
+            const unsigned long long q = list ? (unsigned long long)list[j] : cp0 + j;
+            if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
+            const float ga = D.gs[q], gb = D.gs[q + 1];
+            viol = gb < ga;
+            unsigned long long a = 0;
+            if (PM == PM_ALL || gb == ga) {
+                a = D.o[q];
+                const unsigned long long b = D.o[q + 1];
+                if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
+                else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
+            } else if (viol) {
+                a = D.o[q];
+            }
+            if (viol) {
+                const FieldDesc &F = D.fields[a >> LOCAL_BITS];
+                const uint64_t t = a & LOCAL_MASK;
+                if (PM != PM_PINNED || (D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) tile = request_vertex(D, F, t);
+                else viol = false;
+            }
         }
-        if (viol) {
-            const FieldDesc &F = D.fields[a >> LOCAL_BITS];
-            const uint64_t t = a & LOCAL_MASK;
-            if (PM != PM_PINNED || (D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) request_vertex(D, F, t);
-        }
+        if (viol && !(__ldcg(&D.apply_bits[tile >> 5]) & (1u << (tile & 31))))
+            atomicOr(&D.apply_bits[tile >> 5], 1u << (tile & 31));
     }
     }
 }
@@ -759,15 +793,15 @@ __device__ __forceinline__ unsigned long long warp_reserve(uint32_t c, unsigned 
     return base + (x - c);
 }
 
-// Queue the tiles holding the closed star of vertex (x, y, z) of tile `own`:
-// the star's negative offsets are the non-zero vectors of {0,-1}^3 and its
-// positive ones those of {0,1}^3, so the other tiles it reaches are, on each
-// side, the non-zero combinations of the tile faces the vertex lies on.
-__device__ __forceinline__ void mark_star_tiles(uint32_t own, uint32_t x, uint32_t y, uint32_t z, uint32_t nx,
+// Queue the tiles other than `own` holding the closed star of vertex (x, y, z)
+// of tile `own`: the star's negative offsets are the non-zero vectors of
+// {0,-1}^3 and its positive ones those of {0,1}^3, so the other tiles it
+// reaches are, on each side, the non-zero combinations of the tile faces the
+// vertex lies on.
+__device__ __forceinline__ void mark_face_tiles(uint32_t own, uint32_t x, uint32_t y, uint32_t z, uint32_t nx,
                                                 uint32_t ny, uint32_t nz, uint32_t tnx, uint32_t tny, uint32_t *bits,
                                                 uint32_t *list, unsigned long long *count)
 {
-    mark_tile(bits, list, count, own);
     const uint32_t lo = ((x % TX) == 0 && x > 0 ? 1u : 0u) | ((y % TY) == 0 && y > 0 ? 2u : 0u) |
                         ((z % TZ) == 0 && z > 0 ? 4u : 0u);
     const uint32_t hi = ((x % TX) == TX - 1 && x + 1 < nx ? 1u : 0u) | ((y % TY) == TY - 1 && y + 1 < ny ? 2u : 0u) |
@@ -783,32 +817,46 @@ __device__ __forceinline__ void mark_star_tiles(uint32_t own, uint32_t x, uint32
 
 enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
 
-// One tile of the apply list per block iteration.  The tile's request words
-// are read (and cleared), the requested vertices compacted into a dense list
-// that all threads work through, and the changed vertices collected as row
-// bits in shared memory.
+// One tile holding requested vertices per warp iteration (warps work
+// independently): a warp takes a word of apply_bits (and clears it) and works
+// through the tiles of its set bits.  The tile's 16 request words are read (and
+// cleared) by lanes 0-15, the
+// requested vertices are numbered by a warp prefix sum and worked through 32
+// at a time, and the changed vertices are collected as row bits in the warp's
+// shared words.
 //   PLAIN / FRONTIER: apply the bounded edit (Sec. 3.3) to each requested,
 //     unpinned vertex (at the iteration cap: count it instead), keep the CP
 //     values in gs, queue CP pairs and pinned neighbourhoods; FRONTIER also
-//     sets the next pass's dirty bits -- the closed stars of the changed
-//     vertices, by shifting each changed-row word into the seven star rows
-//     (0,0), -(1,0), -(0,1), -(1,1), +(1,0), +(0,1), +(1,1) (x-1..x+1 in the
-//     centre row, x-1..x below, x..x+1 above) -- and queues their tiles.
+//     sets the next pass's dirty bits (the closed stars of the changed
+//     vertices) and queues their tiles.
 //   COUNT: add the requested (pinned) vertices to the field's residual.
 template <int AM>
-__global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
+__global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
 {
-    __shared__ uint32_t s_rw[ROWS], s_cw[ROWS], s_pre[ROWS + 1];
-    __shared__ uint32_t s_nb, s_cap;
-    const unsigned long long count = D.ls->apply_count;
-    const uint32_t nxt = D.ls->cur ^ 1u;
+    __shared__ uint32_t s_cw_all[WARPS][ROWS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *s_cw = s_cw_all[warp];
+    const uint32_t nxt = D.ls->cur ^ 1u;
     unsigned long long nreq = 0;
-    unsigned long long it0, it1, its;
-    tile_range(D, count, it0, it1, its);
-    for (unsigned long long it = it0; it < it1; it += its) {
-        const uint32_t tile = D.apply_list[it];
-        const uint32_t fid = field_of_tile(D, tile);
+    uint32_t wb, we, wst;
+    word_range(D, tile_words(D), blockIdx.x * WARPS + warp, gridDim.x * WARPS, wb, we, wst);
+    for (uint32_t w = wb; w < we; w += wst) {
+    uint32_t word = D.apply_bits[w];
+    if (!word) continue;
+    __syncwarp();
+    if (lane == 0) D.apply_bits[w] = 0;
+    // the next tile's field is loaded one tile ahead
+    uint32_t tile_n = w * 32u + (uint32_t)(__ffs(word) - 1);
+    uint32_t fid_n = field_of_tile(D, tile_n);
+    word &= word - 1;
+    for (bool more = true; more;) {
+        const uint32_t tile = tile_n, fid = fid_n;
+        more = word != 0;
+        if (more) {
+            tile_n = w * 32u + (uint32_t)(__ffs(word) - 1);
+            word &= word - 1;
+            fid_n = field_of_tile(D, tile_n);
+        }
         const FieldDesc &F = D.fields[fid];
         FieldState *S = &D.fst[fid];
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny, N = F.N;
@@ -816,68 +864,67 @@ __global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
         const uint32_t rest = lt / tnx, tx = lt - rest * tnx, tz = rest / tny, ty = rest - tz * tny;
         const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
         const uint64_t vbase = F.vbase, wbase = F.wbase;
-        if (threadIdx.x < ROWS) {
-            const uint32_t y = y0 + threadIdx.x % TY, z = z0 + threadIdx.x / TY;
-            uint32_t W = 0;
+        uint32_t W = 0;  // lane r < ROWS: request word of tile row r
+        if (lane < ROWS) {
+            const uint32_t y = y0 + lane % TY, z = z0 + lane / TY;
             if (y < ny && z < nz) {
                 uint32_t *wp = D.reqw + wbase + ((uint64_t)z * ny + y) * tnx + tx;
                 W = *wp;
                 if (W) *wp = 0;
             }
-            s_rw[threadIdx.x] = W;
-            s_cw[threadIdx.x] = 0;
+            s_cw[lane] = 0;
         }
-        if (threadIdx.x == 0) {
-            atomicAnd(&D.apply_bits[tile >> 5], ~(1u << (tile & 31)));
-            s_nb = 0;
-            s_cap = 0;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t c = lane < ROWS ? __popc(s_rw[lane]) : 0u;
+        const uint32_t c = __popc(W);
+        uint32_t incl = c;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
-                if (lane >= o) c += y;
-            }
-            if (lane < ROWS) s_pre[lane + 1] = c;
-            if (lane == 0) s_pre[0] = 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        __syncthreads();
-        const int nvisit = (int)s_pre[ROWS];
-        if (threadIdx.x == 0) nreq += nvisit;
+        const uint32_t excl = incl - c;  // requested vertices in the rows before this lane's row
+        const int nvisit = (int)__shfl_sync(0xffffffffu, incl, ROWS - 1);
+        nreq += (unsigned long long)nvisit;
         if (AM == AM_COUNT) {
-            if (threadIdx.x == 0 && nvisit) atomicAdd(&S->pinned_res, (unsigned long long)nvisit);
-            __syncthreads();
+            if (lane == 0 && nvisit) atomicAdd(&S->pinned_res, (unsigned long long)nvisit);
             continue;
         }
+        __syncwarp();
         const bool err = S->err != 0, capped = S->iterations >= F.max_iters;
-        for (int base = 0; base < nvisit; base += CTA) {
-            const int k = base + threadIdx.x;
+        uint32_t ncap = 0;
+        for (int base = 0; base < nvisit; base += 32) {
+            const int k = base + lane;
             const bool sel = k < nvisit && !err;
-            bool applied = false, pinned = false, has_lo = false, has_hi = false;
+            int row = 0;  // the last row whose first request number is <= k
+#pragma unroll
+            for (int step = 8; step >= 1; step >>= 1) {
+                const uint32_t pe = __shfl_sync(0xffffffffu, excl, row + step);
+                if ((int)pe <= k) row += step;
+            }
+            const uint32_t rword = __shfl_sync(0xffffffffu, W, row);
+            const uint32_t rpre = __shfl_sync(0xffffffffu, excl, row);
+            bool pinned = false, has_lo = false, has_hi = false;
             unsigned long long q = 0;
             uint32_t x = 0, y = 0, z = 0;
             if (sel) {
-                int row = 0;
-#pragma unroll
-                for (int step = 8; step >= 1; step >>= 1)
-                    if (row + step <= ROWS - 1 && (int)s_pre[row + step] <= k) row += step;
-                const int lx = nth_set_bit(s_rw[row], k - (int)s_pre[row]);
+                const int lx = nth_set_bit(rword, k - (int)rpre);
                 x = x0 + lx;
                 y = y0 + row % TY;
                 z = z0 + row / TY;
                 const uint64_t t = ((uint64_t)z * ny + y) * nx + x;
+                // all loads of the vertex at once (f, g and the CP rank are not
+                // needed for a pinned target or a regular vertex)
                 const uint32_t d = D.desc[vbase + t];
+                const float fv = F.f[t], g0 = F.g[t];
+                const uint32_t rk = D.cp_rank[vbase + t];
                 uint32_t kk = d >> D_K_SHIFT;
                 if (kk <= N) {  // a pinned target stays as it is
                     if (capped) {
-                        atomicAdd(&s_cap, 1u);
+                        ncap++;
                     } else {
-                        const float fl = __fsub_rn(F.f[t], F.xi);
+                        const float fl = __fsub_rn(fv, F.xi);
                         float gv;
                         if (kk < N) {
-                            const float tt = __fsub_rn(F.g[t], F.delta);
+                            const float tt = __fsub_rn(g0, F.delta);
                             if (tt < fl) {
                                 gv = fl;
                                 kk = N + 1;
@@ -891,11 +938,10 @@ __global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
                         }
                         F.g[t] = gv;
                         D.desc[vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
-                        applied = true;
                         pinned = kk == N + 1;
                         atomicOr(&s_cw[row], 1u << lx);
                         if (d & D_CP) {  // value in sorted order; pairs inside the field
-                            const unsigned long long r = D.cp_rank[vbase + t];
+                            const unsigned long long r = rk;
                             q = S->cp_base + r;
                             D.gs[q] = gv;
                             if (AM == AM_FRONTIER || pinned) {
@@ -927,54 +973,75 @@ __global__ void __launch_bounds__(CTA, 8) k_apply_tiles(Dev D)
                 if (pinned && has_hi) F.pin_pairs[p] = (uint32_t)q;
                 if (pinned && has_lo) F.pin_pairs[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
             }
-            if (pinned)  // the residual check revisits the closed stars of pinned vertices
-                mark_star_tiles(tile, x, y, z, nx, ny, nz, tnx, tny, D.pin_tile_bits, F.pin_tiles,
-                                &S->pin_tile_count);
-            (void)applied;
+            // the residual check revisits the closed stars of pinned vertices:
+            // this tile (queued once per warp) and the tiles across its faces
+            const bool any_pinned = __any_sync(0xffffffffu, pinned);
+            warp_mark_tiles(lane == 0 && any_pinned, tile, D.pin_tile_bits, F.pin_tiles, &S->pin_tile_count);
+            if (pinned) mark_face_tiles(tile, x, y, z, nx, ny, nz, tnx, tny, D.pin_tile_bits, F.pin_tiles,
+                                        &S->pin_tile_count);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (s_cap) atomicAdd(&S->capped, (unsigned long long)s_cap);
-            bool any = false;
-            for (int r = 0; r < ROWS; r++) any |= s_cw[r] != 0;
+        __syncwarp();
+        const uint32_t cw = lane < ROWS ? s_cw[lane] : 0u;
+        const bool any = __any_sync(0xffffffffu, cw != 0);
+        ncap = __reduce_add_sync(0xffffffffu, ncap);
+        if (lane == 0) {
+            if (ncap) atomicAdd(&S->capped, (unsigned long long)ncap);
             if (any && !S->had_req) S->had_req = 1;
         }
-        if (AM == AM_FRONTIER) {
-            // dirty bits: thread (row, star row k) for row < ROWS, k < 7
-            const int row = threadIdx.x / 7, k = threadIdx.x - row * 7;
-            if (row < ROWS && s_cw[row]) {
-                const uint32_t C = s_cw[row];
-                const uint32_t y = y0 + row % TY, z = z0 + row / TY;
-                const int dy = (k == 1 || k == 3) ? -1 : ((k == 4 || k == 6) ? 1 : 0);
-                const int dz = (k == 2 || k == 3) ? -1 : ((k == 5 || k == 6) ? 1 : 0);
-                const int Y = (int)y + dy, Z = (int)z + dz;
-                if (Y >= 0 && Z >= 0 && Y < (int)ny && Z < (int)nz) {
-                    const bool lo = k <= 3, hi = k == 0 || k >= 4;
-                    uint32_t m = C;
-                    if (lo) m |= C >> 1;
-                    if (hi) m |= C << 1;
-                    const uint64_t wi = wbase + ((uint64_t)Z * ny + (uint64_t)Y) * tnx + tx;
-                    const int oy = Y < (int)y0 ? -1 : (Y >= (int)(y0 + TY) ? 1 : 0);
-                    const int oz = Z < (int)z0 ? -1 : (Z >= (int)(z0 + TZ) ? 1 : 0);
-                    uint32_t nb = 1u << nb_index(0, oy, oz);
+        if (AM == AM_FRONTIER && any) {
+            // dirty bits of the next pass: the closed stars of the changed
+            // vertices.  Lane j gathers halo row j (of the 6 x 6 rows around the
+            // tile) from the changed words of the tile rows whose star reaches
+            // it: star row (dy, dz) of a changed word C covers C | C >> 1 for
+            // the rows (0,0), (-1,0), (0,-1), (-1,-1) and C | C << 1 for (0,0),
+            // (1,0), (0,1), (1,1); bits shifted out of the word go to the word
+            // of the tile column on that side.  One atomic per word touched.
+            uint32_t nb = 0;
+            for (int j = lane; j < HY * HZ; j += 32) {
+                const int hz = j / HY, hy = j - hz * HY;
+                uint32_t m = 0, elo = 0, ehi = 0;
+#pragma unroll
+                for (int kk = 0; kk < 7; kk++) {
+                    const int dy = (kk == 1 || kk == 3) ? -1 : ((kk == 4 || kk == 6) ? 1 : 0);
+                    const int dz = (kk == 2 || kk == 3) ? -1 : ((kk == 5 || kk == 6) ? 1 : 0);
+                    const int ly = hy - 1 - dy, lz = hz - 1 - dz;
+                    if (ly < 0 || ly >= TY || lz < 0 || lz >= TZ) continue;
+                    const uint32_t C = s_cw[lz * TY + ly];
+                    m |= C;
+                    if (kk <= 3) {
+                        m |= C >> 1;
+                        elo |= C & 1u;
+                    }
+                    if (kk == 0 || kk >= 4) {
+                        m |= C << 1;
+                        ehi |= C >> 31;
+                    }
+                }
+                const int Y = (int)y0 - 1 + hy, Z = (int)z0 - 1 + hz;
+                if (!(m | elo | ehi) || Y < 0 || Z < 0 || Y >= (int)ny || Z >= (int)nz) continue;
+                const uint64_t wi = wbase + ((uint64_t)Z * ny + (uint64_t)Y) * tnx + tx;
+                const int oy = hy == 0 ? -1 : (hy == TY + 1 ? 1 : 0);
+                const int oz = hz == 0 ? -1 : (hz == TZ + 1 ? 1 : 0);
+                if (m) {
                     atomicOr(&D.dirty[wi], m);
-                    if (lo && (C & 1u) && tx > 0) {
-                        atomicOr(&D.dirty[wi - 1], 0x80000000u);
-                        nb |= 1u << nb_index(-1, oy, oz);
-                    }
-                    if (hi && (C >> 31) && tx + 1 < tnx) {
-                        atomicOr(&D.dirty[wi + 1], 1u);
-                        nb |= 1u << nb_index(1, oy, oz);
-                    }
-                    atomicOr(&s_nb, nb);
+                    nb |= 1u << nb_index(0, oy, oz);
+                }
+                if (elo && tx > 0) {
+                    atomicOr(&D.dirty[wi - 1], 0x80000000u);
+                    nb |= 1u << nb_index(-1, oy, oz);
+                }
+                if (ehi && tx + 1 < tnx) {
+                    atomicOr(&D.dirty[wi + 1], 1u);
+                    nb |= 1u << nb_index(1, oy, oz);
                 }
             }
-            __syncthreads();
-            mark_nb_tiles(s_nb, tile, tnx, tny, D.tile_bits, D.tile_list[nxt], &D.ls->tile_count[nxt]);
+            nb = __reduce_or_sync(0xffffffffu, nb);
+            warp_mark_nb_tiles(nb, tile, tnx, tny, D.tile_bits);
         }
-        __syncthreads();
+        __syncwarp();
     }
-    if (AM != AM_COUNT && threadIdx.x == 0 && nreq) atomicAdd(&D.ls->sum_requests, nreq);
+    }
+    if (AM != AM_COUNT && lane == 0 && nreq) atomicAdd(&D.ls->sum_requests, nreq);
 }
 
 // ------------------------------------------------------------ bookkeeping
@@ -1002,12 +1069,9 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
     if (threadIdx.x == 0) {
         LoopState *L = D.ls;
         const uint32_t c = L->cur;
-        L->sum_tiles += L->tile_count[c];
         L->sum_pairs += L->pair_count[c];
-        L->tile_count[c] = 0;
         L->pair_count[c] = 0;
         L->cur = c ^ 1u;
-        L->apply_count = 0;
         L->pass += 1;
         L->any_active = s_any;
         if (use_graph) cudaGraphSetConditional(h, s_any ? 1u : 0u);
@@ -1039,7 +1103,6 @@ __global__ void k_status(Dev D, FieldSet FS)
         else if (S->capped) S->status = ST_ITER_LIMIT;
         else S->status = (S->pinned_res ? ST_STUCK : ST_CONVERGED);
     }
-    if (threadIdx.x == 0 && blockIdx.x == 0) D.ls->apply_count = 0;
 }
 
 // ------------------------------------------------------------ edit list
@@ -1173,26 +1236,26 @@ int device_sms() { return sms(); }
 
 void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
-    k_stencil<SM_SETUP><<<grid_for(R.tile1 - R.tile0, 1, 16), CTA, 0, s>>>(D, nullptr, nullptr, R.tile0, R.tile1,
+    k_stencil<SM_SETUP><<<grid_for(R.tile1 - R.tile0, 1, 16), SCTA, 0, s>>>(D, nullptr, nullptr, R.tile0, R.tile1,
                                                                           nullptr, 0);
 }
 void launch_check_all(const Dev &D, cudaStream_t s)
 {
-    k_stencil<SM_CHECK_ALL><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(
+    k_stencil<SM_CHECK_ALL><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), SCTA, 0, s>>>(
         D, nullptr, nullptr, 0, D.total_tiles, nullptr, 0);
 }
 void launch_check_list(const Dev &D, cudaStream_t s)
 {
-    k_stencil<SM_CHECK_LIST><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), CTA, 0, s>>>(
+    k_stencil<SM_CHECK_LIST><<<grid_for(D.total_tiles, 1, D.tun.stencil_bps), SCTA, 0, s>>>(
         D, nullptr, nullptr, 0, 0, nullptr, 0);
 }
 void launch_check_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s)
 {
-    k_stencil<SM_PINNED><<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, nullptr, nullptr, 0, 0, FS.fids, FS.n);
+    k_stencil<SM_PINNED><<<grid_for(D.total_tiles, 1, 16), SCTA, 0, s>>>(D, nullptr, nullptr, 0, 0, FS.fids, FS.n);
 }
 void launch_classify(const Dev &D, uint32_t *desc_out, uint8_t *type_out, cudaStream_t s)
 {
-    k_stencil<SM_CLASSIFY><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D, desc_out, type_out, 0, D.total_tiles,
+    k_stencil<SM_CLASSIFY><<<grid_for(D.total_tiles, 1, 16), SCTA, 0, s>>>(D, desc_out, type_out, 0, D.total_tiles,
                                                                          nullptr, 0);
 }
 
@@ -1250,8 +1313,8 @@ void launch_pairs_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s)
 
 void launch_apply(const Dev &D, int frontier, cudaStream_t s)
 {
-    if (frontier) k_apply_tiles<AM_FRONTIER><<<grid_for(D.total_tiles, 1, D.tun.apply_bps), CTA, 0, s>>>(D);
-    else k_apply_tiles<AM_PLAIN><<<grid_for(D.total_tiles, 1, D.tun.apply_bps), CTA, 0, s>>>(D);
+    if (frontier) k_apply_tiles<AM_FRONTIER><<<grid_for(D.total_tiles, WARPS, D.tun.apply_bps), CTA, 0, s>>>(D);
+    else k_apply_tiles<AM_PLAIN><<<grid_for(D.total_tiles, WARPS, D.tun.apply_bps), CTA, 0, s>>>(D);
 }
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s)
 {
@@ -1263,7 +1326,7 @@ void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph,
 }
 void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s)
 {
-    k_apply_tiles<AM_COUNT><<<grid_for(D.total_tiles, 1, 16), CTA, 0, s>>>(D);
+    k_apply_tiles<AM_COUNT><<<grid_for(D.total_tiles, WARPS, 16), CTA, 0, s>>>(D);
     k_status<<<(FS.n + 255) / 256, 256, 0, s>>>(D, FS);
 }
 void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s)

@@ -118,7 +118,7 @@ struct exactz_server {
     float *f = nullptr, *fhat = nullptr, *g = nullptr;
     uint32_t *desc = nullptr, *cp_rank = nullptr;
     uint32_t *cpwords = nullptr, *reqw = nullptr, *dirty = nullptr;
-    uint32_t *tile_list[2] = {nullptr, nullptr}, *tile_bits = nullptr, *apply_list = nullptr, *apply_bits = nullptr;
+    uint32_t *tile_bits = nullptr, *apply_bits = nullptr;
     uint32_t *pin_tile_bits = nullptr, *pin_tile_arena = nullptr, *tile_field = nullptr;
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
@@ -205,10 +205,7 @@ Dev server_dev(const exactz_server *S)
     D.dirty = S->dirty;
     D.gs = S->gs;
     D.pairbits = S->pairbits;
-    D.apply_list = S->apply_list;
     D.apply_bits = S->apply_bits;
-    D.tile_list[0] = S->tile_list[0];
-    D.tile_list[1] = S->tile_list[1];
     D.tile_bits = S->tile_bits;
     D.pin_tile_bits = S->pin_tile_bits;
     D.pair_list[0] = S->pair_list[0];
@@ -517,9 +514,8 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
     bool ok = salloc(S, S->d_fields, S->slots) && salloc(S, S->d_fst, S->slots) && salloc(S, S->d_ls, 1) &&
               salloc(S, S->d_multi, 512) && salloc(S, S->f, V) && salloc(S, S->fhat, V) && salloc(S, S->g, V) &&
               salloc(S, S->desc, V) && salloc(S, S->cp_rank, V) && salloc(S, S->cpwords, W) &&
-              salloc(S, S->reqw, W) && salloc(S, S->dirty, W) && salloc(S, S->tile_list[0], T) &&
-              salloc(S, S->tile_list[1], T) && salloc(S, S->tile_bits, T / 32 + 1) &&
-              salloc(S, S->apply_list, T) && salloc(S, S->apply_bits, T / 32 + 1) &&
+              salloc(S, S->reqw, W) && salloc(S, S->dirty, W) && salloc(S, S->tile_bits, T / 32 + 1) &&
+              salloc(S, S->apply_bits, T / 32 + 1) &&
               salloc(S, S->pin_tile_bits, T / 32 + 1) && salloc(S, S->pin_tile_arena, T) &&
               salloc(S, S->tile_field, T) && salloc(S, S->cp_key[0], C) && salloc(S, S->cp_key[1], C) &&
               salloc(S, S->cp_ent[0], C) && salloc(S, S->cp_ent[1], C) && salloc(S, S->gs, C) &&
