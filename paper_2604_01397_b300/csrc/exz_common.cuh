@@ -19,10 +19,17 @@ constexpr int TX = 32;   // tile width: one warp per tile row, one cp-bitmap wor
 constexpr int TY = 4;
 constexpr int TZ = 4;
 constexpr int TILE_V = TX * TY * TZ;
-constexpr int HXP = TX + 2;  // halo tile row length (x0-1 .. x0+TX)
+// Halo tile in shared memory: HY x HZ rows of HXP floats.  Slot XOFF + j of a
+// row holds x = x0 + j, so x0 - 1 .. x0 + TX sit at slots XOFF - 1 .. XOFF + TX
+// and the TX tile values start on a 16-byte boundary.  The last slot of a row,
+// XOFF + TX = HXP, is the first (padding) slot of the next row; one spare float
+// after the last row holds it there.
+constexpr int XOFF = 4;
+constexpr int HXP = TX + XOFF;
 constexpr int HY = TY + 2;
 constexpr int HZ = TZ + 2;
-constexpr int HALO_N = HXP * HY * HZ;
+constexpr int HALO_N = (HXP * HY * HZ + 1 + 3) / 4 * 4;  // rounded to 16 bytes
+static_assert(HXP % 4 == 0 && XOFF >= 1, "halo rows start and tile values sit on 16-byte boundaries");
 constexpr int CTA = 256;
 constexpr int WARPS = CTA / 32;
 constexpr int ROWS = TY * TZ;
@@ -168,8 +175,8 @@ struct Dev {
     uint32_t *dirty;     // vertices whose closed star changed last pass (row words)
     float *gs;           // g of the critical points, in f's sorted order
     uint32_t *pairbits;  // CP pairs already queued for the next pass
-    uint32_t *apply_bits;  // tiles holding requested vertices (read and cleared by the apply kernel)
-    uint32_t *tile_bits;   // tiles to check next pass (read and cleared by the check kernel)
+    uint8_t *apply_flag;  // per tile: holds requested vertices (taken and cleared by the apply kernel)
+    uint8_t *tile_flag;   // per tile: to check next pass (taken and cleared by the check kernel)
     uint32_t *pin_tile_bits;
     uint32_t *pair_list[2];
     uint32_t *cp_key[2];
@@ -222,25 +229,23 @@ __device__ __forceinline__ void tile_range(const Dev &D, unsigned long long coun
     }
 }
 
-// Words [beg, end) with stride `step` of a tile bitmap handled by worker `w` of
-// `nworkers` (a block or a warp).
-__device__ __forceinline__ void word_range(const Dev &D, uint32_t nwords, uint32_t w, uint32_t nworkers,
-                                           uint32_t &beg, uint32_t &end, uint32_t &step)
+// Positions beg, beg + step, ... (< end) of the n tiles handled by worker `w`
+// of `nworkers` (a block or a warp): every nworkers-th tile, or a contiguous
+// chunk with the chunked schedule.
+__device__ __forceinline__ void work_range(const Dev &D, uint32_t n, uint32_t w, uint32_t nworkers, uint32_t &beg,
+                                           uint32_t &end, uint32_t &step)
 {
     if (D.tun.chunked) {
-        const uint32_t c = (nwords + nworkers - 1) / nworkers;
-        beg = min(nwords, w * c);
-        end = min(nwords, beg + c);
+        const uint32_t c = (n + nworkers - 1) / nworkers;
+        beg = (uint32_t)min((uint64_t)n, (uint64_t)w * c);
+        end = (uint32_t)min((uint64_t)n, (uint64_t)beg + c);
         step = 1;
     } else {
         beg = w;
-        end = nwords;
+        end = n;
         step = nworkers;
     }
 }
-
-// Number of words of the tile bitmaps.
-__device__ __forceinline__ uint32_t tile_words(const Dev &D) { return (D.total_tiles + 31u) / 32u; }
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t field_of_tile(const Dev &D, uint32_t tile)

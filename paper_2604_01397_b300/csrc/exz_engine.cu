@@ -137,9 +137,9 @@ struct exactz_workspace {
     LoopState *d_ls = nullptr;
     uint32_t *d_multi = nullptr;
     uint32_t *desc = nullptr, *cp_rank = nullptr, *cpwords = nullptr, *reqw = nullptr;
-    uint32_t *dirty = nullptr, *pairbits = nullptr, *apply_bits = nullptr;
+    uint32_t *dirty = nullptr, *pairbits = nullptr;
+    uint8_t *apply_flag = nullptr, *tile_flag = nullptr;
     float *gs = nullptr;
-    uint32_t *tile_bits = nullptr;
     uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
     uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_arena = nullptr;
     uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
@@ -245,8 +245,8 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->dirty, W);
     AL(ws->gs, C);
     AL(ws->pairbits, C / 32 + 1);
-    AL(ws->apply_bits, T / 32 + 1);
-    AL(ws->tile_bits, T / 32 + 1);
+    AL(ws->apply_flag, T);
+    AL(ws->tile_flag, T);
     AL(ws->pin_tile_arena, T);
     AL(ws->pin_tile_bits, T / 32 + 1);
     AL(ws->pair_list[0], 2 * C);
@@ -295,8 +295,8 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.dirty = ws->dirty;
     D.gs = ws->gs;
     D.pairbits = ws->pairbits;
-    D.apply_bits = ws->apply_bits;
-    D.tile_bits = ws->tile_bits;
+    D.apply_flag = ws->apply_flag;
+    D.tile_flag = ws->tile_flag;
     D.pin_tile_bits = ws->pin_tile_bits;
     D.pair_list[0] = ws->pair_list[0];
     D.pair_list[1] = ws->pair_list[1];
@@ -463,10 +463,10 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemcpyAsync(ws->d_fields, L.fd.data(), sizeof(FieldDesc) * nf, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ws->d_fst, 0, sizeof(FieldState) * nf, s));
     CK(cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s));
-    CK(cudaMemsetAsync(ws->tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->tile_flag, 0, L.total_tiles, s));
     CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->pairbits, 0, (L.total_real / 32 + 1) * 4, s));
-    CK(cudaMemsetAsync(ws->apply_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->apply_flag, 0, L.total_tiles, s));
     const Dev D = make_dev(ws, L);
     const int frontier = opt.mode != EXACTZ_MODE_PLAIN;
     const bool prof = opt.profile != 0;
@@ -919,8 +919,7 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
     bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
               c.take(ws->d_ls, 1) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
               c.take(ws->cpwords, W) && c.take(ws->reqw, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
-              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_bits, T / 32 + 1) &&
-              c.take(ws->tile_bits, T / 32 + 1) &&
+              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_flag, T) && c.take(ws->tile_flag, T) &&
               c.take(ws->pin_tile_arena, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
               c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
               c.take(ws->pin_pair_arena, 2 * C) && c.take(ws->fids, L.nfields) && c.take(ws->cp_key[0], C) &&

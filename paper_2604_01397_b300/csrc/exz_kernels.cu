@@ -38,6 +38,7 @@ static_assert(CTA % 32 == 0 && ROWS <= 32, "tile-row prefix sums run in one warp
 // tiles are in flight per SM (its time goes mostly to memory latency per tile).
 constexpr int SCTA = 128, STWARPS = SCTA / 32;
 static_assert(SCTA % 32 == 0 && SCTA >= 32 && SCTA >= ROWS, "stencil blocks: whole warps, one thread per tile row");
+static_assert(STWARPS == TZ && TY <= 32, "frontier check: warp w visits the dirty vertices of z-slab w");
 static_assert(WBLOCK % CTA == 0 && VBLOCK % (4 * CTA) == 0, "compaction and edit-list blocks");
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
@@ -68,16 +69,16 @@ __device__ __forceinline__ void tile_targets_add(TileTargets &T, int lx, int ly,
 
 __device__ __forceinline__ int nb_index(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
-// Mark the tiles of a 27-bit neighbourhood mask around `tile` in a tile
-// bitmap; lane j of the calling warp handles neighbour j.
+// Flag the tiles of a 27-bit neighbourhood mask around `tile`; lane j of the
+// calling warp handles neighbour j.  Flags are plain byte stores: setting one
+// twice, or from several threads, leaves the same result.
 __device__ __forceinline__ void warp_mark_nb_tiles(uint32_t nb, uint32_t tile, uint32_t tnx, uint32_t tny,
-                                                   uint32_t *bits)
+                                                   uint8_t *flags)
 {
     const int j = threadIdx.x & 31;
     if (j < 27 && ((nb >> j) & 1u)) {
         const int ox = j % 3 - 1, oy = (j / 3) % 3 - 1, oz = j / 9 - 1;
-        const uint32_t t = (uint32_t)((int64_t)tile + ox + (int64_t)tnx * (oy + (int64_t)tny * oz));
-        atomicOr(&bits[t >> 5], 1u << (t & 31));
+        flags[(int64_t)tile + ox + (int64_t)tnx * (oy + (int64_t)tny * oz)] = 1;
     }
 }
 
@@ -125,7 +126,7 @@ __device__ __forceinline__ void tile_targets_commit(TileTargets &T, const Dev &D
     }
     __syncthreads();
     const uint32_t nb = T.nb;
-    if (threadIdx.x < 32) warp_mark_nb_tiles(nb, tile, tnx, tny, D.apply_bits);
+    if (threadIdx.x < 32) warp_mark_nb_tiles(nb, tile, tnx, tny, D.apply_flag);
     __syncthreads();
     if (threadIdx.x == 0) T.nb = 0;
 }
@@ -218,22 +219,67 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
     return pos;
 }
 
+// cp.async of one 4-byte word into shared memory (completes at the next wait).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// cp.async of 16 bytes (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+constexpr uint32_t NO_TILE = 0xFFFFFFFFu;
+
+// Position of a tile in its field.
+struct TileGeo {
+    uint32_t fid, tx;
+    int x0, y0, z0;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
+{
+    TileGeo G;
+    G.fid = field_of_tile(D, tile);
+    const FieldDesc &F = D.fields[G.fid];
+    const uint32_t lt = (uint32_t)(tile - F.tbase);
+    const uint32_t rest = lt / F.tnx;
+    G.tx = lt - rest * F.tnx;
+    const uint32_t tz = rest / F.tny, ty = rest - tz * F.tny;
+    G.x0 = (int)(G.tx * TX);
+    G.y0 = (int)(ty * TY);
+    G.z0 = (int)(tz * TZ);
+    return G;
+}
+
 // One tile per block iteration: the tile's values plus a one-vertex halo are
 // staged in shared memory (NaN outside the domain), then every vertex (SETUP,
 // CHECK_ALL, PINNED, CLASSIFY) or every dirty vertex (CHECK_LIST) is checked.
-// Tiles come from [t0, t1) (SETUP, CHECK_ALL, CLASSIFY), the current frontier
-// list (CHECK_LIST), or the pinned-tile lists of fields fids[0..nf) (PINNED).
+// Tiles come from [t0, t1) (SETUP, CHECK_ALL, CLASSIFY), the set bits of
+// tile_flag (CHECK_LIST, taken and cleared 32 candidates at a time), or the
+// pinned-tile lists of fields fids[0..nf) (PINNED).
+// The modes that read one array stage the next tile with cp.async into a
+// second buffer while the current one is checked; SETUP (two arrays) loads
+// each tile directly.
 template <int MODE>
 __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
-                                                    uint32_t t1, const uint32_t *fids, uint32_t nf)
+                                                      uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
-    __shared__ float sa[HALO_N];
-    __shared__ float sb[MODE == SM_SETUP ? HALO_N : 1];
+    constexpr bool PIPE = MODE != SM_SETUP;
+    constexpr int NB = PIPE ? 2 : 1;
+    __shared__ __align__(16) float sa[NB][HALO_N];
+    __shared__ __align__(16) float sb[MODE == SM_SETUP ? HALO_N : 1];
     __shared__ uint32_t smulti[512];
     __shared__ TileTargets tt;
     __shared__ uint32_t s_err;
-    __shared__ uint32_t s_rw[ROWS];       // dirty row words of the tile (CHECK_LIST)
-    __shared__ uint32_t s_pre[ROWS + 1];  // their prefix popcounts
+    __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
+    __shared__ uint32_t s_tile[2];        // the tile staged in each buffer
+    __shared__ TileGeo s_geo[NB];         // its position
 
     for (int j = threadIdx.x; j < 512; j += SCTA) smulti[j] = D.multi[j];
     for (int w = threadIdx.x; w < HY * HZ; w += SCTA) tt.row[w] = 0;
@@ -242,86 +288,119 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
         s_err = 0;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    auto do_tile = [&](const uint32_t tile) {
-        const uint32_t fid = field_of_tile(D, tile);
-        const FieldDesc &F = D.fields[fid];
-        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
-        const uint64_t vbase = F.vbase;
-        const uint32_t lt = (uint32_t)(tile - F.tbase);
-        const uint32_t tnx = F.tnx, tny = F.tny;
-        const uint32_t rest = lt / tnx;
-        const uint32_t tx = lt - rest * tnx;
-        const uint32_t tz = rest / tny, ty = rest - tz * tny;
-        const int x0 = (int)(tx * TX), y0 = (int)(ty * TY), z0 = (int)(tz * TZ);
-        if (MODE == SM_CHECK_LIST && threadIdx.x < ROWS) {
-            // take (and clear) the dirty bits of this tile's rows
-            const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
-            uint32_t w = 0;
-            if (y < ny && z < nz) {
-                uint32_t *p = D.dirty + F.wbase + ((uint64_t)z * ny + y) * tnx + tx;
-                w = *p;
-                if (w) *p = 0;
-            }
-            s_rw[threadIdx.x] = w;
-        }
+    const float qnan = __int_as_float(0x7fc00000);
 
-        // halo tile, one warp per row of HXP values (x0-1 .. x0+TX); NaN outside the domain
+    // Stage tile into buffer b: the halo rows (one warp per row of HXP values,
+    // x0-1 .. x0+TX) and, for CHECK_LIST, the tile's dirty row words.
+    auto stage = [&](const uint32_t tile, const int b) {
+        const TileGeo G = tile_geo(D, tile);
+        if (threadIdx.x == 0) s_geo[b] = G;
+        const FieldDesc &F = D.fields[G.fid];
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
+        if (MODE == SM_CHECK_LIST && threadIdx.x < ROWS) {
+            const uint32_t y = (uint32_t)G.y0 + threadIdx.x % TY, z = (uint32_t)G.z0 + threadIdx.x / TY;
+            if (y < ny && z < nz) cp_async4(&s_rw[b][threadIdx.x], D.dirty + F.wbase + ((uint64_t)z * ny + y) * F.tnx + G.tx);
+            else s_rw[b][threadIdx.x] = 0;
+        }
         const float *A = (MODE == SM_SETUP || MODE == SM_CLASSIFY) ? F.f : F.g;
         const float *B = F.fhat;
-        const float qnan = __int_as_float(0x7fc00000);
+        const bool interior = G.x0 >= 1 && G.x0 + TX < (int)nx && G.y0 >= 1 && G.y0 + TY < (int)ny && G.z0 >= 1 &&
+                              G.z0 + TZ < (int)nz;
+        if (PIPE && interior && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (nx & 3u) == 0) {
+            // every halo value is inside the field and each row's tile values
+            // start on 16 bytes: 8 copies of 16 bytes per row plus its two ends
+            const uint64_t nxy = (uint64_t)nx * ny;
+            const float *base = A + ((uint64_t)(G.z0 - 1) * ny + (uint64_t)(G.y0 - 1)) * nx + G.x0;
+            constexpr int PARTS = TX / 4 + 2;
+            for (int j = threadIdx.x; j < HY * HZ * PARTS; j += SCTA) {
+                const int row = j / PARTS, part = j - row * PARTS;
+                const int hz = row / HY, hy = row - hz * HY;
+                const float *g = base + (uint64_t)hz * nxy + (uint64_t)hy * nx;
+                float *sr = sa[b] + row * HXP + XOFF;
+                if (part < TX / 4) cp_async16(sr + 4 * part, g + 4 * part);
+                else if (part == TX / 4) cp_async4(sr - 1, g - 1);
+                else cp_async4(sr + TX, g + TX);
+            }
+            return;
+        }
         for (int row = warp; row < HY * HZ; row += STWARPS) {
             const int hz = row / HY, hy = row - hz * HY;
-            const int Y = y0 - 1 + hy, Z = z0 - 1 + hz;
+            const int Y = G.y0 - 1 + hy, Z = G.z0 - 1 + hz;
             const bool rin = Y >= 0 && Z >= 0 && Y < (int)ny && Z < (int)nz;
             const uint64_t rb = rin ? ((uint64_t)Z * ny + (uint64_t)Y) * nx : 0;
-            const int X0 = x0 - 1 + lane, X1 = x0 + TX - 1 + lane;
+            const int X0 = G.x0 - 1 + lane, X1 = G.x0 + TX - 1 + lane;
             const bool in0 = rin && X0 >= 0 && X0 < (int)nx;
             const bool in1 = rin && lane < 2 && X1 < (int)nx;
-            float *sr = sa + row * HXP;
-            sr[lane] = in0 ? A[rb + X0] : qnan;
-            if (lane < 2) sr[TX + lane] = in1 ? A[rb + X1] : qnan;
-            if (MODE == SM_SETUP) {
-                float *tr = sb + row * HXP;
-                tr[lane] = in0 ? B[rb + X0] : qnan;
-                if (lane < 2) tr[TX + lane] = in1 ? B[rb + X1] : qnan;
-            }
-        }
-        if (MODE == SM_CHECK_LIST) {
-            __syncthreads();
-            if (warp == 0) {
-                uint32_t c = lane < ROWS ? __popc(s_rw[lane]) : 0u;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
-                    if (lane >= o) c += y;
+            float *sr = sa[b] + row * HXP + (XOFF - 1);  // slot of x0 - 1
+            if (PIPE) {
+                if (in0) cp_async4(sr + lane, A + rb + X0);
+                else sr[lane] = qnan;
+                if (lane < 2) {
+                    if (in1) cp_async4(sr + TX + lane, A + rb + X1);
+                    else sr[TX + lane] = qnan;
                 }
-                if (lane < ROWS) s_pre[lane + 1] = c;
-                if (lane == 0) s_pre[0] = 0;
+            } else {
+                sr[lane] = in0 ? A[rb + X0] : qnan;
+                if (lane < 2) sr[TX + lane] = in1 ? A[rb + X1] : qnan;
+                if (MODE == SM_SETUP) {
+                    float *tr = sb + row * HXP + (XOFF - 1);
+                    tr[lane] = in0 ? B[rb + X0] : qnan;
+                    if (lane < 2) tr[TX + lane] = in1 ? B[rb + X1] : qnan;
+                }
             }
         }
-        __syncthreads();
+    };
+
+    // Check (or classify) the staged tile in buffer b; ends with a barrier.
+    auto process = [&](const uint32_t tile, const int b) {
+        const TileGeo G = s_geo[b];
+        const uint32_t fid = G.fid, tx = G.tx;
+        const int x0 = G.x0, y0 = G.y0, z0 = G.z0;
+        const FieldDesc &F = D.fields[fid];
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny;
+        const uint64_t vbase = F.vbase;
+        const float *S = sa[b];
+        const uint32_t *RW = s_rw[b];
+        // CHECK_LIST: warp w visits the dirty vertices of the four rows of
+        // z-slab w, numbered by a prefix sum over those rows (lanes 0-3)
+        uint32_t myw = 0, pre = 0, e1 = 0, e2 = 0, e3 = 0;
+        int nvisit = ROWS * TX;
+        if (MODE == SM_CHECK_LIST) {
+            if (threadIdx.x < ROWS && RW[threadIdx.x]) {  // the dirty bits are taken: clear them
+                const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
+                D.dirty[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = 0;
+            }
+            myw = lane < TY ? RW[warp * TY + lane] : 0u;
+            const uint32_t cnt = __popc(myw);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < TY; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            pre = incl - cnt;
+            e1 = __shfl_sync(0xffffffffu, pre, 1);
+            e2 = __shfl_sync(0xffffffffu, pre, 2);
+            e3 = __shfl_sync(0xffffffffu, pre, 3);
+            nvisit = (int)__shfl_sync(0xffffffffu, incl, TY - 1);
+        }
         const bool interior = x0 >= 1 && x0 + TX < (int)nx && y0 >= 1 && y0 + TY < (int)ny && z0 >= 1 &&
                               z0 + TZ < (int)nz;
-        // vertices of this tile to visit: all rows (one warp per row) or the dirty list
-        const int nvisit = MODE == SM_CHECK_LIST ? (int)s_pre[ROWS] : ROWS * TX;
+        // vertices of this tile to visit: all rows (one warp per row) or the warp's dirty vertices
         for (int base = (MODE == SM_CHECK_LIST ? 0 : warp * TX); base < nvisit;
-             base += (MODE == SM_CHECK_LIST ? SCTA : STWARPS * TX)) {
+             base += (MODE == SM_CHECK_LIST ? 32 : STWARPS * TX)) {
             int lx, ly, lz;
             bool sel = true;
             if (MODE == SM_CHECK_LIST) {
-                const int k = base + threadIdx.x;
+                const int k = base + lane;
                 sel = k < nvisit;
-                int row = 0;
-                if (sel) {
-#pragma unroll
-                    for (int step = 8; step >= 1; step >>= 1)
-                        if (row + step <= ROWS - 1 && (int)s_pre[row + step] <= k) row += step;
-                    lx = nth_set_bit(s_rw[row], k - (int)s_pre[row]);
-                } else {
-                    lx = 0;
-                }
-                ly = row % TY;
-                lz = row / TY;
+                // the last of the warp's rows whose first number is <= k
+                const int r = (k >= (int)e1) + (k >= (int)e2) + (k >= (int)e3);
+                const uint32_t rword = __shfl_sync(0xffffffffu, myw, r);
+                const uint32_t rpre = __shfl_sync(0xffffffffu, pre, r);
+                lx = sel ? nth_set_bit(rword, k - (int)rpre) : 0;
+                ly = r;
+                lz = warp;
             } else {
                 const int rr = base / TX;
                 lx = lane;
@@ -330,13 +409,13 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
             }
             const uint32_t x = (uint32_t)(x0 + lx), y = (uint32_t)(y0 + ly), z = (uint32_t)(z0 + lz);
             const bool in = sel && x < nx && y < ny && z < nz;
-            const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lx + 1);
+            const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lx + XOFF);
             bool cp = false;
             uint32_t req = 0;
             const uint64_t i = ((uint64_t)z * ny + y) * nx + x;
             if (in) {
                 if (MODE == SM_SETUP || MODE == SM_CLASSIFY) {
-                    Stn sf = interior ? stencil15<true>(sa, c) : stencil15<false>(sa, c);
+                    Stn sf = interior ? stencil15<true>(S, c) : stencil15<false>(S, c);
                     const uint32_t L = sf.mask, U = sf.valid & ~sf.mask;
                     const bool mn = L == 0, mxx = !mn && U == 0;
                     const bool join = !mn && !mxx && multi_bit(smulti, L);
@@ -349,7 +428,7 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
                         if (type_out)
                             type_out[i] = (uint8_t)(mn ? 1 : (mxx ? 2 : ((join ? 4 : 0) | (split ? 8 : 0))));
                     } else {
-                        const float fv = sa[c], hv = sb[c];
+                        const float fv = S[c], hv = sb[c];
                         uint32_t e = 0;
                         if (!isfinite(fv) || !isfinite(hv)) e = ERR_NONFINITE;
                         else if (hv < __fsub_rn(fv, F.xi) || hv > __fadd_rn(fv, F.xi)) e = ERR_BOUND;
@@ -361,7 +440,7 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
                     }
                 } else {
                     const uint32_t d = __ldg(&D.desc[vbase + i]);
-                    Stn sg = interior ? stencil15<true>(sa, c) : stencil15<false>(sa, c);
+                    Stn sg = interior ? stencil15<true>(S, c) : stencil15<false>(S, c);
                     req = request_mask(smulti, d, sg);
                 }
             }
@@ -378,47 +457,131 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
         }
+        if (MODE == SM_CLASSIFY) __syncthreads();
     };
 
-    if (MODE == SM_CHECK_LIST) {
-        // the tiles of the set bits of tile_bits, a word at a time (read and cleared by thread 0)
-        __shared__ uint32_t s_word[2];
-        unsigned long long nt = 0;
-        uint32_t wb, we, wst;
-        word_range(D, tile_words(D), blockIdx.x, gridDim.x, wb, we, wst);
-        uint32_t par = 0;
-        for (uint32_t w = wb; w < we; w += wst, par ^= 1u) {
-            if (threadIdx.x == 0) {
-                const uint32_t v = D.tile_bits[w];
-                if (v) D.tile_bits[w] = 0;
-                s_word[par] = v;
-            }
+    if (!PIPE) {
+        unsigned long long it0, it1, its;
+        tile_range(D, t1 - t0, it0, it1, its);
+        for (unsigned long long it = it0; it < it1; it += its) {
+            const uint32_t tile = t0 + (uint32_t)it;
+            stage(tile, 0);
             __syncthreads();
-            uint32_t word = s_word[par];  // s_word[par] is rewritten two words later, after another barrier
-            nt += __popc(word);
-            while (word) {
-                const uint32_t tile = w * 32u + (uint32_t)(__ffs(word) - 1);
-                word &= word - 1;
-                do_tile(tile);
-            }
+            process(tile, 0);
         }
-        if (threadIdx.x == 0 && nt) atomicAdd(&D.ls->sum_tiles, nt);
-    } else {
-        const uint32_t nouter = MODE == SM_PINNED ? nf : 1u;
-        for (uint32_t fi = 0; fi < nouter; fi++) {
-            unsigned long long count;
-            const uint32_t *list = nullptr;
-            if (MODE == SM_PINNED) {
-                count = D.fst[fids[fi]].pin_tile_count;
-                list = D.fields[fids[fi]].pin_tiles;
-            } else {
-                count = t1 - t0;
-            }
-            unsigned long long it0, it1, its;
-            tile_range(D, count, it0, it1, its);
-            for (unsigned long long it = it0; it < it1; it += its) do_tile(list ? list[it] : t0 + (uint32_t)it);
+        return;
+    }
+
+    // Tile source, advanced by warp 0; its state lives in shared memory so that
+    // it holds no registers while tiles are checked.
+    struct Source {
+        unsigned long long it, it1, its, ntiles;  // ranges and pinned lists; tiles taken
+        const uint32_t *plist;
+        uint32_t fi;
+        uint32_t nxt, end, step, pend, pbase;  // CHECK_LIST: next position, taken flags of the last probe
+    };
+    __shared__ Source src;
+    if (threadIdx.x == 0) {
+        src.it = src.it1 = src.ntiles = 0;
+        src.its = 1;
+        src.plist = nullptr;
+        src.fi = src.nxt = src.end = src.pend = src.pbase = 0;
+        src.step = 1;
+        if (MODE == SM_CHECK_LIST) {
+            work_range(D, D.total_tiles, blockIdx.x, gridDim.x, src.nxt, src.end, src.step);
+        } else if (MODE != SM_PINNED) {
+            tile_range(D, t1 - t0, src.it, src.it1, src.its);
         }
     }
+    __syncthreads();
+    auto next_tile = [&]() -> uint32_t {  // warp 0, all lanes
+        uint32_t t = NO_TILE;
+        if (MODE == SM_CHECK_LIST) {
+            uint32_t nxt = src.nxt, pend = src.pend, pbase = src.pbase;
+            const uint32_t end = src.end, step = src.step;
+            uint32_t taken = 0;
+            while (pend == 0 && nxt < end) {
+                // probe the next 32 tiles of this block at once; take the flagged ones
+                const uint64_t ti = (uint64_t)nxt + (uint64_t)lane * step;
+                const bool f = ti < end && D.tile_flag[ti] != 0;
+                if (f) D.tile_flag[ti] = 0;
+                pend = __ballot_sync(0xffffffffu, f);
+                pbase = nxt;
+                taken += __popc(pend);
+                const uint64_t nn = (uint64_t)nxt + 32ull * step;
+                nxt = nn < end ? (uint32_t)nn : end;
+            }
+            if (pend) {
+                t = pbase + (uint32_t)(__ffs(pend) - 1) * step;
+                pend &= pend - 1;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                src.nxt = nxt;
+                src.pend = pend;
+                src.pbase = pbase;
+                src.ntiles += taken;
+            }
+        } else if (MODE == SM_PINNED) {
+            unsigned long long it = src.it, it1 = src.it1, its = src.its;
+            const uint32_t *plist = src.plist;
+            uint32_t fi = src.fi;
+            while (it >= it1 && fi < nf) {
+                const unsigned long long count = D.fst[fids[fi]].pin_tile_count;
+                plist = D.fields[fids[fi]].pin_tiles;
+                fi++;
+                tile_range(D, count, it, it1, its);
+            }
+            if (it < it1) {
+                t = plist[it];
+                it += its;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                src.it = it;
+                src.it1 = it1;
+                src.its = its;
+                src.plist = plist;
+                src.fi = fi;
+            }
+        } else {
+            const unsigned long long it = src.it;
+            if (it < src.it1) {
+                t = t0 + (uint32_t)it;
+                __syncwarp();
+                if (lane == 0) src.it = it + src.its;
+            }
+        }
+        __syncwarp();
+        return t;
+    };
+
+    if (warp == 0) {
+        const uint32_t t = next_tile();
+        if (lane == 0) s_tile[0] = t;
+    }
+    __syncthreads();
+    {
+        const uint32_t t = s_tile[0];
+        if (t != NO_TILE) stage(t, 0);
+        cp_async_commit();
+    }
+    for (int b = 0;; b ^= 1) {
+        const uint32_t cur = s_tile[b];
+        if (cur == NO_TILE) break;
+        if (warp == 0) {
+            const uint32_t t = next_tile();
+            if (lane == 0) s_tile[b ^ 1] = t;
+        }
+        __syncthreads();  // s_tile[b ^ 1] is set; buffer b ^ 1 is free
+        const uint32_t nxt = s_tile[b ^ 1];
+        if (nxt != NO_TILE) stage(nxt, b ^ 1);
+        cp_async_commit();
+        cp_async_wait_prev();  // this thread's copies of `cur` have landed
+        __syncthreads();       // everyone's have
+        process(cur, b);
+    }
+    if (MODE == SM_CHECK_LIST && threadIdx.x == 0 && src.ntiles) atomicAdd(&D.ls->sum_tiles, src.ntiles);
 }
 
 // ------------------------------------------------------------ block scan helpers
@@ -768,8 +931,7 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
                 else viol = false;
             }
         }
-        if (viol && !(__ldcg(&D.apply_bits[tile >> 5]) & (1u << (tile & 31))))
-            atomicOr(&D.apply_bits[tile >> 5], 1u << (tile & 31));
+        if (viol && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
     }
     }
 }
@@ -818,8 +980,8 @@ __device__ __forceinline__ void mark_face_tiles(uint32_t own, uint32_t x, uint32
 enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
 
 // One tile holding requested vertices per warp iteration (warps work
-// independently): a warp takes a word of apply_bits (and clears it) and works
-// through the tiles of its set bits.  The tile's 16 request words are read (and
+// independently): a warp probes 32 of its tiles' flags at once, takes (and
+// clears) the flagged ones and works through them.  The tile's 16 request words are read (and
 // cleared) by lanes 0-15, the
 // requested vertices are numbered by a warp prefix sum and worked through 32
 // at a time, and the changed vertices are collected as row bits in the warp's
@@ -838,25 +1000,17 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
     uint32_t *s_cw = s_cw_all[warp];
     const uint32_t nxt = D.ls->cur ^ 1u;
     unsigned long long nreq = 0;
-    uint32_t wb, we, wst;
-    word_range(D, tile_words(D), blockIdx.x * WARPS + warp, gridDim.x * WARPS, wb, we, wst);
-    for (uint32_t w = wb; w < we; w += wst) {
-    uint32_t word = D.apply_bits[w];
-    if (!word) continue;
-    __syncwarp();
-    if (lane == 0) D.apply_bits[w] = 0;
-    // the next tile's field is loaded one tile ahead
-    uint32_t tile_n = w * 32u + (uint32_t)(__ffs(word) - 1);
-    uint32_t fid_n = field_of_tile(D, tile_n);
-    word &= word - 1;
-    for (bool more = true; more;) {
-        const uint32_t tile = tile_n, fid = fid_n;
-        more = word != 0;
-        if (more) {
-            tile_n = w * 32u + (uint32_t)(__ffs(word) - 1);
-            word &= word - 1;
-            fid_n = field_of_tile(D, tile_n);
-        }
+    uint32_t pb, pe, pst;
+    work_range(D, D.total_tiles, blockIdx.x * WARPS + warp, gridDim.x * WARPS, pb, pe, pst);
+    for (uint64_t p = pb; p < pe; p += 32ull * pst) {
+    const uint64_t ti = p + (uint64_t)lane * pst;
+    const bool flagged = ti < pe && D.apply_flag[ti] != 0;
+    if (flagged) D.apply_flag[ti] = 0;
+    uint32_t pend = __ballot_sync(0xffffffffu, flagged);
+    while (pend) {
+        const uint32_t tile = (uint32_t)(p + (uint64_t)(__ffs(pend) - 1) * pst);
+        pend &= pend - 1;
+        const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
         FieldState *S = &D.fst[fid];
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny, N = F.N;
@@ -1036,7 +1190,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                 }
             }
             nb = __reduce_or_sync(0xffffffffu, nb);
-            warp_mark_nb_tiles(nb, tile, tnx, tny, D.tile_bits);
+            warp_mark_nb_tiles(nb, tile, tnx, tny, D.tile_flag);
         }
         __syncwarp();
     }

@@ -118,7 +118,7 @@ struct exactz_server {
     float *f = nullptr, *fhat = nullptr, *g = nullptr;
     uint32_t *desc = nullptr, *cp_rank = nullptr;
     uint32_t *cpwords = nullptr, *reqw = nullptr, *dirty = nullptr;
-    uint32_t *tile_bits = nullptr, *apply_bits = nullptr;
+    uint8_t *tile_flag = nullptr, *apply_flag = nullptr;
     uint32_t *pin_tile_bits = nullptr, *pin_tile_arena = nullptr, *tile_field = nullptr;
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
@@ -205,8 +205,8 @@ Dev server_dev(const exactz_server *S)
     D.dirty = S->dirty;
     D.gs = S->gs;
     D.pairbits = S->pairbits;
-    D.apply_bits = S->apply_bits;
-    D.tile_bits = S->tile_bits;
+    D.apply_flag = S->apply_flag;
+    D.tile_flag = S->tile_flag;
     D.pin_tile_bits = S->pin_tile_bits;
     D.pair_list[0] = S->pair_list[0];
     D.pair_list[1] = S->pair_list[1];
@@ -350,8 +350,8 @@ int start_request(exactz_server *S, const Dev &D, Req *r)
     SK(cudaMemsetAsync(S->dirty + r->w0, 0, r->nw * 4, S->cs));
     const uint64_t tw0 = r->t0 / 32, tw1 = (r->t0 + r->nt + 31) / 32;
     SK(cudaMemsetAsync(S->pin_tile_bits + tw0, 0, (tw1 - tw0) * 4, S->cs));
-    SK(cudaMemsetAsync(S->tile_bits + tw0, 0, (tw1 - tw0) * 4, S->cs));
-    SK(cudaMemsetAsync(S->apply_bits + tw0, 0, (tw1 - tw0) * 4, S->cs));
+    SK(cudaMemsetAsync(S->tile_flag + r->t0, 0, r->nt, S->cs));
+    SK(cudaMemsetAsync(S->apply_flag + r->t0, 0, r->nt, S->cs));
     const uint64_t cw0 = r->c0 / 32, cw1 = (r->c0 + r->n + 31) / 32;
     SK(cudaMemsetAsync(S->pairbits + cw0, 0, (cw1 - cw0) * 4, S->cs));
     launch_fill_u32(S->tile_field + r->t0, slot, r->nt, S->cs);
@@ -514,8 +514,8 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
     bool ok = salloc(S, S->d_fields, S->slots) && salloc(S, S->d_fst, S->slots) && salloc(S, S->d_ls, 1) &&
               salloc(S, S->d_multi, 512) && salloc(S, S->f, V) && salloc(S, S->fhat, V) && salloc(S, S->g, V) &&
               salloc(S, S->desc, V) && salloc(S, S->cp_rank, V) && salloc(S, S->cpwords, W) &&
-              salloc(S, S->reqw, W) && salloc(S, S->dirty, W) && salloc(S, S->tile_bits, T / 32 + 1) &&
-              salloc(S, S->apply_bits, T / 32 + 1) &&
+              salloc(S, S->reqw, W) && salloc(S, S->dirty, W) && salloc(S, S->tile_flag, T) &&
+              salloc(S, S->apply_flag, T) &&
               salloc(S, S->pin_tile_bits, T / 32 + 1) && salloc(S, S->pin_tile_arena, T) &&
               salloc(S, S->tile_field, T) && salloc(S, S->cp_key[0], C) && salloc(S, S->cp_key[1], C) &&
               salloc(S, S->cp_ent[0], C) && salloc(S, S->cp_ent[1], C) && salloc(S, S->gs, C) &&
@@ -538,8 +538,7 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
              cudaMemset(S->d_ls, 0, sizeof(LoopState)) == cudaSuccess &&
              cudaMemcpy(S->d_multi, host_multi_table(), 2048, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemset(S->reqw, 0, W * 4) == cudaSuccess && cudaMemset(S->dirty, 0, W * 4) == cudaSuccess &&
-             cudaMemset(S->tile_bits, 0, (T / 32 + 1) * 4) == cudaSuccess &&
-             cudaMemset(S->apply_bits, 0, (T / 32 + 1) * 4) == cudaSuccess &&
+             cudaMemset(S->tile_flag, 0, T) == cudaSuccess && cudaMemset(S->apply_flag, 0, T) == cudaSuccess &&
              cudaMemset(S->pin_tile_bits, 0, (T / 32 + 1) * 4) == cudaSuccess &&
              cudaMemset(S->pairbits, 0, (C / 32 + 1) * 4) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
     }
