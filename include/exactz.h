@@ -158,6 +158,12 @@ typedef struct {
     uint64_t sum_tiles;       /* tiles re-checked by frontier passes (0 for PLAIN) */
     uint64_t sum_pairs;       /* CP pairs re-checked by frontier passes (0 for PLAIN) */
     float stage_ms[8];
+    /* PLAIN and FRONTIER with opts.profile = 1: summed CUDA-event times of the
+     * loop passes' kernels (after the first pass), [0] vertex checks (rules R1,
+     * R2), [1] CP-pair checks (R3), [2] edits; loop_passes = passes timed. */
+    float loop_kernel_ms[3];
+    uint32_t reserved;
+    uint64_t loop_passes;
 } exactz_stats;
 
 int exactz_ws_stats(const exactz_workspace *ws, exactz_stats *out);

@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("passes", ctypes.c_uint64),
                 ("total_critical", ctypes.c_uint64), ("sum_requests", ctypes.c_uint64),
                 ("sum_tiles", ctypes.c_uint64), ("sum_pairs", ctypes.c_uint64),
-                ("stage_ms", ctypes.c_float * 8)]
+                ("stage_ms", ctypes.c_float * 8), ("loop_kernel_ms", ctypes.c_float * 3),
+                ("reserved", ctypes.c_uint32), ("loop_passes", ctypes.c_uint64)]
 
 
 class Tuning(ctypes.Structure):

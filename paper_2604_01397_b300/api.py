@@ -108,7 +108,9 @@ class Workspace:
         return dict(kernel_launches=int(st.kernel_launches), passes=int(st.passes),
                     total_critical=int(st.total_critical), sum_requests=int(st.sum_requests),
                     sum_tiles=int(st.sum_tiles), sum_pairs=int(st.sum_pairs),
-                    stage_ms={k: float(v) for k, v in zip(N.STAGES, st.stage_ms)})
+                    stage_ms={k: float(v) for k, v in zip(N.STAGES, st.stage_ms)},
+                    loop_kernel_ms={k: float(v) for k, v in zip(("check", "pairs", "apply"), st.loop_kernel_ms)},
+                    loop_passes=int(st.loop_passes))
 
     def tuning(self) -> dict:
         t = N.Tuning()

@@ -166,6 +166,7 @@ struct exactz_workspace {
     uint64_t layout_hash = 0;  // dims of the previous run (padding must hold k = 0, no CP bits)
     exactz_stats stats{};
     cudaEvent_t ev[9] = {};
+    cudaEvent_t kev[4] = {};  // around the loop kernels of one host-driven pass (profiling)
     Tuning tun;
 
     std::mutex mu;
@@ -194,6 +195,8 @@ void free_ws(exactz_workspace *ws)
     if (ws->graph) cudaGraphDestroy(ws->graph);
     if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
     for (cudaEvent_t e : ws->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ws->kev)
         if (e) cudaEventDestroy(e);
     for (void *p : ws->allocs) cudaFree(p);
     if (ws->st_f) cudaFree(ws->st_f);
@@ -275,6 +278,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     CK(cudaMallocHost(&ws->h_ls, sizeof(LoopState)));
     CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
     for (cudaEvent_t &e : ws->ev) CK(cudaEventCreate(&e));
+    for (cudaEvent_t &e : ws->kev) CK(cudaEventCreate(&e));
     return EXACTZ_OK;
 }
 
@@ -476,7 +480,8 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     const uint64_t P = (uint64_t)sort_passes(0, nf);
     const SetupRange R{0, L.total_tiles, 0, L.total_w / WBLOCK, 0, nf, 0, &ws->d_ls->total_cp};
     const FieldSet FS{ws->fids, nf, 0, L.total_v / VBLOCK, 0, nf};
-    uint64_t launches = 0;
+    uint64_t launches = 0, loop_passes = 0;
+    double loop_ms[3] = {0.0, 0.0, 0.0};
 
     // set-up and the first pass
     mark(0);
@@ -501,18 +506,26 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         for (;;) {
             CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            if (!ws->h_ls->any_active) break;
-            if (opt.mode == EXACTZ_MODE_PLAIN) {
-                launch_check_all(D, s);
-                launch_pairs_all(D, R, s);
-                launch_apply(D, 0, s);
-            } else {
-                launch_check_list(D, s);
-                launch_pairs_list(D, s);
-                launch_apply(D, 1, s);
+            if (prof && loop_passes) {  // the previous pass's kernels have run
+                for (int k = 0; k < 3; k++) {
+                    float t = 0.0f;
+                    cudaEventElapsedTime(&t, ws->kev[k], ws->kev[k + 1]);
+                    loop_ms[k] += t;
+                }
             }
+            if (!ws->h_ls->any_active) break;
+            if (prof) cudaEventRecord(ws->kev[0], s);
+            if (opt.mode == EXACTZ_MODE_PLAIN) launch_check_all(D, s);
+            else launch_check_list(D, s);
+            if (prof) cudaEventRecord(ws->kev[1], s);
+            if (opt.mode == EXACTZ_MODE_PLAIN) launch_pairs_all(D, R, s);
+            else launch_pairs_list(D, s);
+            if (prof) cudaEventRecord(ws->kev[2], s);
+            launch_apply(D, opt.mode == EXACTZ_MODE_PLAIN ? 0 : 1, s);
+            if (prof) cudaEventRecord(ws->kev[3], s);
             launch_book(D, 0, 0, s);
             launches += 4;
+            loop_passes++;
             CK(cudaGetLastError());
         }
     }
@@ -537,6 +550,8 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     ws->stats.sum_pairs = ws->h_ls->sum_pairs;
     if (opt.mode == EXACTZ_MODE_GRAPH) launches += 4 * (ws->h_ls->pass > 0 ? ws->h_ls->pass - 1 : 0);
     ws->stats.kernel_launches = launches;
+    ws->stats.loop_passes = loop_passes;
+    for (int k = 0; k < 3; k++) ws->stats.loop_kernel_ms[k] = (float)loop_ms[k];
     if (prof) {
         for (int i = 0; i < 7; i++) cudaEventElapsedTime(&ws->stats.stage_ms[i], ws->ev[i], ws->ev[i + 1]);
         cudaEventElapsedTime(&ws->stats.stage_ms[7], ws->ev[0], ws->ev[7]);
