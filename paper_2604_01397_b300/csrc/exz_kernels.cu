@@ -1,26 +1,30 @@
 // exz_kernels.cu -- sm_103a kernels of the EXaCTz correction (Algorithm 1).
 //
-//   k_stencil<SETUP>   per-vertex descriptor of f (steepest up/down rank, lower
-//                      link mask, saddle / critical flags; Sec. 3.2, Sec. 4.2),
-//                      input validation, g := f_hat, k := 0, critical-point
-//                      bitmap, and the first pass's EG / saddle-link checks.
-//   k_stencil<CHECK_*> EG constraints and saddle-link rule on the edited field
-//                      g (Sec. 4.2) for all tiles or the tiles touched by the
-//                      previous pass; emits decrease requests.
-//   k_cp_*             ordered compaction of critical points; stable LSD radix
-//                      sort by (field, value key) -> f's global CP order (Sec. 4.3).
-//   k_pairs            reformulated event constraint: adjacent CP pairs whose
-//                      g-order is reversed (Sec. 4.3).
-//   k_apply            bounded monotone edit (Sec. 3.3) of each requested vertex
-//                      once, frontier marking for the next pass.
-//   k_book             per-field convergence bookkeeping, device-side loop flag.
-//   k_finish/k_status  residual violations and final status.
-//   k_edit_*           ordered compaction of the edit list.
+//   k_stencil<SETUP>      per-vertex descriptor of f (steepest up/down rank,
+//                         lower link mask, saddle / critical flags; Sec. 3.2,
+//                         Sec. 4.2), input validation, g := f_hat, k := 0, the
+//                         critical-point bitmap and the first pass's checks.
+//   k_stencil<CHECK_*>    EG constraints and saddle-link rule on the edited
+//                         field g (Sec. 4.2) for every tile, the flagged tiles'
+//                         dirty vertices (frontier) or the pinned tiles
+//                         (residual); emits decrease requests.
+//   k_cp_*, k_sort_*      ordered compaction of critical points; stable LSD
+//                         radix sort by (field, value key) -> f's global CP
+//                         order (Sec. 4.3).
+//   k_pairs               reformulated event constraint: adjacent CP pairs
+//                         whose g-order is reversed (Sec. 4.3).
+//   k_apply_tiles         bounded monotone edit (Sec. 3.3) of each requested
+//                         vertex once; dirty bits and tile flags of the next pass.
+//   k_book, k_loop_flag   per-field convergence bookkeeping, device loop flag.
+//   k_status              residual violations and final status.
+//   k_edit_*              ordered compaction of the edit list.
 //
-// Requests are deduplicated by an atomic bitmap over the arena; a vertex is
-// edited at most once per pass (synchronous semantics, Sec. 4.4 proof).
-// Requests to pinned vertices (already at the lossless bound) may enter the
-// list; k_apply leaves them unchanged and they do not keep the loop running.
+// Requests are deduplicated by a bitmap of row words over the arena; a vertex
+// is edited at most once per pass (synchronous semantics, Sec. 4.4 proof).
+// Requests to pinned vertices (already at the lossless bound) may be set; the
+// apply kernel leaves them unchanged and they do not keep the loop running.
+// Tiles to check or to apply are flagged with plain byte stores (one byte per
+// tile); the consuming kernel takes and clears the flags.
 #include <cmath>
 #include <cstdio>
 
