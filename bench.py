@@ -168,9 +168,14 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources with comments and layout removed: it changes
+    when the code of a kernel does, not when a comment does."""
     h = hashlib.sha256()
     for fn in ("exz_kernels.cu", "exz_common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2604_01397_b300", "csrc", fn), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2604_01397_b300", "csrc", fn)).read()
+        src = re.sub(r"//[^\n]*", "", src)
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        h.update(re.sub(r"\s+", " ", src).strip().encode())
     return h.hexdigest()[:16]
 
 
