@@ -250,7 +250,7 @@ int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, flo
 
 /* A server corrects fields submitted one at a time from HOST memory.  It owns
  * one device arena planned from budget_bytes (about 1/8 for edit records, the
- * rest at 76 bytes per resident vertex) and a host thread that runs the passes
+ * rest at 60 bytes per resident vertex) and a host thread that runs the passes
  * of Algorithm 1 over every resident field at once.  At each pass boundary it
  * admits queued requests in submission order while a field slot and arena room
  * are free (a request that does not fit waits; later ones wait behind it),

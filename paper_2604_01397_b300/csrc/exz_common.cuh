@@ -140,12 +140,10 @@ struct FieldState {
 };
 
 struct LoopState {
-    unsigned long long pair_count[2];
     unsigned long long total_cp;
     unsigned long long sum_requests;  // requests applied or skipped, over all passes
     unsigned long long sum_tiles;     // tiles checked by frontier passes
     unsigned long long sum_pairs;     // CP pairs checked by frontier passes
-    uint32_t cur;
     uint32_t any_active;
     uint32_t pass;
     uint32_t overflow;
@@ -174,17 +172,15 @@ struct Dev {
     uint32_t *reqw;      // vertices requested this pass (row words)
     uint32_t *dirty;     // vertices whose closed star changed last pass (row words)
     float *gs;           // g of the critical points, in f's sorted order
-    uint32_t *pairbits;  // CP pairs already queued for the next pass
+    uint32_t *pairbits;  // CP pairs (q, q+1) to check next pass, bit q
     uint8_t *apply_flag;  // per tile: holds requested vertices (taken and cleared by the apply kernel)
     uint8_t *tile_flag;   // per tile: to check next pass (taken and cleared by the check kernel)
     uint32_t *pin_tile_bits;
-    uint32_t *pair_list[2];
     uint32_t *cp_key[2];
     unsigned long long *cp_ent[2];
     unsigned long long *o;  // sorted critical points (aliases one of cp_ent)
     const uint32_t *multi;  // 2^14-bit table: link subset has >= 2 components
     uint64_t cp_cap;
-    uint64_t pair_cap;
     // scratch for scans, histograms and block counts
     uint32_t *blk;
     unsigned long long *blk_off;

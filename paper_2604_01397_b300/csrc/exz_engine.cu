@@ -141,7 +141,7 @@ struct exactz_workspace {
     uint8_t *apply_flag = nullptr, *tile_flag = nullptr;
     float *gs = nullptr;
     uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
-    uint32_t *pair_list[2] = {nullptr, nullptr}, *pin_pair_arena = nullptr;
+    uint32_t *pin_pair_arena = nullptr;
     uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
@@ -252,8 +252,6 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->tile_flag, T);
     AL(ws->pin_tile_arena, T);
     AL(ws->pin_tile_bits, T / 32 + 1);
-    AL(ws->pair_list[0], 2 * C);
-    AL(ws->pair_list[1], 2 * C);
     AL(ws->pin_pair_arena, 2 * C);
     AL(ws->fids, L.nfields);
     AL(ws->cp_key[0], C);
@@ -302,8 +300,6 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.apply_flag = ws->apply_flag;
     D.tile_flag = ws->tile_flag;
     D.pin_tile_bits = ws->pin_tile_bits;
-    D.pair_list[0] = ws->pair_list[0];
-    D.pair_list[1] = ws->pair_list[1];
     D.cp_key[0] = ws->cp_key[0];
     D.cp_key[1] = ws->cp_key[1];
     D.cp_ent[0] = ws->cp_ent[0];
@@ -311,7 +307,6 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     D.o = ws->cp_ent[sort_passes(0, L.nfields) & 1];
     D.multi = ws->d_multi;
     D.cp_cap = ws->cap_real;
-    D.pair_cap = 2 * ws->cap_real;
     D.blk = ws->blk;
     D.blk_off = ws->blk_off;
     D.hist = ws->hist;
@@ -936,7 +931,6 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
               c.take(ws->cpwords, W) && c.take(ws->reqw, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
               c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_flag, T) && c.take(ws->tile_flag, T) &&
               c.take(ws->pin_tile_arena, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
-              c.take(ws->pair_list[0], 2 * C) && c.take(ws->pair_list[1], 2 * C) &&
               c.take(ws->pin_pair_arena, 2 * C) && c.take(ws->fids, L.nfields) && c.take(ws->cp_key[0], C) &&
               c.take(ws->cp_key[1], C) &&
               c.take(ws->cp_ent[0], C) && c.take(ws->cp_ent[1], C) && c.take(ws->blk, nblk) &&

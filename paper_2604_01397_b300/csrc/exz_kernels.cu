@@ -883,60 +883,95 @@ enum { PM_ALL = 0, PM_LIST = 1, PM_PINNED = 2 };
 // Rule R3 on adjacent pairs (q, q+1) of the sorted critical points, reading
 // their current values from gs (kept in sorted order by the apply kernel); the
 // sorted entries are gathered only to resolve a tie by index or to name the
-// target.  ALL: every pair (the first pass; pairs may straddle two fields).
-// LIST / PINNED: pairs queued by the apply kernel, always inside one field;
-// LIST also clears each pair's queued bit.  PINNED keeps pinned targets only.
-// ALL covers the CP segment [cp0, cp0 + *countp); PINNED the pinned-pair lists
-// of fields fids[0..nf).
+// target.  ALL: every pair of the CP segment [cp0, cp0 + *countp) (the first
+// pass; pairs may straddle two fields).  LIST: the pairs whose bit the apply
+// kernel set in pairbits (always inside one field); each warp scans whole
+// words, takes and clears them, and each lane checks the pair of its bit.
+// PINNED: the pinned-pair lists of fields fids[0..nf), pinned targets only.
 template <int PM>
 __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsigned long long *countp,
                                                const uint32_t *fids, uint32_t nf)
 {
-    const uint32_t nouter = PM == PM_PINNED ? nf : 1u;
-    for (uint32_t fi = 0; fi < nouter; fi++) {
-    unsigned long long count;
-    const uint32_t *list = nullptr;
-    if (PM == PM_ALL) {
-        const unsigned long long total = *countp;
-        count = total ? total - 1 : 0;
-    } else if (PM == PM_LIST) {
-        const uint32_t c = D.ls->cur;
-        count = D.ls->pair_count[c];
-        list = D.pair_list[c];
-    } else {
-        count = D.fst[fids[fi]].pin_pair_count;
-        list = D.fields[fids[fi]].pin_pairs;
-    }
-    // warp-uniform trip counts: the request's tile is queued by the whole warp
+    const int lane = threadIdx.x & 31;
+    // evaluate pair q; true (and the tile of the request) when its target is requested
+    auto check = [&](const unsigned long long q, uint32_t &tile) -> bool {
+        const float ga = D.gs[q], gb = D.gs[q + 1];
+        bool viol = gb < ga;
+        unsigned long long a = 0;
+        if (PM == PM_ALL || gb == ga) {
+            a = D.o[q];
+            const unsigned long long b = D.o[q + 1];
+            if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
+            else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
+        } else if (viol) {
+            a = D.o[q];
+        }
+        if (!viol) return false;
+        const FieldDesc &F = D.fields[a >> LOCAL_BITS];
+        const uint64_t t = a & LOCAL_MASK;
+        if (PM == PM_PINNED && (D.desc[F.vbase + t] >> D_K_SHIFT) <= F.N) return false;
+        tile = request_vertex(D, F, t);
+        return true;
+    };
     const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
-    for (unsigned long long j0 = (unsigned long long)blockIdx.x * CTA + (threadIdx.x & ~31u); j0 < count;
-         j0 += stride) {
-        const unsigned long long j = j0 + (threadIdx.x & 31);
-        bool viol = false;
-        uint32_t tile = 0;
-        if (j < count) {
-            const unsigned long long q = list ? (unsigned long long)list[j] : cp0 + j;
-            if (PM == PM_LIST) atomicAnd(&D.pairbits[q >> 5], ~(1u << (q & 31)));
-            const float ga = D.gs[q], gb = D.gs[q + 1];
-            viol = gb < ga;
-            unsigned long long a = 0;
-            if (PM == PM_ALL || gb == ga) {
-                a = D.o[q];
-                const unsigned long long b = D.o[q + 1];
-                if ((a >> LOCAL_BITS) != (b >> LOCAL_BITS)) viol = false;  // different fields
-                else if (gb == ga) viol = (b & LOCAL_MASK) < (a & LOCAL_MASK);
-            } else if (viol) {
-                a = D.o[q];
+    if (PM == PM_LIST) {
+        // each warp takes 32 consecutive words of pairbits at a time (one per
+        // lane), clears them, numbers their set bits and checks them 32 at once
+        const unsigned long long nwords = (D.cp_cap + 31) / 32;
+        const unsigned long long gw = ((unsigned long long)blockIdx.x * CTA + threadIdx.x) >> 5;
+        const unsigned long long nw = stride >> 5;
+        uint32_t npairs = 0;
+        for (unsigned long long c = gw; c * 32 < nwords; c += nw) {
+            const unsigned long long w = c * 32 + lane;
+            const uint32_t word = w < nwords ? D.pairbits[w] : 0u;
+            if (!__any_sync(0xffffffffu, word != 0)) continue;
+            if (word) D.pairbits[w] = 0;  // taken
+            const uint32_t cnt = __popc(word);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            if (viol) {
-                const FieldDesc &F = D.fields[a >> LOCAL_BITS];
-                const uint64_t t = a & LOCAL_MASK;
-                if (PM != PM_PINNED || (D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) tile = request_vertex(D, F, t);
-                else viol = false;
+            const uint32_t excl = incl - cnt;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            npairs += total;
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t k = base + lane;
+                int src = 0;  // the last lane whose first number is <= k
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t pe = __shfl_sync(0xffffffffu, excl, src + step);
+                    if (pe <= k) src += step;
+                }
+                const uint32_t rword = __shfl_sync(0xffffffffu, word, src);
+                const uint32_t rpre = __shfl_sync(0xffffffffu, excl, src);
+                uint32_t tile = 0;
+                if (k < total) {
+                    const unsigned long long q = (c * 32 + src) * 32 + nth_set_bit(rword, (int)(k - rpre));
+                    if (check(q, tile) && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
+                }
             }
         }
-        if (viol && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
+        if (lane == 0 && npairs) atomicAdd(&D.ls->sum_pairs, (unsigned long long)npairs);
+        return;
     }
+    const uint32_t nouter = PM == PM_PINNED ? nf : 1u;
+    for (uint32_t fi = 0; fi < nouter; fi++) {
+        unsigned long long count;
+        const uint32_t *list = nullptr;
+        if (PM == PM_ALL) {
+            const unsigned long long total = *countp;
+            count = total ? total - 1 : 0;
+        } else {
+            count = D.fst[fids[fi]].pin_pair_count;
+            list = D.fields[fids[fi]].pin_pairs;
+        }
+        for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
+            uint32_t tile = 0;
+            if (check(list ? (unsigned long long)list[j] : cp0 + j, tile) && !D.apply_flag[tile])
+                D.apply_flag[tile] = 1;
+        }
     }
 }
 
@@ -959,26 +994,26 @@ __device__ __forceinline__ unsigned long long warp_reserve(uint32_t c, unsigned 
     return base + (x - c);
 }
 
-// Queue the tiles other than `own` holding the closed star of vertex (x, y, z)
-// of tile `own`: the star's negative offsets are the non-zero vectors of
-// {0,-1}^3 and its positive ones those of {0,1}^3, so the other tiles it
-// reaches are, on each side, the non-zero combinations of the tile faces the
-// vertex lies on.
-__device__ __forceinline__ void mark_face_tiles(uint32_t own, uint32_t x, uint32_t y, uint32_t z, uint32_t nx,
-                                                uint32_t ny, uint32_t nz, uint32_t tnx, uint32_t tny, uint32_t *bits,
-                                                uint32_t *list, unsigned long long *count)
+// The tiles holding the closed star of vertex (x, y, z), as a 27-bit mask of
+// neighbour tiles (bit (ox+1) + 3 (oy+1) + 9 (oz+1); bit 13 = the vertex's own
+// tile): the star's negative offsets are the non-zero vectors of {0,-1}^3 and
+// its positive ones those of {0,1}^3, so on each side the other tiles it
+// reaches are the non-zero combinations of the tile faces the vertex lies on.
+__device__ __forceinline__ uint32_t star_tiles(uint32_t x, uint32_t y, uint32_t z, uint32_t nx, uint32_t ny,
+                                               uint32_t nz)
 {
     const uint32_t lo = ((x % TX) == 0 && x > 0 ? 1u : 0u) | ((y % TY) == 0 && y > 0 ? 2u : 0u) |
                         ((z % TZ) == 0 && z > 0 ? 4u : 0u);
     const uint32_t hi = ((x % TX) == TX - 1 && x + 1 < nx ? 1u : 0u) | ((y % TY) == TY - 1 && y + 1 < ny ? 2u : 0u) |
                         ((z % TZ) == TZ - 1 && z + 1 < nz ? 4u : 0u);
-    const uint32_t sy = tnx, sz = tnx * tny;
+    uint32_t nb = 1u << 13;
 #pragma unroll 1
     for (uint32_t m = lo; m; m = (m - 1) & lo)
-        mark_tile(bits, list, count, own - (m & 1u) - ((m >> 1) & 1u) * sy - ((m >> 2) & 1u) * sz);
+        nb |= 1u << (13 - (int)(m & 1u) - 3 * (int)((m >> 1) & 1u) - 9 * (int)((m >> 2) & 1u));
 #pragma unroll 1
     for (uint32_t m = hi; m; m = (m - 1) & hi)
-        mark_tile(bits, list, count, own + (m & 1u) + ((m >> 1) & 1u) * sy + ((m >> 2) & 1u) * sz);
+        nb |= 1u << (13 + (int)(m & 1u) + 3 * (int)((m >> 1) & 1u) + 9 * (int)((m >> 2) & 1u));
+    return nb;
 }
 
 enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
@@ -1002,18 +1037,29 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
     __shared__ uint32_t s_cw_all[WARPS][ROWS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *s_cw = s_cw_all[warp];
-    const uint32_t nxt = D.ls->cur ^ 1u;
     unsigned long long nreq = 0;
     uint32_t pb, pe, pst;
     work_range(D, D.total_tiles, blockIdx.x * WARPS + warp, gridDim.x * WARPS, pb, pe, pst);
-    for (uint64_t p = pb; p < pe; p += 32ull * pst) {
-    const uint64_t ti = p + (uint64_t)lane * pst;
-    const bool flagged = ti < pe && D.apply_flag[ti] != 0;
-    if (flagged) D.apply_flag[ti] = 0;
-    uint32_t pend = __ballot_sync(0xffffffffu, flagged);
-    while (pend) {
-        const uint32_t tile = (uint32_t)(p + (uint64_t)(__ffs(pend) - 1) * pst);
+    // The warp's flagged tiles, one at a time: probe 32 flags at once and take
+    // the flagged ones.
+    uint64_t p = pb;
+    uint64_t pbase = 0;
+    uint32_t pend = 0;
+    auto next_tile = [&]() -> uint32_t {
+        while (!pend && p < pe) {
+            const uint64_t ti = p + (uint64_t)lane * pst;
+            const bool flagged = ti < pe && D.apply_flag[ti] != 0;
+            if (flagged) D.apply_flag[ti] = 0;
+            pend = __ballot_sync(0xffffffffu, flagged);
+            pbase = p;
+            p += 32ull * pst;
+        }
+        if (!pend) return NO_TILE;
+        const uint32_t t = (uint32_t)(pbase + (uint64_t)(__ffs(pend) - 1) * pst);
         pend &= pend - 1;
+        return t;
+    };
+    for (uint32_t tile = next_tile(); tile != NO_TILE; tile = next_tile()) {
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
         FieldState *S = &D.fst[fid];
@@ -1022,7 +1068,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         const uint32_t rest = lt / tnx, tx = lt - rest * tnx, tz = rest / tny, ty = rest - tz * tny;
         const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
         const uint64_t vbase = F.vbase, wbase = F.wbase;
-        uint32_t W = 0;  // lane r < ROWS: request word of tile row r
+        uint32_t W = 0;  // lane r < ROWS: request word of tile row r (taken: read and cleared)
         if (lane < ROWS) {
             const uint32_t y = y0 + lane % TY, z = z0 + lane / TY;
             if (y < ny && z < nz) {
@@ -1048,7 +1094,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         }
         __syncwarp();
         const bool err = S->err != 0, capped = S->iterations >= F.max_iters;
-        uint32_t ncap = 0;
+        uint32_t ncap = 0, pin_nb = 0;
         for (int base = 0; base < nvisit; base += 32) {
             const int k = base + lane;
             const bool sel = k < nvisit && !err;
@@ -1110,20 +1156,9 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                     }
                 }
             }
-            if (AM == AM_FRONTIER && __any_sync(0xffffffffu, has_lo || has_hi)) {
-                bool new_lo = false, new_hi = false;
-                if (has_hi) {
-                    const uint32_t bit = 1u << (q & 31);
-                    new_hi = !(atomicOr(&D.pairbits[q >> 5], bit) & bit);
-                }
-                if (has_lo) {
-                    const unsigned long long p0 = q - 1;
-                    const uint32_t bit = 1u << (p0 & 31);
-                    new_lo = !(atomicOr(&D.pairbits[p0 >> 5], bit) & bit);
-                }
-                const unsigned long long p = warp_reserve((uint32_t)new_hi + (uint32_t)new_lo, &D.ls->pair_count[nxt]);
-                if (new_hi) D.pair_list[nxt][p] = (uint32_t)q;
-                if (new_lo) D.pair_list[nxt][p + (new_hi ? 1 : 0)] = (uint32_t)(q - 1);
+            if (AM == AM_FRONTIER) {  // the pairs (q, q+1) and (q-1, q) are checked next pass
+                if (has_hi) atomicOr(&D.pairbits[q >> 5], 1u << (q & 31));
+                if (has_lo) atomicOr(&D.pairbits[(q - 1) >> 5], 1u << ((q - 1) & 31));
             }
             const uint32_t npp = pinned ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
             if (__any_sync(0xffffffffu, npp != 0)) {
@@ -1131,12 +1166,17 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                 if (pinned && has_hi) F.pin_pairs[p] = (uint32_t)q;
                 if (pinned && has_lo) F.pin_pairs[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
             }
-            // the residual check revisits the closed stars of pinned vertices:
-            // this tile (queued once per warp) and the tiles across its faces
-            const bool any_pinned = __any_sync(0xffffffffu, pinned);
-            warp_mark_tiles(lane == 0 && any_pinned, tile, D.pin_tile_bits, F.pin_tiles, &S->pin_tile_count);
-            if (pinned) mark_face_tiles(tile, x, y, z, nx, ny, nz, tnx, tny, D.pin_tile_bits, F.pin_tiles,
-                                        &S->pin_tile_count);
+            if (pinned) pin_nb |= star_tiles(x, y, z, nx, ny, nz);
+        }
+        // the residual check revisits the closed stars of pinned vertices: their
+        // tiles are queued once per tile, one lane per neighbour tile
+        pin_nb = __reduce_or_sync(0xffffffffu, pin_nb);
+        if (pin_nb) {
+            const int j = lane;
+            const int ox = j % 3 - 1, oy = (j / 3) % 3 - 1, oz = j / 9 - 1;
+            warp_mark_tiles(j < 27 && ((pin_nb >> j) & 1u),
+                            (uint32_t)((int64_t)tile + ox + (int64_t)tnx * (oy + (int64_t)tny * oz)), D.pin_tile_bits,
+                            F.pin_tiles, &S->pin_tile_count);
         }
         __syncwarp();
         const uint32_t cw = lane < ROWS ? s_cw[lane] : 0u;
@@ -1198,7 +1238,6 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         }
         __syncwarp();
     }
-    }
     if (AM != AM_COUNT && lane == 0 && nreq) atomicAdd(&D.ls->sum_requests, nreq);
 }
 
@@ -1226,10 +1265,6 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
     __syncthreads();
     if (threadIdx.x == 0) {
         LoopState *L = D.ls;
-        const uint32_t c = L->cur;
-        L->sum_pairs += L->pair_count[c];
-        L->pair_count[c] = 0;
-        L->cur = c ^ 1u;
         L->pass += 1;
         L->any_active = s_any;
         if (use_graph) cudaGraphSetConditional(h, s_any ? 1u : 0u);

@@ -123,7 +123,7 @@ struct exactz_server {
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
     float *gs = nullptr;
-    uint32_t *pairbits = nullptr, *pair_list[2] = {nullptr, nullptr}, *pin_pair_arena = nullptr;
+    uint32_t *pairbits = nullptr, *pin_pair_arena = nullptr;
     EditRec *edits = nullptr;
     uint32_t *blk = nullptr;
     unsigned long long *blk_off = nullptr;
@@ -208,8 +208,6 @@ Dev server_dev(const exactz_server *S)
     D.apply_flag = S->apply_flag;
     D.tile_flag = S->tile_flag;
     D.pin_tile_bits = S->pin_tile_bits;
-    D.pair_list[0] = S->pair_list[0];
-    D.pair_list[1] = S->pair_list[1];
     D.cp_key[0] = S->cp_key[0];
     D.cp_key[1] = S->cp_key[1];
     D.cp_ent[0] = S->cp_ent[0];
@@ -217,7 +215,6 @@ Dev server_dev(const exactz_server *S)
     D.o = S->cp_ent[sort_passes(0, 1) & 1];  // every set-up sorts one field
     D.multi = S->d_multi;
     D.cp_cap = S->C;
-    D.pair_cap = 2 * S->C;
     D.blk = S->blk;
     D.blk_off = S->blk_off;
     D.hist = S->hist;
@@ -499,12 +496,12 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
     S->slots = cfg->max_fields;
     S->opts = o;
     // Arena capacities from the budget: 1/8 for edit records, the rest at
-    // 76 bytes per resident vertex (f, f_hat, g, descriptor, CP rank: 20; one
-    // CP entry per vertex for keys, entries, sorted values, pair lists: 52;
+    // 60 bytes per resident vertex (f, f_hat, g, descriptor, CP rank: 20; one
+    // CP slot per vertex for keys, entries, sorted values, pinned pairs: 36;
     // row words, tiles and rounding: the rest).
     const uint64_t B = cfg->budget_bytes;
     S->E = B / 8 / sizeof(EditRec);
-    S->V = (B - S->E * sizeof(EditRec)) / 76 / VBLOCK * VBLOCK;
+    S->V = (B - S->E * sizeof(EditRec)) / 60 / VBLOCK * VBLOCK;
     S->C = S->V;
     S->W = rup(S->V / 16 + (uint64_t)S->slots * WBLOCK, WBLOCK);
     S->T = rup(S->V / 256 + (uint64_t)S->slots * 32, 32);
@@ -519,8 +516,7 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
               salloc(S, S->pin_tile_bits, T / 32 + 1) && salloc(S, S->pin_tile_arena, T) &&
               salloc(S, S->tile_field, T) && salloc(S, S->cp_key[0], C) && salloc(S, S->cp_key[1], C) &&
               salloc(S, S->cp_ent[0], C) && salloc(S, S->cp_ent[1], C) && salloc(S, S->gs, C) &&
-              salloc(S, S->pairbits, C / 32 + 1) && salloc(S, S->pair_list[0], 2 * C) &&
-              salloc(S, S->pair_list[1], 2 * C) && salloc(S, S->pin_pair_arena, 2 * C) &&
+              salloc(S, S->pairbits, C / 32 + 1) && salloc(S, S->pin_pair_arena, 2 * C) &&
               salloc(S, S->edits, S->E) && salloc(S, S->blk, nblk) && salloc(S, S->blk_off, nblk) &&
               salloc(S, S->hist, 256ull * S->sort_blocks) && salloc(S, S->d_retire, S->slots);
     ok = ok && cudaMallocHost(&S->h_fst, sizeof(FieldState) * S->slots) == cudaSuccess &&

@@ -98,14 +98,14 @@ def test_server_equals_frontier_entry_point():
 def test_budget_limits_residency_and_refuses_oversized():
     import paper_2604_01397_b300 as ez
 
-    with ez.Server(budget_bytes=64 << 20, max_fields=8) as s:
+    with ez.Server(budget_bytes=96 << 20, max_fields=8) as s:
         cap = s.stats()["capacity_vertices"]
-        # two 64^3 fields fit the arena at once, three do not
-        assert 2 * 64 ** 3 <= cap < 3 * 64 ** 3
-        big = torch.zeros(96 ** 3, dtype=torch.float32)
+        # two 80^3 fields fit the arena at once, three do not
+        assert 2 * 80 ** 3 <= cap < 3 * 80 ** 3
+        big = torch.zeros(120 ** 3, dtype=torch.float32)
         with pytest.raises(ez.ExactzError, match="ESIZE"):
-            s.submit(big, big, 0.1, dims=(96, 96, 96))
-        fields = _fields([((64, 64, 64), 30 + i, "uniform", 1e-3) for i in range(5)])
+            s.submit(big, big, 0.1, dims=(120, 120, 120))
+        fields = _fields([((80, 80, 80), 30 + i, "uniform", 1e-3) for i in range(5)])
         tickets = [s.submit(f, fh, xi, dims=dims, edits_cap=1 << 16) for dims, f, fh, xi in fields]
         got = [_wait(s, t) for t in tickets]
         st = s.stats()
