@@ -114,7 +114,8 @@ struct FieldDesc {
     uint64_t edits_cap;
     uint32_t *pin_tiles;    // tiles around this field's pinned vertices (capacity: its tile count)
     uint32_t *pin_pairs;    // CP pairs next to its pinned critical points (capacity: 2 n)
-    FastDiv div_nx, div_ny;  // x = t mod nx, row = t / nx, z = row / ny (fields below 2^32 vertices)
+    FastDiv div_nx, div_ny;    // x = t mod nx, row = t / nx, z = row / ny (fields below 2^32 vertices)
+    FastDiv div_tnx, div_tny;  // the same for tile coordinates
 };
 
 // One applied edit; same layout as exactz_edit (16 bytes).

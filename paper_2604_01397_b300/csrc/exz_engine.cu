@@ -103,6 +103,8 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
         F.tbase = t;
         F.div_nx = make_fastdiv(F.nx);
         F.div_ny = make_fastdiv(F.ny);
+        F.div_tnx = make_fastdiv(F.tnx);
+        F.div_tny = make_fastdiv(F.tny);
         t += (uint64_t)F.tnx * F.tny * F.tnz;
         v = round_up(v, VBLOCK);
         F.vbase = v;

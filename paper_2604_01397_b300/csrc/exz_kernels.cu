@@ -252,9 +252,9 @@ __device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
     G.fid = field_of_tile(D, tile);
     const FieldDesc &F = D.fields[G.fid];
     const uint32_t lt = (uint32_t)(tile - F.tbase);
-    const uint32_t rest = lt / F.tnx;
+    const uint32_t rest = fdiv(lt, F.div_tnx);
     G.tx = lt - rest * F.tnx;
-    const uint32_t tz = rest / F.tny, ty = rest - tz * F.tny;
+    const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * F.tny;
     G.x0 = (int)(G.tx * TX);
     G.y0 = (int)(ty * TY);
     G.z0 = (int)(tz * TZ);
@@ -267,21 +267,20 @@ __device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
 // Tiles come from [t0, t1) (SETUP, CHECK_ALL, CLASSIFY), the set bits of
 // tile_flag (CHECK_LIST, taken and cleared 32 candidates at a time), or the
 // pinned-tile lists of fields fids[0..nf) (PINNED).
-// The modes that read one array stage the next tile with cp.async into a
-// second buffer while the current one is checked; SETUP (two arrays) loads
-// each tile directly.
+// The next tile is staged with cp.async into a second buffer while the
+// current one is checked.
 template <int MODE>
 __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
                                                       uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
-    constexpr bool PIPE = MODE != SM_SETUP;
-    constexpr int NB = PIPE ? 2 : 1;
+    constexpr int NB = 2;
     __shared__ __align__(16) float sa[NB][HALO_N];
-    __shared__ __align__(16) float sb[MODE == SM_SETUP ? HALO_N : 1];
+    __shared__ __align__(16) float sb[MODE == SM_SETUP ? NB : 1][MODE == SM_SETUP ? HALO_N : 4];
     __shared__ uint32_t smulti[512];
     __shared__ TileTargets tt;
     __shared__ uint32_t s_err;
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
+    __shared__ uint8_t s_vis[MODE == SM_CHECK_LIST ? STWARPS : 1][TY * TX];  // a warp's dirty vertices (ly << 5 | lx)
     __shared__ uint32_t s_tile[2];        // the tile staged in each buffer
     __shared__ TileGeo s_geo[NB];         // its position
 
@@ -310,20 +309,32 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
         const float *B = F.fhat;
         const bool interior = G.x0 >= 1 && G.x0 + TX < (int)nx && G.y0 >= 1 && G.y0 + TY < (int)ny && G.z0 >= 1 &&
                               G.z0 + TZ < (int)nz;
-        if (PIPE && interior && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (nx & 3u) == 0) {
+        const bool aligned = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) &&
+                             (MODE != SM_SETUP || (reinterpret_cast<uintptr_t>(B) & 15u) == 0);
+        if (interior && aligned && (nx & 3u) == 0) {
             // every halo value is inside the field and each row's tile values
             // start on 16 bytes: 8 copies of 16 bytes per row plus its two ends
             const uint64_t nxy = (uint64_t)nx * ny;
-            const float *base = A + ((uint64_t)(G.z0 - 1) * ny + (uint64_t)(G.y0 - 1)) * nx + G.x0;
+            const uint64_t corner = ((uint64_t)(G.z0 - 1) * ny + (uint64_t)(G.y0 - 1)) * nx + G.x0;
+            const float *base = A + corner;
+            const float *base_b = B + corner;
             constexpr int PARTS = TX / 4 + 2;
             for (int j = threadIdx.x; j < HY * HZ * PARTS; j += SCTA) {
                 const int row = j / PARTS, part = j - row * PARTS;
                 const int hz = row / HY, hy = row - hz * HY;
-                const float *g = base + (uint64_t)hz * nxy + (uint64_t)hy * nx;
+                const uint64_t off = (uint64_t)hz * nxy + (uint64_t)hy * nx;
+                const float *g = base + off;
                 float *sr = sa[b] + row * HXP + XOFF;
                 if (part < TX / 4) cp_async16(sr + 4 * part, g + 4 * part);
                 else if (part == TX / 4) cp_async4(sr - 1, g - 1);
                 else cp_async4(sr + TX, g + TX);
+                if (MODE == SM_SETUP) {
+                    const float *h = base_b + off;
+                    float *tr = sb[b] + row * HXP + XOFF;
+                    if (part < TX / 4) cp_async16(tr + 4 * part, h + 4 * part);
+                    else if (part == TX / 4) cp_async4(tr - 1, h - 1);
+                    else cp_async4(tr + TX, h + TX);
+                }
             }
             return;
         }
@@ -336,20 +347,19 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
             const bool in0 = rin && X0 >= 0 && X0 < (int)nx;
             const bool in1 = rin && lane < 2 && X1 < (int)nx;
             float *sr = sa[b] + row * HXP + (XOFF - 1);  // slot of x0 - 1
-            if (PIPE) {
-                if (in0) cp_async4(sr + lane, A + rb + X0);
-                else sr[lane] = qnan;
+            if (in0) cp_async4(sr + lane, A + rb + X0);
+            else sr[lane] = qnan;
+            if (lane < 2) {
+                if (in1) cp_async4(sr + TX + lane, A + rb + X1);
+                else sr[TX + lane] = qnan;
+            }
+            if (MODE == SM_SETUP) {
+                float *tr = sb[b] + row * HXP + (XOFF - 1);
+                if (in0) cp_async4(tr + lane, B + rb + X0);
+                else tr[lane] = qnan;
                 if (lane < 2) {
-                    if (in1) cp_async4(sr + TX + lane, A + rb + X1);
-                    else sr[TX + lane] = qnan;
-                }
-            } else {
-                sr[lane] = in0 ? A[rb + X0] : qnan;
-                if (lane < 2) sr[TX + lane] = in1 ? A[rb + X1] : qnan;
-                if (MODE == SM_SETUP) {
-                    float *tr = sb + row * HXP + (XOFF - 1);
-                    tr[lane] = in0 ? B[rb + X0] : qnan;
-                    if (lane < 2) tr[TX + lane] = in1 ? B[rb + X1] : qnan;
+                    if (in1) cp_async4(tr + TX + lane, B + rb + X1);
+                    else tr[TX + lane] = qnan;
                 }
             }
         }
@@ -366,44 +376,41 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
         const float *S = sa[b];
         const uint32_t *RW = s_rw[b];
         // CHECK_LIST: warp w visits the dirty vertices of the four rows of
-        // z-slab w, numbered by a prefix sum over those rows (lanes 0-3)
-        uint32_t myw = 0, pre = 0, e1 = 0, e2 = 0, e3 = 0;
-        int nvisit = ROWS * TX;
+        // z-slab w, listed in shared memory (each lane writes its own bits)
+        int nvisit = 0;
         if (MODE == SM_CHECK_LIST) {
             if (threadIdx.x < ROWS && RW[threadIdx.x]) {  // the dirty bits are taken: clear them
                 const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
                 D.dirty[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = 0;
             }
-            myw = lane < TY ? RW[warp * TY + lane] : 0u;
-            const uint32_t cnt = __popc(myw);
-            uint32_t incl = cnt;
+            uint8_t *vis = s_vis[MODE == SM_CHECK_LIST ? warp : 0];
+            int cnt = 0;
 #pragma unroll
-            for (int o = 1; o < TY; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+            for (int r = 0; r < TY; r++) {
+                const uint32_t w = RW[warp * TY + r];
+                if ((w >> lane) & 1u) vis[cnt + __popc(w & lanemask_lt())] = (uint8_t)((r << 5) | lane);
+                cnt += __popc(w);
             }
-            pre = incl - cnt;
-            e1 = __shfl_sync(0xffffffffu, pre, 1);
-            e2 = __shfl_sync(0xffffffffu, pre, 2);
-            e3 = __shfl_sync(0xffffffffu, pre, 3);
-            nvisit = (int)__shfl_sync(0xffffffffu, incl, TY - 1);
+            __syncwarp();
+            nvisit = cnt;
         }
+        // index of this warp's first vertex (x0, y0, z0 + warp) in the field
+        const uint64_t wfirst = ((uint64_t)(z0 + warp) * ny + (uint64_t)y0) * nx + (uint64_t)x0;
         const bool interior = x0 >= 1 && x0 + TX < (int)nx && y0 >= 1 && y0 + TY < (int)ny && z0 >= 1 &&
                               z0 + TZ < (int)nz;
         // vertices of this tile to visit: all rows (one warp per row) or the warp's dirty vertices
-        for (int base = (MODE == SM_CHECK_LIST ? 0 : warp * TX); base < nvisit;
-             base += (MODE == SM_CHECK_LIST ? 32 : STWARPS * TX)) {
+        // (all modes: warp w takes the rows of z-slab w)
+        const int vend = MODE == SM_CHECK_LIST ? nvisit : (warp + 1) * TY * TX;
+        for (int base = (MODE == SM_CHECK_LIST ? 0 : warp * TY * TX); base < vend;
+             base += (MODE == SM_CHECK_LIST ? 32 : TX)) {
             int lx, ly, lz;
             bool sel = true;
             if (MODE == SM_CHECK_LIST) {
                 const int k = base + lane;
                 sel = k < nvisit;
-                // the last of the warp's rows whose first number is <= k
-                const int r = (k >= (int)e1) + (k >= (int)e2) + (k >= (int)e3);
-                const uint32_t rword = __shfl_sync(0xffffffffu, myw, r);
-                const uint32_t rpre = __shfl_sync(0xffffffffu, pre, r);
-                lx = sel ? nth_set_bit(rword, k - (int)rpre) : 0;
-                ly = r;
+                const uint32_t code = sel ? s_vis[MODE == SM_CHECK_LIST ? warp : 0][k] : 0u;
+                lx = (int)(code & 31u);
+                ly = (int)(code >> 5);
                 lz = warp;
             } else {
                 const int rr = base / TX;
@@ -412,11 +419,11 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
                 lz = rr / TY;
             }
             const uint32_t x = (uint32_t)(x0 + lx), y = (uint32_t)(y0 + ly), z = (uint32_t)(z0 + lz);
-            const bool in = sel && x < nx && y < ny && z < nz;
+            const bool in = sel && (interior || (x < nx && y < ny && z < nz));
             const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lx + XOFF);
             bool cp = false;
             uint32_t req = 0;
-            const uint64_t i = ((uint64_t)z * ny + y) * nx + x;
+            const uint64_t i = wfirst + (uint64_t)ly * nx + (uint64_t)lx;  // lz == warp
             if (in) {
                 if (MODE == SM_SETUP || MODE == SM_CLASSIFY) {
                     Stn sf = interior ? stencil15<true>(S, c) : stencil15<false>(S, c);
@@ -432,14 +439,15 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
                         if (type_out)
                             type_out[i] = (uint8_t)(mn ? 1 : (mxx ? 2 : ((join ? 4 : 0) | (split ? 8 : 0))));
                     } else {
-                        const float fv = S[c], hv = sb[c];
+                        const float *SB = sb[b];
+                        const float fv = S[c], hv = SB[c];
                         uint32_t e = 0;
                         if (!isfinite(fv) || !isfinite(hv)) e = ERR_NONFINITE;
                         else if (hv < __fsub_rn(fv, F.xi) || hv > __fadd_rn(fv, F.xi)) e = ERR_BOUND;
                         if (e) atomicOr(&s_err, e);
                         D.desc[vbase + i] = d;  // edit count k = 0 in the top byte
                         F.g[i] = hv;
-                        Stn sg = interior ? stencil15<true>(sb, c) : stencil15<false>(sb, c);
+                        Stn sg = interior ? stencil15<true>(SB, c) : stencil15<false>(SB, c);
                         req = request_mask(smulti, d, sg);
                     }
                 } else {
@@ -463,18 +471,6 @@ __global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out,
         }
         if (MODE == SM_CLASSIFY) __syncthreads();
     };
-
-    if (!PIPE) {
-        unsigned long long it0, it1, its;
-        tile_range(D, t1 - t0, it0, it1, its);
-        for (unsigned long long it = it0; it < it1; it += its) {
-            const uint32_t tile = t0 + (uint32_t)it;
-            stage(tile, 0);
-            __syncthreads();
-            process(tile, 0);
-        }
-        return;
-    }
 
     // Tile source, advanced by warp 0; its state lives in shared memory so that
     // it holds no registers while tiles are checked.
@@ -1065,7 +1061,8 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         FieldState *S = &D.fst[fid];
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny, N = F.N;
         const uint32_t lt = (uint32_t)(tile - F.tbase);
-        const uint32_t rest = lt / tnx, tx = lt - rest * tnx, tz = rest / tny, ty = rest - tz * tny;
+        const uint32_t rest = fdiv(lt, F.div_tnx), tx = lt - rest * tnx;
+        const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * tny;
         const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
         const uint64_t vbase = F.vbase, wbase = F.wbase;
         uint32_t W = 0;  // lane r < ROWS: request word of tile row r (taken: read and cleared)
@@ -1429,7 +1426,7 @@ int device_sms() { return sms(); }
 
 void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
-    k_stencil<SM_SETUP><<<grid_for(R.tile1 - R.tile0, 1, 16), SCTA, 0, s>>>(D, nullptr, nullptr, R.tile0, R.tile1,
+    k_stencil<SM_SETUP><<<grid_for(R.tile1 - R.tile0, 1, 8), SCTA, 0, s>>>(D, nullptr, nullptr, R.tile0, R.tile1,
                                                                           nullptr, 0);
 }
 void launch_check_all(const Dev &D, cudaStream_t s)

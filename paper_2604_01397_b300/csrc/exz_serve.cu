@@ -241,6 +241,8 @@ bool geometry(const exactz_dims &d, FieldDesc &F, uint64_t &nw, uint64_t &nt)
     F.tnz = (uint32_t)((nz + TZ - 1) / TZ);
     F.div_nx = make_fastdiv(F.nx);
     F.div_ny = make_fastdiv(F.ny);
+    F.div_tnx = make_fastdiv(F.tnx);
+    F.div_tny = make_fastdiv(F.tny);
     nw = ny * nz * F.tnx;
     nt = (uint64_t)F.tnx * F.tny * F.tnz;
     return true;
