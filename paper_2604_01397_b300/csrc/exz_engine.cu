@@ -722,17 +722,19 @@ int exactz_ws_autotune(exactz_workspace *ws, uint32_t nfields, const float *cons
     float best = 0.f;
     if (!rc) rc = time_one(best);  // also warms the graph and caches
     if (!rc) rc = time_one(best);
-    static const uint32_t bps[] = {4, 8, 16, 32};
-    static const uint32_t pbps[] = {2, 4, 8, 16};
+    // candidates per knob: blocks per SM of the check (12 resident), apply (4
+    // resident) and pair kernels, and the schedule
+    static const uint32_t cands[4][5] = {{6, 12, 24, 36, 48}, {4, 8, 16, 32, 0}, {2, 4, 8, 16, 0}, {0, 1, 0, 0, 0}};
+    static const int ncand[4] = {5, 4, 4, 2};
     for (int knob = 0; knob < 4 && !rc; knob++) {
-        const int nc = knob == 3 ? 2 : 4;
+        const int nc = ncand[knob];
         Tuning keep = ws->tun;
         for (int c = 0; c < nc && !rc; c++) {
             Tuning cand = keep;
-            if (knob == 0) cand.stencil_bps = bps[c];
-            else if (knob == 1) cand.apply_bps = bps[c];
-            else if (knob == 2) cand.pairs_bps = pbps[c];
-            else cand.chunked = (uint32_t)c;
+            if (knob == 0) cand.stencil_bps = cands[0][c];
+            else if (knob == 1) cand.apply_bps = cands[1][c];
+            else if (knob == 2) cand.pairs_bps = cands[2][c];
+            else cand.chunked = cands[3][c];
             if (std::memcmp(&cand, &keep, sizeof(Tuning)) == 0) continue;
             {
                 std::lock_guard<std::mutex> lk(ws->mu);

@@ -40,7 +40,7 @@ static_assert(TX == 32, "one row word (and one warp) per tile row");
 static_assert(CTA % 32 == 0 && ROWS <= 32, "tile-row prefix sums run in one warp");
 // The tile-stencil kernel runs smaller blocks than the others, so that more
 // tiles are in flight per SM (its time goes mostly to memory latency per tile).
-constexpr int SCTA = 128, STWARPS = SCTA / 32;
+constexpr int SCTA = 128, STWARPS = SCTA / 32;  // 12 blocks per SM: 40 registers, no spills
 static_assert(SCTA % 32 == 0 && SCTA >= 32 && SCTA >= ROWS, "stencil blocks: whole warps, one thread per tile row");
 static_assert(STWARPS == TZ && TY <= 32, "frontier check: warp w visits the dirty vertices of z-slab w");
 static_assert(WBLOCK % CTA == 0 && VBLOCK % (4 * CTA) == 0, "compaction and edit-list blocks");
@@ -270,7 +270,7 @@ __device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
 // The next tile is staged with cp.async into a second buffer while the
 // current one is checked.
 template <int MODE>
-__global__ void __launch_bounds__(SCTA, 16) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
+__global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
                                                       uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
     constexpr int NB = 2;

@@ -223,7 +223,8 @@ def test_launch_schedule_never_changes_results():
                 for r, ref, c in zip(ws.correct(fs, fhs, xis, mode=mode), refs, cases):
                     assert_same(r, ref, c[0].size)
         t = ws.autotune(fs, fhs, xis, repeats=1)
-        assert t["stencil_blocks_per_sm"] in (4, 8, 16, 32) and t["chunked_schedule"] in (0, 1)
+        # a candidate, or the schedule the search started from (the last one set)
+        assert t["stencil_blocks_per_sm"] in (6, 12, 24, 36, 48, 16) and t["chunked_schedule"] in (0, 1)
         assert t["best_ms"] > 0 and ws.tuning()["apply_blocks_per_sm"] == t["apply_blocks_per_sm"]
         for r, ref, c in zip(ws.correct(fs, fhs, xis), refs, cases):
             assert_same(r, ref, c[0].size)
