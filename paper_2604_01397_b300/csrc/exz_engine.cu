@@ -233,7 +233,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     ws->cap_w = L.total_w;
     ws->cap_real = L.total_real;
     ws->cap_tiles = L.total_tiles;
-    ws->sort_blocks = (uint32_t)nsm * 8;
+    ws->sort_blocks = (uint32_t)nsm * 2;
     const uint64_t V = L.total_v, W = L.total_w, T = L.total_tiles, C = L.total_real;
     const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
     int rc = EXACTZ_OK;
@@ -929,7 +929,7 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
     Carver c{base, 0, kNoallocBytes};
     const uint64_t V = L.total_v, W = L.total_w, T = L.total_tiles, C = L.total_real;
     const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
-    ws->sort_blocks = (uint32_t)nsm * 8;
+    ws->sort_blocks = (uint32_t)nsm * 2;
     bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
               c.take(ws->d_ls, 1) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
               c.take(ws->cpwords, W) && c.take(ws->reqw, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&

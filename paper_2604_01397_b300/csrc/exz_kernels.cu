@@ -614,6 +614,38 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t &excl, 
     return total;
 }
 
+// Exclusive scan of one uint32 per thread across a block of NT threads;
+// returns the block total.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan_n(uint32_t v, uint32_t &excl, uint32_t *swarp)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) swarp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? swarp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) swarp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = warp ? swarp[warp - 1] : 0;
+    const uint32_t total = swarp[NW - 1];
+    excl = before + x - v;
+    __syncthreads();
+    return total;
+}
+
 // Exclusive scan of n uint32 values into uint64 offsets; one block of 1024.
 __global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n,
                                                    unsigned long long *total)
@@ -811,65 +843,106 @@ __global__ void __launch_bounds__(RADIX) k_sort_hist(Dev D, int pass, const uint
     D.hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
+// One LSD pass, tile by tile: each block owns a contiguous chunk of the input
+// (the same chunk its histogram counted) and takes it SORT_TILE elements at a
+// time.  Warp w ranks the w-th 256-element slice of the tile by itself, 32
+// elements per round (warp match for the rank within a round, a running count
+// per digit in the warp's shared counters); then the warps' counts are
+// prefixed per digit and the digits' tile counts scanned, which places every
+// element of the tile in digit order, stably, in shared memory; from there
+// consecutive threads write consecutive positions of each digit's run.
 // last != 0: this is the final pass; also record each critical point's rank
-// within its field (cp_rank), which the frontier uses to find its CP pairs.
+// within its field (cp_rank), which the frontier uses to find its CP pairs,
+// and its value in sorted order (gs).
+constexpr int SORT_ROUNDS = 8;
+constexpr int SORT_TILE = RADIX * SORT_ROUNDS;
+
 __global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const uint32_t *ksrc,
                                                         const unsigned long long *esrc, uint32_t *kdst,
                                                         unsigned long long *edst, int last,
                                                         const unsigned long long *countp, uint64_t cp0)
 {
-    __shared__ uint32_t s_run[RADIX];
-    __shared__ uint32_t s_wc[SWARPS][RADIX];
-    __shared__ uint32_t s_tot[RADIX];
-    const int warp = threadIdx.x >> 5;
+    __shared__ uint32_t s_key[SORT_TILE];
+    __shared__ unsigned long long s_ent[SORT_TILE];
+    __shared__ uint32_t s_wc[SWARPS][RADIX];  // a warp's running digit counts, then their prefixes
+    __shared__ uint32_t s_tbase[RADIX];       // first position of each digit in the tile
+    __shared__ uint32_t s_gbase[RADIX];       // next output position of each digit for this block
+    __shared__ uint32_t s_sw[SWARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long count = *countp;
     const unsigned long long chunk = (count + gridDim.x - 1) / gridDim.x;
     const unsigned long long b = blockIdx.x * chunk, e = min(count, b + chunk);
-    s_run[threadIdx.x] = D.hist[threadIdx.x * gridDim.x + blockIdx.x];
     const bool move_keys = pass < 3;  // keys are not needed after the last value pass
-    for (unsigned long long base = b; base < e; base += RADIX) {
+    s_gbase[threadIdx.x] = D.hist[threadIdx.x * gridDim.x + blockIdx.x];
+    uint32_t *wc = s_wc[warp];
+    for (unsigned long long base = b; base < e; base += SORT_TILE) {
+        const uint32_t ntile = (uint32_t)min((unsigned long long)SORT_TILE, e - base);
+        const uint32_t w0 = (uint32_t)warp * (SORT_TILE / SWARPS);  // this warp's slice of the tile
+        uint32_t key[SORT_ROUNDS], dig[SORT_ROUNDS], lrank[SORT_ROUNDS];
+        unsigned long long ent[SORT_ROUNDS];
 #pragma unroll
-        for (int w = 0; w < SWARPS; w++) s_wc[w][threadIdx.x] = 0;
-        __syncthreads();
-        const unsigned long long j = base + threadIdx.x;
-        const bool valid = j < e;
-        uint32_t key = 0;
-        unsigned long long ent = 0;
-        uint32_t d = 0x100u + 0;  // never equals a real digit
-        if (valid) {
-            if (pass < 4) key = ksrc[j];
-            ent = esrc[j];
-            d = sort_digit(pass, key, ent);
-        }
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lanemask_lt());
-        if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t s = 0;
-#pragma unroll
-            for (int w = 0; w < SWARPS; w++) {
-                const uint32_t t = s_wc[w][threadIdx.x];
-                s_wc[w][threadIdx.x] = s;
-                s += t;
+        for (int r = 0; r < SORT_ROUNDS; r++) {  // all loads of the slice first
+            const uint32_t jt = w0 + (uint32_t)r * 32 + lane;
+            key[r] = 0;
+            ent[r] = 0;
+            if (jt < ntile) {
+                if (pass < 4) key[r] = ksrc[base + jt];
+                ent[r] = esrc[base + jt];
             }
-            s_tot[threadIdx.x] = s;
+        }
+#pragma unroll
+        for (int j = 0; j < RADIX / 32; j++) wc[j * 32 + lane] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < SORT_ROUNDS; r++) {
+            const bool valid = w0 + (uint32_t)r * 32 + lane < ntile;
+            dig[r] = valid ? sort_digit(pass, key[r], ent[r]) : 0x100u;  // 0x100: never a real digit
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+            const uint32_t rank = __popc(peers & lanemask_lt());
+            const uint32_t before = valid ? wc[dig[r]] : 0u;
+            __syncwarp();
+            if (valid && rank == 0) wc[dig[r]] = before + __popc(peers);
+            __syncwarp();
+            lrank[r] = before + rank;
         }
         __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_run[d] + s_wc[warp][d] + rank;
-            if (move_keys) kdst[pos] = key;
-            edst[pos] = ent;
+        // per digit: prefix of the warps' counts, and the tile count
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < SWARPS; w++) {
+            const uint32_t t = s_wc[w][threadIdx.x];
+            s_wc[w][threadIdx.x] = run;
+            run += t;
+        }
+        uint32_t ex;
+        block_excl_scan_n<RADIX>(run, ex, s_sw);  // (has barriers)
+        s_tbase[threadIdx.x] = ex;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SORT_ROUNDS; r++) {
+            if (dig[r] < 0x100u) {
+                const uint32_t p = s_tbase[dig[r]] + wc[dig[r]] + lrank[r];
+                s_key[p] = key[r];
+                s_ent[p] = ent[r];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < ntile; i += RADIX) {
+            const uint32_t k = s_key[i];
+            const unsigned long long en = s_ent[i];
+            const uint32_t d = sort_digit(pass, k, en);
+            const uint32_t pos = s_gbase[d] + (i - s_tbase[d]);
+            if (move_keys) kdst[pos] = k;
+            edst[pos] = en;
             if (last) {
-                const uint32_t fid = (uint32_t)(ent >> LOCAL_BITS);
+                const uint32_t fid = (uint32_t)(en >> LOCAL_BITS);
                 const FieldDesc &F = D.fields[fid];
-                D.cp_rank[F.vbase + (ent & LOCAL_MASK)] = (uint32_t)(cp0 + pos - D.fst[fid].cp_base);
-                D.gs[cp0 + pos] = F.g[ent & LOCAL_MASK];  // g == f_hat before the first edit
+                D.cp_rank[F.vbase + (en & LOCAL_MASK)] = (uint32_t)(cp0 + pos - D.fst[fid].cp_base);
+                D.gs[cp0 + pos] = F.g[en & LOCAL_MASK];  // g == f_hat before the first edit
             }
         }
         __syncthreads();
-        s_run[threadIdx.x] += s_tot[threadIdx.x];
-        __syncthreads();
+        s_gbase[threadIdx.x] += run;
     }
 }
 

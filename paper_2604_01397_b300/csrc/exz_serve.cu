@@ -507,7 +507,7 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
     S->C = S->V;
     S->W = rup(S->V / 16 + (uint64_t)S->slots * WBLOCK, WBLOCK);
     S->T = rup(S->V / 256 + (uint64_t)S->slots * 32, 32);
-    S->sort_blocks = (uint32_t)device_sms() * 8;
+    S->sort_blocks = (uint32_t)device_sms() * 2;
     const uint64_t V = S->V, W = S->W, T = S->T, C = S->C;
     const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
     bool ok = salloc(S, S->d_fields, S->slots) && salloc(S, S->d_fst, S->slots) && salloc(S, S->d_ls, 1) &&
