@@ -158,6 +158,23 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's step time (all ranks get it), then a barrier."""
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(world: int, n: int, ms: float) -> float:
+    """Whole-job GB/s: every rank corrects its own replica of n float32 values
+    in ms milliseconds (the slowest rank's time)."""
+    return world * 4.0 * n / (ms / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------- helpers
 def peaks():
     try:
@@ -303,11 +320,8 @@ def run_ours(a):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / a.steps
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = world * 4.0 * n / (ms / 1e3) / 1e9
+        ms = max_over_ranks(ms, dist, dev)
+    value = replica_throughput(world, n, ms)
     if rank != 0:
         ws.close()
         if dist:
