@@ -1,8 +1,9 @@
 """The oracle -- TEST INFRASTRUCTURE ONLY.
 
 A plain, slow CPU implementation of the EXaCTz correction (Algorithm 1 with the
-EG constraints of Sec. 4.2 and the reformulated event constraints of Sec. 4.3)
-plus brute-force topology tools (``oracle.topology``).  Only ``tests/``, the
+EG constraints of Sec. 4.2 and either the reformulated event constraints of
+Sec. 4.3 or the saddle-ordering and original merge / split event constraints of
+Sec. 4.2) plus brute-force topology tools (``oracle.topology``).  Only ``tests/``, the
 smoke check and the benchmark's CPU-baseline leg import this package; the
 library under ``paper_2604_01397_b300`` never does, and the two share no code.
 
@@ -16,6 +17,11 @@ Parity status per function (each pin lives under ``tests/``):
                 component counts.
   cp_order      pinned: equals numpy lexsort on (value, index).
   requests      pinned through ``correct`` (R empty at a converged fixpoint).
+  correct(events=True), requests(events=True)
+                pinned: brute-force extremum graphs, merge and split trees and
+                event selections of converged results, fixpoint invariants
+                with the saddle order, hand-derived request sets on two- and
+                three-well fields, planted mistakes (tests/test_oracle_events.py).
 """
 from __future__ import annotations
 
@@ -47,6 +53,8 @@ def lib():
         L.oracle_correct.argtypes = [P, P, i64, i64, i64, ctypes.c_float, ctypes.c_int,
                                      i64, ctypes.c_int, P, P, P]
         L.oracle_requests.argtypes = [P, P, i64, i64, i64, P, P]
+        L.oracle_correct_events.argtypes = [P, P, i64, i64, i64, ctypes.c_float, ctypes.c_int, i64, P, P, P]
+        L.oracle_requests_events.argtypes = [P, P, i64, i64, i64, P, P]
         _lib = L
     return _lib
 
@@ -111,9 +119,11 @@ def cp_order(f, dims=None) -> np.ndarray:
 
 
 def correct(f, fhat, xi: float, dims=None, N: int = 5, max_iters: int = 1 << 30,
-            worklist: bool = False) -> dict:
+            worklist: bool = False, events: bool = False) -> dict:
     """Run the correction to its fixpoint.  Returns g, k, iterations, residual,
-    status, n_edits, n_lossless and the edit list (ascending index)."""
+    status, n_edits, n_lossless and the edit list (ascending index).
+    events=True: the saddle-ordering and original event constraints replace the
+    reformulated ones (every rule is evaluated in full each pass)."""
     f = _f32(f)
     fhat = _f32(fhat)
     nx, ny, nz = _dims_of(f, dims)
@@ -121,9 +131,14 @@ def correct(f, fhat, xi: float, dims=None, N: int = 5, max_iters: int = 1 << 30,
     g = np.empty(n, np.float32)
     k = np.empty(n, np.uint8)
     info = np.zeros(5, np.int64)
-    rc = lib().oracle_correct(_p(f.reshape(-1)), _p(fhat.reshape(-1)), nx, ny, nz,
-                              ctypes.c_float(np.float32(xi)), int(N), int(max_iters),
-                              int(bool(worklist)), _p(g), _p(k), _p(info))
+    if events:
+        rc = lib().oracle_correct_events(_p(f.reshape(-1)), _p(fhat.reshape(-1)), nx, ny, nz,
+                                         ctypes.c_float(np.float32(xi)), int(N), int(max_iters),
+                                         _p(g), _p(k), _p(info))
+    else:
+        rc = lib().oracle_correct(_p(f.reshape(-1)), _p(fhat.reshape(-1)), nx, ny, nz,
+                                  ctypes.c_float(np.float32(xi)), int(N), int(max_iters),
+                                  int(bool(worklist)), _p(g), _p(k), _p(info))
     if rc != 0:
         raise ValueError(f"oracle_correct failed: {rc}")
     idx = np.nonzero(k)[0]
@@ -147,15 +162,15 @@ def correct_rc(f, fhat, xi: float, dims=None, N: int = 5) -> int:
                                 _p(g), _p(k), _p(info))
 
 
-def requests(f, g, dims=None):
+def requests(f, g, dims=None, events: bool = False):
     """Full request set R (bool per vertex) of the edited field g."""
     f = _f32(f)
     g = _f32(g)
     nx, ny, nz = _dims_of(f, dims)
     req = np.empty(f.size, np.uint8)
     cnt = ctypes.c_int64()
-    rc = lib().oracle_requests(_p(f.reshape(-1)), _p(g.reshape(-1)), nx, ny, nz, _p(req),
-                               ctypes.byref(cnt))
+    fn = lib().oracle_requests_events if events else lib().oracle_requests
+    rc = fn(_p(f.reshape(-1)), _p(g.reshape(-1)), nx, ny, nz, _p(req), ctypes.byref(cnt))
     if rc != 0:
         raise ValueError(f"oracle_requests failed: {rc}")
     return req.astype(bool), int(cnt.value)

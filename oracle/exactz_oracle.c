@@ -3,7 +3,8 @@
  *
  * A plain, slow CPU statement of the EXaCTz bounded-iteration correction
  * (Li et al., "EXaCTz", Algorithm 1 with the EG constraints of Sec. 4.2 and the
- * reformulated event constraints of Sec. 4.3).  Only the test-suite, the smoke
+ * reformulated event constraints of Sec. 4.3, or the saddle-ordering and the
+ * original merge / split event constraints of Sec. 4.2).  Only the test-suite, the smoke
  * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
  * header, table or helper with the CUDA library: the mesh is re-derived here
  * from explicit tetrahedra, neighbour searches compare values one pair at a
@@ -46,6 +47,22 @@
  *    through float ties at the floors).  Stop with ITER_LIMIT when R* is not
  *    empty after max_iters edit passes.  iterations = edit passes executed;
  *    residual = |R| of the last check.
+ *
+ * Original event constraints (Sec. 4.2 "Saddle Ordering Constraints" and
+ * "Merge and Split Event Constraints"; oracle_correct_events), used instead of
+ * R3:
+ *      C2: with so the saddles of f sorted by the f-order, for each adjacent
+ *          pair (so[q], so[q+1]) whose g-order is reversed, request so[q].
+ *      C3: the extremum graph of f links a join saddle s to minimum m when
+ *          the steepest-descent path (down_f repeatedly) from some neighbour
+ *          of s below s ends at m (Sec. 3.2 Step 1).  Extremum Graph Pairing
+ *          selects the largest of the minima linked to s.  If the largest in g
+ *          (among the same minima) differs from the one in f, request the one
+ *          selected in g (it lies below the f-selection in f).  Split saddles
+ *          symmetrically: steepest-ascent paths (up_f) from the neighbours above
+ *          a split saddle reach its maxima, EGP selects the smallest maximum, and a
+ *          differing g-selection requests the f-selection (the lower of the two
+ *          in f).  A saddle whose paths reach a single extremum has no event.
  *
  * Worklist mode evaluates R1/R2 only at vertices whose closed neighbourhood
  * holds a vertex edited in the previous pass, and R3 only on pairs touching an
@@ -295,7 +312,16 @@ typedef struct {
     int64_t *o;       /* critical points of f, sorted by the f-order */
     int64_t ncp;
     int64_t *rank;    /* position of a critical point in o, -1 otherwise */
+    /* original event constraints (events = 1) */
+    int events;
+    int64_t *so;      /* saddles of f, sorted by the f-order */
+    int64_t nso;
+    int64_t *ev_ext;  /* per vertex, up to EV_MAX extrema: minima of a join saddle, then maxima of a split */
+    uint8_t *ev_nmin, *ev_nmax;
+    int64_t *sel_min, *sel_max;  /* EGP selection in f, -1 if none */
 } ctx_t;
+
+#define EV_MAX 16
 
 static void mark(uint8_t *req, int64_t x)
 {
@@ -332,6 +358,32 @@ static void check_pair(const ctx_t *C, const float *g, int64_t q, uint8_t *req)
     if (prec(g, b, a)) mark(req, a);
 }
 
+/* C2 on the sorted saddle pair (so[q], so[q+1]). */
+static void check_saddle_pair(const ctx_t *C, const float *g, int64_t q, uint8_t *req)
+{
+    int64_t a = C->so[q], b = C->so[q + 1];
+    if (prec(g, b, a)) mark(req, a);
+}
+
+/* C3 at saddle s: the EGP selection among its connected extrema in g. */
+static void check_events(const ctx_t *C, const float *g, int64_t s, uint8_t *req)
+{
+    const int64_t *e = C->ev_ext + s * EV_MAX;
+    int nm = C->ev_nmin[s], nx = C->ev_nmax[s];
+    if (C->sel_min[s] >= 0) {
+        int64_t best = e[0];
+        for (int j = 1; j < nm; j++)
+            if (prec(g, best, e[j])) best = e[j];
+        if (best != C->sel_min[s]) mark(req, best);
+    }
+    if (C->sel_max[s] >= 0) {
+        int64_t best = e[nm];
+        for (int j = 1; j < nx; j++)
+            if (prec(g, e[nm + j], best)) best = e[nm + j];
+        if (best != C->sel_max[s]) mark(req, C->sel_max[s]);
+    }
+}
+
 static int64_t count_set(const uint8_t *req, int64_t n)
 {
     int64_t c = 0;
@@ -345,18 +397,99 @@ static int64_t check_full(const ctx_t *C, const float *g, uint8_t *req)
     memset(req, 0, (size_t)C->G.n);
 #pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t p = 0; p < C->G.n; p++) check_vertex(C, g, p, req);
-    const int64_t npairs = C->ncp - 1;
+    if (!C->events) {
+        const int64_t npairs = C->ncp - 1;
 #pragma omp parallel for schedule(static)
-    for (int64_t q = 0; q < npairs; q++) check_pair(C, g, q, req);
+        for (int64_t q = 0; q < npairs; q++) check_pair(C, g, q, req);
+    } else {
+        const int64_t npairs = C->nso - 1;
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < npairs; q++) check_saddle_pair(C, g, q, req);
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < C->nso; q++) check_events(C, g, C->so[q], req);
+    }
     return count_set(req, C->G.n);
+}
+
+/* Terminal extremum of the integral path from v along the steepest links. */
+static int64_t path_end(const int64_t *step, int64_t v)
+{
+    while (step[v] != v) v = step[v];
+    return v;
+}
+
+/* The extremum graph of f at its saddles and its EGP selections (C3), and the
+ * sorted saddles (C2). */
+static int setup_events(ctx_t *C)
+{
+    const int64_t n = C->G.n;
+    C->so = malloc(sizeof(int64_t) * n);
+    C->ev_ext = malloc(sizeof(int64_t) * n * EV_MAX);
+    C->ev_nmin = calloc((size_t)n, 1);
+    C->ev_nmax = calloc((size_t)n, 1);
+    C->sel_min = malloc(sizeof(int64_t) * n);
+    C->sel_max = malloc(sizeof(int64_t) * n);
+    if (!C->so || !C->ev_ext || !C->ev_nmin || !C->ev_nmax || !C->sel_min || !C->sel_max) return OR_ENOMEM;
+    C->nso = 0;
+    for (int64_t q = 0; q < C->ncp; q++)
+        if (C->tyf[C->o[q]] & (T_JOIN | T_SPLIT)) C->so[C->nso++] = C->o[q];
+    for (int64_t p = 0; p < n; p++) C->sel_min[p] = C->sel_max[p] = -1;
+    for (int64_t q = 0; q < C->nso; q++) {
+        const int64_t s = C->so[q];
+        int64_t nb[32];
+        int slot[32];
+        const int cnt = neighbours(&C->G, s, nb, slot);
+        int64_t *e = C->ev_ext + s * EV_MAX;
+        int ne = 0;
+        if (C->tyf[s] & T_JOIN) {
+            for (int j = 0; j < cnt; j++) {
+                if (!prec(C->f, nb[j], s)) continue;
+                const int64_t m = path_end(C->dnf, nb[j]);
+                int dup = 0;
+                for (int i = 0; i < ne; i++) dup |= e[i] == m;
+                if (!dup) e[ne++] = m;
+            }
+            C->ev_nmin[s] = (uint8_t)ne;
+            if (ne >= 2) {
+                int64_t best = e[0];
+                for (int i = 1; i < ne; i++)
+                    if (prec(C->f, best, e[i])) best = e[i];
+                C->sel_min[s] = best;
+            }
+        }
+        const int nm = ne;
+        if (C->tyf[s] & T_SPLIT) {
+            for (int j = 0; j < cnt; j++) {
+                if (!prec(C->f, s, nb[j])) continue;
+                const int64_t m = path_end(C->upf, nb[j]);
+                int dup = 0;
+                for (int i = nm; i < ne; i++) dup |= e[i] == m;
+                if (!dup) e[ne++] = m;
+            }
+            C->ev_nmax[s] = (uint8_t)(ne - nm);
+            if (ne - nm >= 2) {
+                int64_t best = e[nm];
+                for (int i = nm + 1; i < ne; i++)
+                    if (prec(C->f, e[i], best)) best = e[i];
+                C->sel_max[s] = best;
+            }
+        }
+    }
+    return 0;
+}
+
+static void free_events(ctx_t *C)
+{
+    free(C->so); free(C->ev_ext); free(C->ev_nmin); free(C->ev_nmax); free(C->sel_min); free(C->sel_max);
+    C->so = NULL; C->ev_ext = NULL; C->ev_nmin = C->ev_nmax = NULL; C->sel_min = C->sel_max = NULL;
 }
 
 int oracle_requests(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz,
                     uint8_t *req_out, int64_t *count_out);
 
-int oracle_correct(const float *f, const float *fhat, int64_t nx, int64_t ny, int64_t nz,
-                   float xi, int N, int64_t max_iters, int worklist,
-                   float *g, uint8_t *k, int64_t *info)
+static int correct_impl(const float *f, const float *fhat, int64_t nx, int64_t ny, int64_t nz,
+                        float xi, int N, int64_t max_iters, int worklist, int events,
+                        float *g, uint8_t *k, int64_t *info)
 {
     /* info: [0] iterations, [1] residual, [2] status, [3] n_edits, [4] n_lossless */
     if (!dims_ok(nx, ny, nz) || !(xi > 0.0f) || !isfinite(xi) || N < 1 || N > 254 || max_iters < 0)
@@ -387,6 +520,17 @@ int oracle_correct(const float *f, const float *fhat, int64_t nx, int64_t ny, in
     C.ncp = cp_order(f, C.tyf, n, C.o);
     for (int64_t p = 0; p < n; p++) C.rank[p] = -1;
     for (int64_t q = 0; q < C.ncp; q++) C.rank[C.o[q]] = q;
+    C.events = events;
+    C.so = NULL; C.ev_ext = NULL; C.ev_nmin = C.ev_nmax = NULL; C.sel_min = C.sel_max = NULL;
+    if (events) {
+        worklist = 0;  /* the event rules are evaluated in full every pass */
+        if (setup_events(&C) != 0) {
+            free_events(&C);
+            free(C.upf); free(C.dnf); free(C.tyf); free(C.o); free(C.rank);
+            free(req); free(active); free(pact); free(changed);
+            return OR_ENOMEM;
+        }
+    }
 
     const float delta = xi / (float)N;
     for (int64_t p = 0; p < n; p++) {
@@ -468,14 +612,48 @@ int oracle_correct(const float *f, const float *fhat, int64_t nx, int64_t ny, in
     info[2] = status;
     info[3] = ne;
     info[4] = nl;
+    free_events(&C);
     free(C.upf); free(C.dnf); free(C.tyf); free(C.o); free(C.rank);
     free(req); free(active); free(pact); free(changed);
     return 0;
 }
 
+/* Algorithm 1 with the EG constraints and the reformulated event constraints. */
+int oracle_correct(const float *f, const float *fhat, int64_t nx, int64_t ny, int64_t nz,
+                   float xi, int N, int64_t max_iters, int worklist,
+                   float *g, uint8_t *k, int64_t *info)
+{
+    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, worklist, 0, g, k, info);
+}
+
+/* Algorithm 1 with the EG constraints, the saddle-ordering constraints and the
+ * original merge / split event constraints (C2, C3). */
+int oracle_correct_events(const float *f, const float *fhat, int64_t nx, int64_t ny, int64_t nz,
+                          float xi, int N, int64_t max_iters,
+                          float *g, uint8_t *k, int64_t *info)
+{
+    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, 0, 1, g, k, info);
+}
+
+static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events,
+                         uint8_t *req_out, int64_t *count_out);
+
 /* The full request set R for a given edited field g (no pinned filter). */
 int oracle_requests(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz,
                     uint8_t *req_out, int64_t *count_out)
+{
+    return requests_impl(f, g, nx, ny, nz, 0, req_out, count_out);
+}
+
+/* The same with the original event constraints in place of R3. */
+int oracle_requests_events(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz,
+                           uint8_t *req_out, int64_t *count_out)
+{
+    return requests_impl(f, g, nx, ny, nz, 1, req_out, count_out);
+}
+
+static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events,
+                         uint8_t *req_out, int64_t *count_out)
 {
     if (!dims_ok(nx, ny, nz)) return OR_EINVAL;
     derive_mesh();
@@ -494,7 +672,15 @@ int oracle_requests(const float *f, const float *g, int64_t nx, int64_t ny, int6
     }
     oracle_classify(f, nx, ny, nz, C.upf, C.dnf, C.tyf);
     C.ncp = cp_order(f, C.tyf, n, C.o);
+    C.events = events;
+    C.so = NULL; C.ev_ext = NULL; C.ev_nmin = C.ev_nmax = NULL; C.sel_min = C.sel_max = NULL;
+    if (events && setup_events(&C) != 0) {
+        free_events(&C);
+        free(C.upf); free(C.dnf); free(C.tyf); free(C.o);
+        return OR_ENOMEM;
+    }
     *count_out = check_full(&C, g, req_out);
+    free_events(&C);
     free(C.upf); free(C.dnf); free(C.tyf); free(C.o);
     return 0;
 }

@@ -10,7 +10,9 @@ on (value, index), and the structures are built from their definitions:
 * extremum graphs by following steepest-descent / -ascent integral paths from
   the neighbours of every saddle (Sec. 3.1, Sec. 3.2 Step 1);
 * join / split trees by a union-find sweep of the sublevel / superlevel sets
-  (Sec. 3.1, merge trees; the contour tree is their combination);
+  (Sec. 3.1, merge trees; the contour tree is their combination), and their
+  branch decompositions by the elder rule of the same sweep (the pairs that
+  Extremum Graph Pairing extracts, Sec. 3.2 Step 2);
 * weak / strong / reduced vulnerability graphs and the longest path D_max of
   Thm. 4.1 (Sec. 4.4).
 Pure Python loops: use on fields of at most a few thousand vertices.
@@ -182,6 +184,71 @@ def join_tree(grid: Grid, h) -> Set[Tuple[int, int]]:
 def split_tree(grid: Grid, h) -> Set[Tuple[int, int]]:
     """Arcs of the split tree (superlevel sets merging when sweeping down)."""
     return _merge_tree(grid, ranks(h), ascending=False)
+
+
+def _branch_pairs(grid: Grid, r: np.ndarray, ascending: bool) -> Set[Tuple[int, int]]:
+    """Elder rule on the sweep: where components meet, the one born at the
+    oldest extremum (lowest rank going up, highest going down) survives and every
+    other is paired with the meeting vertex as (its birth extremum, vertex)."""
+    order = np.argsort(r if ascending else -r, kind="stable")
+    key = r if ascending else -r
+    parent = {}
+    birth = {}
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    pairs = set()
+    for v in order:
+        v = int(v)
+        roots = {find(u) for u in grid.neighbours(v) if u in parent}
+        parent[v] = v
+        if not roots:
+            birth[v] = v
+            continue
+        elder = min(roots, key=lambda q: key[birth[q]])
+        if len(roots) >= 2:
+            for q in roots:
+                if q != elder:
+                    pairs.add((birth[q], v))
+        for q in roots:
+            parent[q] = v
+        birth[v] = birth[elder]
+    return pairs
+
+
+def branch_pairs(grid: Grid, h) -> Set[Tuple[str, int, int]]:
+    """Branches of the join ('j': minimum, join saddle) and split ('s': maximum,
+    split saddle) trees, as extracted by Extremum Graph Pairing."""
+    r = ranks(h)
+    return ({("j",) + p for p in _branch_pairs(grid, r, True)} |
+            {("s",) + p for p in _branch_pairs(grid, r, False)})
+
+
+def event_selections(eg, h) -> Dict[Tuple[str, int], int]:
+    """The two selections of the merge / split event constraints (Sec. 4.2,
+    C3) over the links of extremum graph eg, ranked by h: per saddle with two
+    or more linked extrema, its largest minimum ('join') or smallest maximum
+    ('split'); per extremum, its lowest join saddle ('min') or highest split
+    saddle ('max')."""
+    r = ranks(h)
+    by_saddle: Dict[Tuple[str, int], Set[int]] = {}
+    by_ext: Dict[Tuple[str, int], Set[int]] = {}
+    for s, e, kind in eg:
+        by_saddle.setdefault((kind, s), set()).add(e)
+        by_ext.setdefault(("min" if kind == "join" else "max", e), set()).add(s)
+    out = {}
+    for (kind, s), es in by_saddle.items():
+        if len(es) >= 2:
+            pick = max if kind == "join" else min
+            out[(kind, s)] = pick(es, key=lambda v: r[v])
+    for (kind, e), ss in by_ext.items():
+        pick = min if kind == "min" else max
+        out[(kind, e)] = pick(ss, key=lambda v: r[v])
+    return out
 
 
 def recalls(grid: Grid, f, g) -> Dict[str, float]:

@@ -265,11 +265,6 @@ __device__ __forceinline__ uint32_t fkey(float v)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__device__ __forceinline__ int64_t lin_delta(int r, uint64_t nx, uint64_t nxny)
-{
-    return (int64_t)rdx(r) + (int64_t)nx * rdy(r) + (int64_t)nxny * rdz(r);
-}
-
 __device__ __forceinline__ bool multi_bit(const uint32_t *tab, uint32_t s)
 {
     return (tab[s >> 5] >> (s & 31)) & 1u;
@@ -280,19 +275,6 @@ __device__ __forceinline__ bool is_saddle(const uint32_t *tab, uint32_t L, uint3
 {
     uint32_t U = valid & ~L;
     return L != 0 && U != 0 && (multi_bit(tab, L) || multi_bit(tab, U));
-}
-
-// Mark a tile in a bitmap; append it to a list the first time.
-__device__ __forceinline__ void mark_tile(uint32_t *bits, uint32_t *list, unsigned long long *count,
-                                          uint32_t tile)
-{
-    uint32_t bit = 1u << (tile & 31);
-    if (__ldcg(&bits[tile >> 5]) & bit) return;
-    uint32_t old = atomicOr(&bits[tile >> 5], bit);
-    if (!(old & bit)) {
-        unsigned long long p = atomicAdd(count, 1ull);
-        list[p] = tile;
-    }
 }
 
 // Warp-wide tile marking: each lane with `want` marks `tile` in the bitmap, and

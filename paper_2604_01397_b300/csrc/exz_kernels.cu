@@ -585,35 +585,6 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
 }
 
 // ------------------------------------------------------------ block scan helpers
-// Exclusive scan of one uint32 per thread across the block; returns the block total.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t &excl, uint32_t *swarp)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) swarp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < WARPS ? swarp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < WARPS) swarp[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t before = warp ? swarp[warp - 1] : 0;
-    const uint32_t total = swarp[WARPS - 1];
-    excl = before + x - v;
-    __syncthreads();
-    return total;
-}
-
 // Exclusive scan of one uint32 per thread across a block of NT threads;
 // returns the block total.
 template <int NT>
@@ -761,7 +732,7 @@ __global__ void __launch_bounds__(CTA) k_cp_count(Dev D, uint64_t wblk0)
 #pragma unroll
     for (int j = 0; j < WPT; j++) c += __popc(D.cpwords[w0 + j]);
     uint32_t ex;
-    uint32_t tot = block_excl_scan(c, ex, sw);
+    uint32_t tot = block_excl_scan_n<CTA>(c, ex, sw);
     if (threadIdx.x == 0) D.blk[blockIdx.x] = tot;
 }
 
@@ -781,7 +752,7 @@ __global__ void __launch_bounds__(CTA) k_cp_write(Dev D, SetupRange R)
         c += __popc(words[j]);
     }
     uint32_t ex;
-    block_excl_scan(c, ex, sw);
+    block_excl_scan_n<CTA>(c, ex, sw);
     unsigned long long pos = cp0 + D.blk_off[blockIdx.x] + ex;
     if (blk0 == F.wbase && threadIdx.x == 0) D.fst[fid].cp_base = cp0 + D.blk_off[blockIdx.x];
     const uint64_t ny = F.ny;
@@ -1408,7 +1379,7 @@ __global__ void __launch_bounds__(CTA) k_edit_count(Dev D, FieldSet FS)
     __syncthreads();
     if (l) atomicAdd(&s_lossless, l);
     uint32_t ex;
-    const uint32_t tot = block_excl_scan(c, ex, sw);
+    const uint32_t tot = block_excl_scan_n<CTA>(c, ex, sw);
     if (threadIdx.x == 0) {
         D.blk[blockIdx.x] = tot;
         if (tot) atomicAdd(&D.fst[fid].n_edits, (unsigned long long)tot);
@@ -1440,7 +1411,7 @@ __global__ void __launch_bounds__(CTA) k_edit_write(Dev D, FieldSet FS)
 #pragma unroll
     for (int j = 0; j < EPT; j++) c += kks[j] != 0;
     uint32_t ex;
-    block_excl_scan(c, ex, sw);
+    block_excl_scan_n<CTA>(c, ex, sw);
     const unsigned long long fbase = D.blk_off[F.vbase / VBLOCK - vblk0];
     unsigned long long pos = D.blk_off[blockIdx.x] + ex - fbase;
     if (!c) return;

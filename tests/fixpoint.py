@@ -22,7 +22,9 @@ def replay(fhat, k, f, xi, N):
     return g
 
 
-def check_fixpoint(f, fhat, xi, N, g, k, status, residual=None, dims=None, full=True):
+def check_fixpoint(f, fhat, xi, N, g, k, status, residual=None, dims=None, full=True, events=False):
+    """events=True: the result of the original event constraints, which fix the
+    order of the saddles (C2) rather than of every critical point."""
     f = np.asarray(f, np.float32).reshape(-1)
     fhat = np.asarray(fhat, np.float32).reshape(-1)
     g = np.asarray(g, np.float32).reshape(-1)
@@ -39,7 +41,7 @@ def check_fixpoint(f, fhat, xi, N, g, k, status, residual=None, dims=None, full=
     tol = np.spacing(np.abs(f).astype(np.float32) + xi32).astype(np.float64)
     assert np.all(d >= -float(xi32) - tol) and np.all(d <= float(xi32) + tol)
     if full:
-        req, cnt = oracle.requests(f, g, dims)
+        req, cnt = oracle.requests(f, g, dims, events=events)
         if status == oracle.CONVERGED:
             assert cnt == 0
             up_f, dn_f, ty_f = oracle.classify(f, dims)
@@ -47,6 +49,8 @@ def check_fixpoint(f, fhat, xi, N, g, k, status, residual=None, dims=None, full=
             assert np.array_equal(up_f, up_g) and np.array_equal(dn_f, dn_g)
             assert np.array_equal(ty_f, ty_g)
             o = oracle.cp_order(f, dims)
+            if events:
+                o = o[(ty_f[o] & (oracle.T_JOIN | oracle.T_SPLIT)) != 0]
             gv = g[o]
             # strictly increasing in the g-order, ties broken by index
             ok = (gv[1:] > gv[:-1]) | ((gv[1:] == gv[:-1]) & (o[1:] > o[:-1]))

@@ -5,12 +5,6 @@ Each mutant is compiled with gcc into a temporary directory, swapped in for
 the oracle library, and run through the hand-derived runs, the independent
 classifier and the fixpoint / topology properties on small fields.
 """
-import ctypes
-import os
-import shutil
-import subprocess
-import tempfile
-
 import numpy as np
 import pytest
 
@@ -19,8 +13,7 @@ from oracle import topology as T
 import synth
 from conftest import read_golden
 from fixpoint import check_fixpoint
-
-SRC = os.path.join(os.path.dirname(oracle.__file__), "exactz_oracle.c")
+from mutant_util import mutant
 
 MUTANTS = {
     "R1-down-targets-g-min": ("if (dng != C->dnf[p]) mark(req, C->dnf[p]);",
@@ -29,8 +22,10 @@ MUTANTS = {
                             "if (upg != C->upf[p]) mark(req, C->upf[p]);"),
     "R2-raises-wrong-end": ("mark(req, below_f ? nb[j] : p);", "mark(req, below_f ? p : nb[j]);"),
     "R2-only-f-saddles": ("if (saddle_f || saddle_g) {", "if (saddle_f) {"),
-    "R3-wrong-target": ("if (prec(g, b, a)) mark(req, a);", "if (prec(g, b, a)) mark(req, b);"),
-    "R3-dropped": ("if (prec(g, b, a)) mark(req, a);", "if (0 && prec(g, b, a)) mark(req, a);"),
+    "R3-wrong-target": ("C->o[q + 1];\n    if (prec(g, b, a)) mark(req, a);",
+                        "C->o[q + 1];\n    if (prec(g, b, a)) mark(req, b);"),
+    "R3-dropped": ("C->o[q + 1];\n    if (prec(g, b, a)) mark(req, a);",
+                   "C->o[q + 1];\n    if (0 && prec(g, b, a)) mark(req, a);"),
     "SoS-reversed": ("(h[a] == h[b] && a < b)", "(h[a] == h[b] && a > b)"),
     "floor-wrong": ("float floor_x = f[x] - xi;", "float floor_x = f[x] - 2.0f * xi;"),
     "delta-wrong": ("const float delta = xi / (float)N;", "const float delta = xi / (float)(N + 1);"),
@@ -95,26 +90,8 @@ def _detected() -> bool:
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_is_caught(name, monkeypatch):
-    old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name} not unique"
-    tmp = tempfile.mkdtemp(prefix="oracle_mutant_")
-    try:
-        path = os.path.join(tmp, "mutant.c")
-        open(path, "w").write(src.replace(old, new))
-        so = os.path.join(tmp, "libmutant.so")
-        subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                        "-mfpmath=sse", path, "-o", so, "-lm"], check=True)
-        real = oracle.lib()
-        L = ctypes.CDLL(so)
-        for fn in ("oracle_mesh", "oracle_classify", "oracle_cp_order", "oracle_correct",
-                   "oracle_requests"):
-            getattr(L, fn).argtypes = getattr(real, fn).argtypes
-            getattr(L, fn).restype = getattr(real, fn).restype
-        monkeypatch.setattr(oracle, "_lib", L)
+    with mutant(monkeypatch, name, *MUTANTS[name]):
         assert _detected(), f"planted mistake {name!r} passed every pin"
-    finally:
-        shutil.rmtree(tmp, ignore_errors=True)
 
 
 def test_unmutated_copy_passes():
