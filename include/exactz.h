@@ -12,7 +12,11 @@
  *   - every vertex that is a saddle of f or of the edited field orders against
  *     all its neighbours as in f (Sec. 4.2, saddles);
  *   - all critical points of f keep f's global order (reformulated event
- *     constraints, Sec. 4.3, which subsume the saddle-ordering constraint C2).
+ *     constraints, Sec. 4.3, which subsume the saddle-ordering constraint C2);
+ *     or, with opts.events = EXACTZ_EVENTS_ORIGINAL, the saddles of f keep
+ *     their order (C2) and every saddle keeps the extremum that Extremum Graph
+ *     Pairing selects among the extrema its integral paths reach in f (merge
+ *     and split event constraints C3, Sec. 4.2).
  * A vertex needing more than N edits stores the lossless bound fl(f - xi).
  * The result is the edited field g, the sparse edit list and the number of
  * edit passes; at the fixpoint the extremum graphs and the contour tree of g
@@ -66,6 +70,12 @@ extern "C" {
 #define EXACTZ_MODE_FRONTIER 1  /* re-check only tiles touched by last pass's edits, host-driven loop */
 #define EXACTZ_MODE_GRAPH 2     /* frontier passes in a CUDA graph; device-side while-loop exit */
 
+/* Event constraints (opts.events). */
+#define EXACTZ_EVENTS_REFORMULATED 0 /* global order of all critical points (Sec. 4.3) */
+#define EXACTZ_EVENTS_ORIGINAL 1     /* saddle order C2 + extremum-graph merge/split events C3 (Sec. 4.2);
+                                        set-up traces the integral paths of f once (pointer jumping);
+                                        every field below 2^32 vertices, the workspace below 2^32 */
+
 typedef struct {
     uint32_t nx, ny, nz;
 } exactz_dims;
@@ -76,6 +86,8 @@ typedef struct {
     uint64_t max_iters;      /* cap on edit passes (0 = no edit is applied) */
     uint32_t want_edit_list; /* 0: skip the edit-list compaction */
     uint32_t profile;        /* 1: time the stages with CUDA events (see exactz_ws_stats) */
+    uint32_t events;         /* EXACTZ_EVENTS_* (default REFORMULATED) */
+    uint32_t reserved;       /* must be 0 */
 } exactz_opts;
 
 /* One applied edit.  value = g at idx; k = number of decrements applied (1..N)
@@ -147,13 +159,13 @@ int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const
 
 /* Statistics of the last exactz_ws_correct on a workspace.  stage_ms holds
  * CUDA-event times on the call's stream when opts.profile was 1 (else 0):
- * [0] set-up stencil kernel, [1] critical-point compaction, [2] radix sort,
- * [3] first pass (pair check, apply, bookkeeping), [4] the loop,
+ * [0] set-up stencil kernel, [1] critical-point compaction, [2] radix sort
+ * (with EXACTZ_EVENTS_ORIGINAL also the extremum-graph set-up), [3] first pass (pair check, apply, bookkeeping), [4] the loop,
  * [5] residual and status, [6] edit list, [7] whole call on the device. */
 typedef struct {
     uint64_t kernel_launches; /* kernels the call executed (graph bodies counted per pass) */
     uint64_t passes;          /* edit passes run for the slowest field, including the last check */
-    uint64_t total_critical;  /* critical points over all fields */
+    uint64_t total_critical;  /* listed critical points over all fields (saddles only with EXACTZ_EVENTS_ORIGINAL) */
     uint64_t sum_requests;    /* deduplicated edit requests over all passes */
     uint64_t sum_tiles;       /* tiles re-checked by frontier passes (0 for PLAIN) */
     uint64_t sum_pairs;       /* CP pairs re-checked by frontier passes (0 for PLAIN) */
@@ -240,8 +252,10 @@ int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t
  * overlapped would race on the array: within one process they are serialised
  * by a lock, and each call returns only after its stream work has finished.
  * A GRAPH mode request runs the same passes as FRONTIER driven from the host
- * (identical results); opts->profile is ignored.
- * Returns EXACTZ_ESIZE for larger fields, otherwise as exactz_correct. */
+ * (identical results); opts->profile is ignored.  EXACTZ_EVENTS_ORIGINAL
+ * needs set-up storage sized by the field's extremum graph and is refused
+ * (EXACTZ_EINVAL).  Returns EXACTZ_ESIZE for larger fields, otherwise as
+ * exactz_correct. */
 int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, float xi,
                            const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
                            uint64_t edits_cap, exactz_result *res, void *cuda_stream);
@@ -265,7 +279,8 @@ typedef struct {
     uint64_t budget_bytes; /* device memory for the arena (>= 64 MiB) */
     uint32_t max_fields;   /* resident fields at most (1..4096) */
     uint32_t reserved;
-    exactz_opts opts;      /* N, max_iters, want_edit_list for every request (N = 0: defaults); mode ignored */
+    exactz_opts opts;      /* N, max_iters, want_edit_list for every request (N = 0: defaults); mode ignored;
+                              events must be EXACTZ_EVENTS_REFORMULATED */
 } exactz_server_config;
 
 typedef struct {

@@ -32,7 +32,8 @@ class Dims(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_iters", ctypes.c_uint64),
-                ("want_edit_list", ctypes.c_uint32), ("profile", ctypes.c_uint32)]
+                ("want_edit_list", ctypes.c_uint32), ("profile", ctypes.c_uint32),
+                ("events", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Edit(ctypes.Structure):

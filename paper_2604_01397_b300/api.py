@@ -16,6 +16,9 @@ import torch
 from . import _native as N
 
 MODES = {"plain": N.MODE_PLAIN, "frontier": N.MODE_FRONTIER, "graph": N.MODE_GRAPH}
+# event constraints: the global order of all critical points (Sec. 4.3), or the
+# saddle order and extremum-graph merge / split events (Sec. 4.2)
+EVENTS = {"reformulated": 0, "original": 1}
 STATUS = {N.CONVERGED: "CONVERGED", N.STUCK: "STUCK", N.ITER_LIMIT: "ITER_LIMIT"}
 
 
@@ -55,7 +58,7 @@ def _check(t: torch.Tensor, name: str, host: bool = False):
 
 
 def make_opts(N_steps: int = 5, mode: str = "graph", max_iters: int = 1_000_000,
-              want_edit_list: bool = True, profile: bool = False) -> N.Opts:
+              want_edit_list: bool = True, profile: bool = False, events: str = "reformulated") -> N.Opts:
     o = N.Opts()
     N.lib().exactz_default_opts(ctypes.byref(o))
     o.N = int(N_steps)
@@ -63,6 +66,7 @@ def make_opts(N_steps: int = 5, mode: str = "graph", max_iters: int = 1_000_000,
     o.max_iters = int(max_iters)
     o.want_edit_list = int(bool(want_edit_list))
     o.profile = int(bool(profile))
+    o.events = EVENTS[events] if isinstance(events, str) else int(events)
     return o
 
 
@@ -125,12 +129,12 @@ class Workspace:
             raise ExactzError(rc, "exactz_ws_set_tuning")
 
     def autotune(self, fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "graph", repeats: int = 2,
-                 stream=None) -> dict:
+                 stream=None, events: str = "reformulated") -> dict:
         """Pick the launch schedule for these fields by timing whole corrections."""
         nf = len(fs)
         dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
         t = N.Tuning()
-        o = make_opts(N_steps, mode, 1_000_000, False)
+        o = make_opts(N_steps, mode, 1_000_000, False, events=events)
         rc = N.lib().exactz_ws_autotune(
             self._h, nf, N.ptr_array([x.data_ptr() for x in fs]), N.ptr_array([x.data_ptr() for x in fhats]),
             (N.Dims * nf)(*[N.Dims(*d) for d in dl]), (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis]),
@@ -159,7 +163,7 @@ class Workspace:
                 max_iters: int = 1_000_000, edits: bool = True, edits_caps=None,
                 g_out: Optional[List[torch.Tensor]] = None, edit_bufs: Optional[List[torch.Tensor]] = None,
                 stream=None, host_buffers: bool = False, raise_on_error: bool = True,
-                profile: bool = False) -> List[dict]:
+                profile: bool = False, events: str = "reformulated") -> List[dict]:
         nf = len(fs)
         dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
         for i in range(nf):
@@ -177,7 +181,7 @@ class Workspace:
         xarr = (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis])
         carr = (ctypes.c_uint64 * nf)(*caps)
         res = (N.Result * nf)()
-        o = make_opts(N_steps, mode, max_iters, edits, profile)
+        o = make_opts(N_steps, mode, max_iters, edits, profile, events)
         rc = N.lib().exactz_ws_correct(
             self._h, nf, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
             darr, xarr, ctypes.byref(o), N.ptr_array([t.data_ptr() for t in g_out]),
@@ -200,8 +204,10 @@ class Workspace:
 
 def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: int = 5,
             mode: str = "graph", max_iters: int = 1_000_000, edits: bool = True, edits_cap=None,
-            stream=None, raise_on_error: bool = True) -> dict:
-    """Correct one field to its fixpoint (exactz_correct)."""
+            stream=None, raise_on_error: bool = True, events: str = "reformulated") -> dict:
+    """Correct one field to its fixpoint (exactz_correct).  events: "reformulated"
+    (all critical points keep their order) or "original" (saddle order and
+    extremum-graph merge / split events)."""
     _check(f, "f")
     _check(fhat, "fhat")
     d = dims_of(f, dims)
@@ -209,7 +215,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: 
     cap = default_edits_cap(f.numel()) if edits_cap is None else int(edits_cap)
     buf = torch.empty((cap if edits else 0, 16), dtype=torch.uint8, device=f.device)
     res = N.Result()
-    o = make_opts(N_steps, mode, max_iters, edits)
+    o = make_opts(N_steps, mode, max_iters, edits, events=events)
     rc = N.lib().exactz_correct(ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(fhat.data_ptr()), N.Dims(*d),
                                 ctypes.c_float(float(np.float32(xi))), ctypes.byref(o),
                                 ctypes.c_void_p(g.data_ptr()),
@@ -228,7 +234,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: 
 
 def correct_batch(fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "graph",
                   max_iters: int = 1_000_000, edits: bool = True, edits_caps=None, stream=None,
-                  raise_on_error: bool = True) -> List[dict]:
+                  raise_on_error: bool = True, events: str = "reformulated") -> List[dict]:
     """Correct many independent fields in one run (exactz_correct_batch)."""
     nf = len(fs)
     dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
@@ -239,7 +245,7 @@ def correct_batch(fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "grap
     caps = [default_edits_cap(f.numel()) if edits_caps is None else int(edits_caps[i]) for i, f in enumerate(fs)]
     bufs = [torch.empty((c if edits else 0, 16), dtype=torch.uint8, device=fs[0].device) for c in caps]
     res = (N.Result * nf)()
-    o = make_opts(N_steps, mode, max_iters, edits)
+    o = make_opts(N_steps, mode, max_iters, edits, events=events)
     rc = N.lib().exactz_correct_batch(
         nf, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
         (N.Dims * nf)(*[N.Dims(*d) for d in dl]), (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis]),

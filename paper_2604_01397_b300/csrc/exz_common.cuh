@@ -58,8 +58,11 @@ __host__ __device__ constexpr int rank_of(int s) { return s < 7 ? s : s + 1; }
 __host__ __device__ constexpr int soff(int r) { return rdx(r) + HXP * rdy(r) + HXP * HY * rdz(r); }
 
 // Descriptor bits (per vertex): steepest up / down rank and lower-link mask of
-// f, saddle / critical flags of f, and in the top byte the vertex's edit count
-// k (0..N, N+1 = pinned at the lossless bound).
+// f, the saddle flag of f, the "listed" flag (the vertex is in the sorted list
+// of critical points whose order is kept: every critical point of f, or only
+// its saddles under the original event constraints), and in the top byte the
+// vertex's edit count k (0..N, N+1 = pinned at the lossless bound).  A vertex
+// is a maximum (minimum) of f iff its steepest up (down) rank is 7, itself.
 constexpr uint32_t D_UP_SHIFT = 0, D_DN_SHIFT = 4, D_MASK_SHIFT = 8;
 constexpr uint32_t D_SADDLE = 1u << 22;
 constexpr uint32_t D_CP = 1u << 23;
@@ -137,6 +140,7 @@ struct FieldState {
     unsigned long long n_lossless;
     unsigned long long pin_tile_count;
     unsigned long long pin_pair_count;
+    unsigned long long ncp_all;     // critical points of f when only the saddles are listed
     uint32_t had_req, done, err, status;
 };
 
@@ -145,9 +149,11 @@ struct LoopState {
     unsigned long long sum_requests;  // requests applied or skipped, over all passes
     unsigned long long sum_tiles;     // tiles checked by frontier passes
     unsigned long long sum_pairs;     // CP pairs checked by frontier passes
+    unsigned long long ev_cursor[3];  // event-list set-up: minima and maxima list ends, saddle-list end
     uint32_t any_active;
     uint32_t pass;
     uint32_t overflow;
+    uint32_t ev_changed;  // event-list set-up: a path end moved in the last jump round
 };
 
 // Launch schedule of the per-pass kernels (chosen by the autotuner): blocks per
@@ -189,6 +195,21 @@ struct Dev {
     uint32_t sort_blocks;
     Tuning tun;
     const uint32_t *tile_field;  // field slot of each tile when fields are placed freely (else null)
+    // Original event constraints (Sec. 4.2), events != 0: the sorted list holds
+    // the saddles of f only (C2 on its adjacent pairs), and per listed saddle q
+    // the extrema its integral paths reach in f (C3): ev_cnt[q] = number of
+    // linked minima | maxima << 8 (a side with fewer than two counts 0),
+    // ev_start[q] = their first positions in ev_list[0] / ev_list[1] (field-local
+    // vertex indices, the f-selection of Extremum Graph Pairing first).  For a
+    // linked extremum e, cp_rank[e] = h > 0 points into ev_radj: ev_radj[h] =
+    // its number of linked saddles, followed by their positions q.  The event
+    // bits of the next pass follow the pair bits in pairbits, from word ev_word0.
+    uint32_t events;
+    uint64_t ev_word0;
+    const uint2 *ev_start;
+    const uint16_t *ev_cnt;
+    const uint32_t *ev_list[2];
+    const uint32_t *ev_radj;
 };
 
 // Fields set up together: tiles [tile0, tile1), compaction blocks

@@ -164,12 +164,20 @@ struct exactz_workspace {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    uint64_t gkey[5] = {0, 0, 0, 0, 0};
+    uint64_t gkey[6] = {0, 0, 0, 0, 0, 0};
     uint64_t layout_hash = 0;  // dims of the previous run (padding must hold k = 0, no CP bits)
     exactz_stats stats{};
     cudaEvent_t ev[9] = {};
     cudaEvent_t kev[4] = {};  // around the loop kernels of one host-driven pass (profiling)
     Tuning tun;
+
+    // extremum-graph lists of the original event constraints, grown on demand
+    uint32_t *ev_E = nullptr;  // path ends (set-up scratch), one per arena vertex
+    uint2 *ev_start = nullptr;
+    uint16_t *ev_cnt = nullptr;
+    uint32_t *ev_list[2] = {nullptr, nullptr};
+    uint32_t *ev_radj = nullptr;
+    uint64_t ev_cap[6] = {0, 0, 0, 0, 0, 0};  // E, start, cnt, list 0, list 1, radj (elements)
 
     std::mutex mu;
 };
@@ -201,6 +209,9 @@ void free_ws(exactz_workspace *ws)
     for (cudaEvent_t e : ws->kev)
         if (e) cudaEventDestroy(e);
     for (void *p : ws->allocs) cudaFree(p);
+    void *ev[6] = {ws->ev_E, ws->ev_start, ws->ev_cnt, ws->ev_list[0], ws->ev_list[1], ws->ev_radj};
+    for (void *p : ev)
+        if (p) cudaFree(p);
     if (ws->st_f) cudaFree(ws->st_f);
     if (ws->st_fhat) cudaFree(ws->st_fhat);
     if (ws->st_g) cudaFree(ws->st_g);
@@ -249,7 +260,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->reqw, W);
     AL(ws->dirty, W);
     AL(ws->gs, C);
-    AL(ws->pairbits, C / 32 + 1);
+    AL(ws->pairbits, 2 * ((C + 31) / 32) + 1);  // pair bits, then the event bits
     AL(ws->apply_flag, T);
     AL(ws->tile_flag, T);
     AL(ws->pin_tile_arena, T);
@@ -320,10 +331,15 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
 // Graph: [loop-flag kernel] -> while (flag) { check, pairs, apply, bookkeeping }.
 int ensure_graph(exactz_workspace *ws, const Dev &D)
 {
-    const uint64_t key[5] = {D.nfields, D.total_tiles, D.total_v, D.total_w,
+    uint64_t evk = D.events;
+    for (const void *p : {(const void *)D.ev_start, (const void *)D.ev_cnt, (const void *)D.ev_list[0],
+                          (const void *)D.ev_list[1], (const void *)D.ev_radj})
+        evk = (evk ^ (uint64_t)(uintptr_t)p) * 1099511628211ull;
+    const uint64_t key[6] = {D.nfields, D.total_tiles, D.total_v, D.total_w,
                              (uint64_t)(uintptr_t)D.o ^ ((uint64_t)D.tun.stencil_bps << 48) ^
                                  ((uint64_t)D.tun.apply_bps << 40) ^ ((uint64_t)D.tun.pairs_bps << 32) ^
-                                 ((uint64_t)D.tun.chunked << 56)};
+                                 ((uint64_t)D.tun.chunked << 56),
+                             evk};
     if (ws->gexec && std::memcmp(key, ws->gkey, sizeof(key)) == 0) return EXACTZ_OK;
     if (ws->gexec) {
         cudaGraphExecDestroy(ws->gexec);
@@ -392,6 +408,78 @@ int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
     return EXACTZ_OK;
 }
 
+// Grow one event buffer (index i of ws->ev_cap) to `need` elements; contents are not kept.
+template <class T>
+int ev_grow(exactz_workspace *ws, T *&p, int i, uint64_t need)
+{
+    if (need == 0) need = 1;
+    if (need <= ws->ev_cap[i]) return EXACTZ_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    ws->bytes -= ws->ev_cap[i] * sizeof(T);
+    ws->ev_cap[i] = 0;
+    CK(cudaMalloc(&p, need * sizeof(T)));
+    ws->ev_cap[i] = need;
+    ws->bytes += need * sizeof(T);
+    return EXACTZ_OK;
+}
+
+// Extremum graph of f for the original event constraints (Sec. 4.2): per
+// listed saddle the extrema its integral paths reach and their EGP selection,
+// per linked extremum the saddles it is linked to.  Runs after the sort (the
+// listed saddles are in D.o); synchronises the stream to size the lists.
+int event_setup(exactz_workspace *ws, Dev &D, const Layout &L, cudaStream_t s, uint64_t &launches)
+{
+    int rc;
+    LoopState *dls = ws->d_ls;
+    CK(cudaMemcpyAsync(ws->h_ls, dls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t nq = ws->h_ls->total_cp;
+    if ((rc = ev_grow(ws, ws->ev_E, 0, L.total_v)) || (rc = ev_grow(ws, ws->ev_start, 1, nq)) ||
+        (rc = ev_grow(ws, ws->ev_cnt, 2, nq)))
+        return rc;
+    D.ev_start = ws->ev_start;
+    D.ev_cnt = ws->ev_cnt;
+    uint64_t entries = 0;
+    for (int up = 0; up < 2; up++) {
+        launch_ev_init(D, ws->ev_E, up, s);
+        launches++;
+        // pointer jumping: each round at least doubles the distance covered, so
+        // a path of any length within the field ends within 64 rounds
+        int rounds = 0;
+        for (;; rounds++) {
+            if (rounds == 64) return EXACTZ_ENODEV;
+            CK(cudaMemsetAsync(&dls->ev_changed, 0, sizeof(uint32_t), s));
+            launch_ev_jump(D, ws->ev_E, s);
+            launches++;
+            CK(cudaMemcpyAsync(&ws->h_ls->ev_changed, &dls->ev_changed, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                               s));
+            CK(cudaStreamSynchronize(s));
+            if (!ws->h_ls->ev_changed) break;
+        }
+        CK(cudaMemsetAsync(&dls->ev_cursor[up], 0, sizeof(unsigned long long), s));
+        launch_ev_lists(D, ws->ev_E, up, 0, nullptr, ws->ev_start, ws->ev_cnt, s);
+        CK(cudaMemcpyAsync(&ws->h_ls->ev_cursor[up], &dls->ev_cursor[up], sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const uint64_t len = ws->h_ls->ev_cursor[up];
+        if (len >= (1ull << 32)) return EXACTZ_ESIZE;
+        if ((rc = ev_grow(ws, ws->ev_list[up], 3 + up, len))) return rc;
+        D.ev_list[up] = ws->ev_list[up];
+        CK(cudaMemsetAsync(&dls->ev_cursor[up], 0, sizeof(unsigned long long), s));
+        launch_ev_lists(D, ws->ev_E, up, 1, ws->ev_list[up], ws->ev_start, ws->ev_cnt, s);
+        launches += 2;
+        entries += len;
+    }
+    if (2 * entries + 1 >= (1ull << 32)) return EXACTZ_ESIZE;
+    if ((rc = ev_grow(ws, ws->ev_radj, 5, 2 * entries + 1))) return rc;
+    D.ev_radj = ws->ev_radj;
+    launch_ev_reverse(D, ws->ev_radj, s);
+    launches += 3;
+    CK(cudaGetLastError());
+    return EXACTZ_OK;
+}
+
 int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *const *fhat,
         const exactz_dims *d, const float *xi, const exactz_opts *o, float *const *g_out,
         exactz_edit *const *edits_out, const uint64_t *caps, exactz_result *res, cudaStream_t s,
@@ -400,7 +488,10 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     exactz_opts opt;
     exactz_default_opts(&opt);
     if (o) opt = *o;
-    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH) return EXACTZ_EINVAL;
+    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH || opt.events > EXACTZ_EVENTS_ORIGINAL ||
+        opt.reserved != 0)
+        return EXACTZ_EINVAL;
+    const bool events = opt.events == EXACTZ_EVENTS_ORIGINAL;
     if (!f || !fhat || !d || !xi || !g_out || !res) return EXACTZ_EINVAL;
     Layout L;
     int rc = make_layout(nf, d, L);
@@ -412,6 +503,9 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     if (nf > ws->cap_nf || L.total_v > ws->cap_v || L.total_w > ws->cap_w || L.total_tiles > ws->cap_tiles ||
         L.total_real > ws->cap_real)
         return EXACTZ_ESIZE;
+    if (events) {  // 32-bit vertex indices in the event lists and path ends
+        if (L.total_v >= (1ull << 32)) return EXACTZ_ESIZE;
+    }
     CK(cudaSetDevice(ws->device));
 
     uint64_t ecap_total = 0;
@@ -466,9 +560,10 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s));
     CK(cudaMemsetAsync(ws->tile_flag, 0, L.total_tiles, s));
     CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
-    CK(cudaMemsetAsync(ws->pairbits, 0, (L.total_real / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->pairbits, 0, (events ? 2 * ((ws->cap_real + 31) / 32) + 1 : L.total_real / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->apply_flag, 0, L.total_tiles, s));
-    const Dev D = make_dev(ws, L);
+    Dev D = make_dev(ws, L);
+    D.events = events ? 1u : 0u;
     const int frontier = opt.mode != EXACTZ_MODE_PLAIN;
     const bool prof = opt.profile != 0;
     auto mark = [&](int i) {
@@ -487,6 +582,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     launch_cp_compact(D, R, s);
     mark(2);
     launch_cp_sort(D, R, s);
+    if (events && (rc = event_setup(ws, D, L, s, launches)) != EXACTZ_OK) return rc;
     mark(3);
     launch_pairs_all(D, R, s);
     launch_apply(D, frontier, s);
@@ -563,7 +659,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         R.n_edits = S.n_edits;
         R.n_lossless = S.n_lossless;
         R.residual_violations = S.capped + S.pinned_res;
-        R.n_critical = S.ncp;
+        R.n_critical = events ? S.ncp_all : S.ncp;
         R.status = (int32_t)S.status;
         if (R.status < 0 && ret == EXACTZ_OK) ret = R.status;
         if (L.fd[i].edits && S.n_edits > L.fd[i].edits_cap && ret == EXACTZ_OK) ret = EXACTZ_ECAP;
@@ -612,6 +708,8 @@ void exactz_default_opts(exactz_opts *o)
     o->max_iters = 1000000;
     o->want_edit_list = 1;
     o->profile = 0;
+    o->events = EXACTZ_EVENTS_REFORMULATED;
+    o->reserved = 0;
 }
 
 exactz_workspace *exactz_workspace_create(uint32_t nfields, const exactz_dims *dims)
@@ -958,6 +1056,7 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     int rc = check_device();
     if (rc) return rc;
     if (!f || !fhat || !g_out || !res) return EXACTZ_EINVAL;
+    if (opts && opts->events != EXACTZ_EVENTS_REFORMULATED) return EXACTZ_EINVAL;  // its lists are allocated
     Layout L;
     if ((rc = make_layout(1, &d, L)) != EXACTZ_OK) return rc;
     if (L.total_real > EXACTZ_NOALLOC_MAX_VERTICES) return EXACTZ_ESIZE;

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
     __shared__ __align__(16) float sb[MODE == SM_SETUP ? NB : 1][MODE == SM_SETUP ? HALO_N : 4];
     __shared__ uint32_t smulti[512];
     __shared__ TileTargets tt;
-    __shared__ uint32_t s_err;
+    __shared__ uint32_t s_err, s_ncp;
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
     __shared__ uint8_t s_vis[MODE == SM_CHECK_LIST ? STWARPS : 1][TY * TX];  // a warp's dirty vertices (ly << 5 | lx)
     __shared__ uint32_t s_tile[2];        // the tile staged in each buffer
@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
     if (threadIdx.x == 0) {
         tt.nb = 0;
         s_err = 0;
+        s_ncp = 0;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float qnan = __int_as_float(0x7fc00000);
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
             const uint32_t x = (uint32_t)(x0 + lx), y = (uint32_t)(y0 + ly), z = (uint32_t)(z0 + lz);
             const bool in = sel && (interior || (x < nx && y < ny && z < nz));
             const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lx + XOFF);
-            bool cp = false;
+            bool cp = false, listed = false;
             uint32_t req = 0;
             const uint64_t i = wfirst + (uint64_t)ly * nx + (uint64_t)lx;  // lz == warp
             if (in) {
@@ -432,8 +433,9 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
                     const bool join = !mn && !mxx && multi_bit(smulti, L);
                     const bool split = !mn && !mxx && multi_bit(smulti, U);
                     cp = mn || mxx || join || split;
+                    listed = (MODE == SM_SETUP && D.events) ? (join || split) : cp;
                     const uint32_t d = sf.up | (sf.dn << 4) | (sf.mask << 8) |
-                                       ((join || split) ? D_SADDLE : 0u) | (cp ? D_CP : 0u);
+                                       ((join || split) ? D_SADDLE : 0u) | (listed ? D_CP : 0u);
                     if (MODE == SM_CLASSIFY) {
                         desc_out[i] = d;
                         if (type_out)
@@ -447,6 +449,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
                         if (e) atomicOr(&s_err, e);
                         D.desc[vbase + i] = d;  // edit count k = 0 in the top byte
                         F.g[i] = hv;
+                        if (D.events && (mn || mxx)) D.cp_rank[vbase + i] = 0;  // no linked saddle yet
                         Stn sg = interior ? stencil15<true>(SB, c) : stencil15<false>(SB, c);
                         req = request_mask(smulti, d, sg);
                     }
@@ -458,9 +461,13 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
             }
             if (MODE != SM_CLASSIFY && req) tile_targets_add(tt, lx, ly, lz, req);
             if (MODE == SM_SETUP) {
-                const uint32_t w = __ballot_sync(0xffffffffu, cp);
+                const uint32_t w = __ballot_sync(0xffffffffu, listed);
                 if (lane == 0 && y < ny && z < nz)
                     D.cpwords[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = w;
+                if (D.events) {
+                    const uint32_t c = __popc(__ballot_sync(0xffffffffu, cp));
+                    if (lane == 0 && c) atomicAdd(&s_ncp, c);
+                }
             }
         }
         __syncthreads();
@@ -468,6 +475,10 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
         if (MODE == SM_SETUP && threadIdx.x == 0 && s_err) {
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
+        }
+        if (MODE == SM_SETUP && threadIdx.x == 0 && s_ncp) {
+            atomicAdd(&D.fst[fid].ncp_all, (unsigned long long)s_ncp);
+            s_ncp = 0;
         }
         if (MODE == SM_CLASSIFY) __syncthreads();
     };
@@ -920,6 +931,63 @@ __global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const u
 // ------------------------------------------------------------ pair check (Sec. 4.3)
 enum { PM_ALL = 0, PM_LIST = 1, PM_PINNED = 2 };
 
+// Merge and split event constraint (Sec. 4.2, C3) at listed saddle q:
+// Extremum Graph Pairing selects, among the extrema linked to q in f, the
+// largest minimum and the smallest maximum (ties by index).  Where the
+// selection under g differs, the join side requests the g-selection and the
+// split side the f-selection, the lower of the two in f either way.  Writes the
+// tiles of the requests (pinned targets only with PINNED_ONLY); returns their
+// number.
+template <bool PINNED_ONLY>
+__device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, uint32_t *tiles)
+{
+    const uint32_t c = D.ev_cnt[q];
+    if (!c) return 0;
+    const unsigned long long ent = D.o[q];
+    const FieldDesc &F = D.fields[ent >> LOCAL_BITS];
+    const float *g = F.g;
+    const uint2 st = D.ev_start[q];
+    const uint32_t nm = c & 255u, nx = c >> 8;
+    uint32_t target[2];
+    int ntar = 0;
+    if (nm) {
+        const uint32_t *l = D.ev_list[0] + st.x;
+        const uint32_t sel = l[0];
+        uint32_t best = sel;
+        float bg = g[sel];
+        for (uint32_t j = 1; j < nm; j++) {
+            const uint32_t e = l[j];
+            const float ge = g[e];
+            if (bg < ge || (bg == ge && best < e)) {
+                best = e;
+                bg = ge;
+            }
+        }
+        if (best != sel) target[ntar++] = best;
+    }
+    if (nx) {
+        const uint32_t *l = D.ev_list[1] + st.y;
+        const uint32_t sel = l[0];
+        uint32_t best = sel;
+        float bg = g[sel];
+        for (uint32_t j = 1; j < nx; j++) {
+            const uint32_t e = l[j];
+            const float ge = g[e];
+            if (ge < bg || (ge == bg && e < best)) {
+                best = e;
+                bg = ge;
+            }
+        }
+        if (best != sel) target[ntar++] = sel;
+    }
+    int nt = 0;
+    for (int k = 0; k < ntar; k++) {
+        if (PINNED_ONLY && (D.desc[F.vbase + target[k]] >> D_K_SHIFT) <= F.N) continue;
+        tiles[nt++] = request_vertex(D, F, target[k]);
+    }
+    return nt;
+}
+
 // Rule R3 on adjacent pairs (q, q+1) of the sorted critical points, reading
 // their current values from gs (kept in sorted order by the apply kernel); the
 // sorted entries are gathered only to resolve a tie by index or to name the
@@ -928,6 +996,11 @@ enum { PM_ALL = 0, PM_LIST = 1, PM_PINNED = 2 };
 // kernel set in pairbits (always inside one field); each warp scans whole
 // words, takes and clears them, and each lane checks the pair of its bit.
 // PINNED: the pinned-pair lists of fields fids[0..nf), pinned targets only.
+// Under the original event constraints the listed points are the saddles
+// (the pairs are rule C2) and each mode also evaluates rule C3 at saddles:
+// ALL and PINNED at every listed saddle, LIST at those whose event bit (the
+// bits after the pair bits, set by the apply kernel when a linked extremum
+// changed) is set.
 template <int PM>
 __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsigned long long *countp,
                                                const uint32_t *fids, uint32_t nf)
@@ -957,7 +1030,8 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
     if (PM == PM_LIST) {
         // each warp takes 32 consecutive words of pairbits at a time (one per
         // lane), clears them, numbers their set bits and checks them 32 at once
-        const unsigned long long nwords = (D.cp_cap + 31) / 32;
+        const unsigned long long pw = (D.cp_cap + 31) / 32;  // pair-bit words; the event bits follow
+        const unsigned long long nwords = D.events ? 2 * pw : pw;
         const unsigned long long gw = ((unsigned long long)blockIdx.x * CTA + threadIdx.x) >> 5;
         const unsigned long long nw = stride >> 5;
         uint32_t npairs = 0;
@@ -989,7 +1063,14 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
                 uint32_t tile = 0;
                 if (k < total) {
                     const unsigned long long q = (c * 32 + src) * 32 + nth_set_bit(rword, (int)(k - rpre));
-                    if (check(q, tile) && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
+                    if (q < pw * 32) {
+                        if (check(q, tile) && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
+                    } else {
+                        uint32_t tl[2];
+                        const int nt = check_events<false>(D, q - pw * 32, tl);
+                        for (int u = 0; u < nt; u++)
+                            if (!D.apply_flag[tl[u]]) D.apply_flag[tl[u]] = 1;
+                    }
                 }
             }
         }
@@ -1011,6 +1092,16 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
             uint32_t tile = 0;
             if (check(list ? (unsigned long long)list[j] : cp0 + j, tile) && !D.apply_flag[tile])
                 D.apply_flag[tile] = 1;
+        }
+    }
+    if (D.events) {  // rule C3 at every listed saddle
+        const unsigned long long first = PM == PM_ALL ? cp0 : 0ull;
+        const unsigned long long count = PM == PM_ALL ? *countp : D.ls->total_cp;
+        for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
+            uint32_t tl[2];
+            const int nt = check_events<PM == PM_PINNED>(D, first + j, tl);
+            for (int u = 0; u < nt; u++)
+                if (!D.apply_flag[tl[u]]) D.apply_flag[tl[u]] = 1;
         }
     }
 }
@@ -1185,6 +1276,16 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                         D.desc[vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
                         pinned = kk == N + 1;
                         atomicOr(&s_cw[row], 1u << lx);
+                        if (AM == AM_FRONTIER && D.events && !(d & D_CP) && rk != 0 &&
+                            ((d & 15u) == 7u || ((d >> 4) & 15u) == 7u)) {
+                            // an extremum linked to saddles: their rule C3 is checked next pass
+                            const unsigned long long pw = (D.cp_cap + 31) / 32;
+                            const uint32_t deg = D.ev_radj[rk];
+                            for (uint32_t j = 0; j < deg; j++) {
+                                const uint32_t qq = D.ev_radj[rk + 1 + j];
+                                atomicOr(&D.pairbits[pw + (qq >> 5)], 1u << (qq & 31));
+                            }
+                        }
                         if (d & D_CP) {  // value in sorted order; pairs inside the field
                             const unsigned long long r = rk;
                             q = S->cp_base + r;
@@ -1280,6 +1381,210 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         __syncwarp();
     }
     if (AM != AM_COUNT && lane == 0 && nreq) atomicAdd(&D.ls->sum_requests, nreq);
+}
+
+// ------------------------------------------------------------ event lists (set-up, Sec. 4.2)
+// The extremum graph of f (Sec. 3.2 Step 1): a join saddle s is linked to the
+// minimum where the steepest-descent path from any neighbour below s ends (split
+// saddles: steepest ascent from the neighbours above, to maxima).  Path ends
+// of all vertices come from pointer jumping on the steepest-neighbour links
+// (E[v] <- E[E[v]] until nothing moves; in place, since every value E[v] ever
+// holds lies on v's path), as arena indices.
+
+// body(F, t, x, y, z, in) for the vertices of the tiles taken by this block
+// (every lane of every warp calls it the same number of times; `in` is false
+// outside the field).
+template <class Body>
+__device__ __forceinline__ void for_tile_vertices(const Dev &D, Body body)
+{
+    for (uint32_t tile = blockIdx.x; tile < D.total_tiles; tile += gridDim.x) {
+        const FieldDesc &F = D.fields[field_of_tile(D, tile)];
+        const uint32_t lt = tile - (uint32_t)F.tbase;
+        const uint32_t rest = fdiv(lt, F.div_tnx), tx = lt - rest * F.tnx;
+        const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * F.tny;
+        for (int j = threadIdx.x; j < TILE_V; j += CTA) {
+            const uint32_t x = tx * TX + (uint32_t)(j % TX), y = ty * TY + (uint32_t)((j / TX) % TY);
+            const uint32_t z = tz * TZ + (uint32_t)(j / (TX * TY));
+            const bool in = x < F.nx && y < F.ny && z < F.nz;
+            body(F, in ? (uint32_t)(((uint64_t)z * F.ny + y) * F.nx + x) : 0u, x, y, z, in);
+        }
+    }
+}
+
+// Signed index offset of neighbour rank r in a field.
+__device__ __forceinline__ int64_t rank_offset(const FieldDesc &F, int r)
+{
+    return (int64_t)rdx(r) + (int64_t)F.nx * ((int64_t)rdy(r) + (int64_t)F.ny * rdz(r));
+}
+
+// E[v] = steepest-descent (up = 0) or -ascent (up = 1) neighbour of v in f.
+__global__ void __launch_bounds__(CTA) k_ev_init(Dev D, uint32_t *E, int up)
+{
+    for_tile_vertices(D, [&](const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
+        if (!in) return;
+        const uint32_t d = D.desc[F.vbase + t];
+        const int r = up ? (int)(d & 15u) : (int)((d >> D_DN_SHIFT) & 15u);
+        E[F.vbase + t] = (uint32_t)((int64_t)(F.vbase + t) + rank_offset(F, r));
+    });
+}
+
+// One jump round; sets ls->ev_changed if some path end moved.
+__global__ void __launch_bounds__(CTA) k_ev_jump(Dev D, uint32_t *E)
+{
+    bool moved = false;
+    for_tile_vertices(D, [&](const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
+        if (!in) return;
+        const uint64_t a = F.vbase + t;
+        const uint32_t e = E[a];
+        const uint32_t e2 = E[e];
+        if (e2 != e) {
+            E[a] = e2;
+            moved = true;
+        }
+    });
+    if (__syncthreads_or(moved) && threadIdx.x == 0) D.ls->ev_changed = 1;
+}
+
+// The extrema linked to listed saddle q on side `up` (0: minima through the
+// neighbours below, 1: maxima through those above), distinct, the
+// f-selection first (largest minimum, smallest maximum, ties by index);
+// returns their number, or 0 when fewer than two.
+__device__ __forceinline__ uint32_t linked_extrema(const Dev &D, const uint32_t *E, unsigned long long q, int up,
+                                                   uint32_t *ext)
+{
+    const unsigned long long ent = D.o[q];
+    const FieldDesc &F = D.fields[ent >> LOCAL_BITS];
+    const uint32_t t = (uint32_t)(ent & LOCAL_MASK);
+    const uint32_t row = fdiv(t, F.div_nx), x = t - row * F.nx;
+    const uint32_t z = fdiv(row, F.div_ny), y = row - z * F.ny;
+    uint32_t valid = 0;
+#pragma unroll
+    for (int sl = 0; sl < 14; sl++) {
+        const int r = rank_of(sl);
+        const int64_t X = (int64_t)x + rdx(r), Y = (int64_t)y + rdy(r), Z = (int64_t)z + rdz(r);
+        if (X >= 0 && Y >= 0 && Z >= 0 && X < F.nx && Y < F.ny && Z < F.nz) valid |= 1u << sl;
+    }
+    const uint32_t L = (D.desc[F.vbase + t] >> D_MASK_SHIFT) & 0x3FFFu;
+    const uint32_t side = up ? (valid & ~L) : L;
+    if (!multi_bit(D.multi, side)) return 0;
+    uint32_t c = 0, bi = 0;
+    float bf = 0.0f;
+    for (uint32_t m = side; m; m &= m - 1) {
+        const int r = rank_of(__ffs(m) - 1);
+        const uint32_t e = E[F.vbase + (uint64_t)((int64_t)t + rank_offset(F, r))] - (uint32_t)F.vbase;
+        bool dup = false;
+        for (uint32_t i = 0; i < c; i++) dup |= ext[i] == e;
+        if (dup) continue;
+        const float fe = F.f[e];
+        if (c == 0) {
+            bf = fe;
+        } else {
+            const uint32_t b = ext[bi];
+            const bool better = up ? (fe < bf || (fe == bf && e < b)) : (bf < fe || (bf == fe && b < e));
+            if (better) {
+                bi = c;
+                bf = fe;
+            }
+        }
+        ext[c++] = e;
+    }
+    if (c < 2) return 0;
+    const uint32_t s0 = ext[0];
+    ext[0] = ext[bi];
+    ext[bi] = s0;
+    return c;
+}
+
+// WRITE = 0: add the list lengths of side `up` to ls->ev_cursor[up].
+// WRITE = 1: place the lists in `list` (space reserved from ev_cursor[up]),
+// record their starts and lengths.
+template <int WRITE>
+__global__ void __launch_bounds__(CTA) k_ev_lists(Dev D, const uint32_t *E, int up, uint32_t *list, uint2 *start,
+                                                  uint16_t *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = D.ls->total_cp;
+    const unsigned long long w0 = ((unsigned long long)blockIdx.x * CTA + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * CTA) >> 5;
+    unsigned long long sum = 0;
+    for (unsigned long long base = w0 * 32; base < total; base += nw * 32) {
+        const unsigned long long q = base + lane;
+        uint32_t ext[14];
+        const uint32_t c = q < total ? linked_extrema(D, E, q, up, ext) : 0u;
+        if (!WRITE) {
+            sum += c;
+            continue;
+        }
+        const unsigned long long pos = warp_reserve(c, &D.ls->ev_cursor[up]);
+        if (q < total) {
+            for (uint32_t i = 0; i < c; i++) list[pos + i] = ext[i];
+            reinterpret_cast<uint32_t *>(start)[2 * q + up] = c ? (uint32_t)pos : 0u;
+            cnt[q] = (uint16_t)(up ? (cnt[q] | (c << 8)) : c);
+        }
+    }
+    if (!WRITE) {
+        sum = __reduce_add_sync(0xffffffffu, (uint32_t)sum);
+        if (lane == 0 && sum) atomicAdd(&D.ls->ev_cursor[up], sum);
+    }
+}
+
+// Reverse links, step 1: cp_rank[e] (0 for every extremum after the set-up
+// check) counts the saddles linked to extremum e; ev_cursor[2] = 1 (position 0
+// of ev_radj is never used, so cp_rank 0 means "no linked saddle").
+__global__ void __launch_bounds__(CTA) k_ev_degree(Dev D)
+{
+    const unsigned long long total = D.ls->total_cp;
+    if (blockIdx.x == 0 && threadIdx.x == 0) D.ls->ev_cursor[2] = 1;
+    for (unsigned long long q = (unsigned long long)blockIdx.x * CTA + threadIdx.x; q < total;
+         q += (unsigned long long)gridDim.x * CTA) {
+        const uint32_t c = D.ev_cnt[q];
+        if (!c) continue;
+        const FieldDesc &F = D.fields[D.o[q] >> LOCAL_BITS];
+        const uint2 st = D.ev_start[q];
+        for (uint32_t i = 0; i < (c & 255u); i++) atomicAdd(&D.cp_rank[F.vbase + D.ev_list[0][st.x + i]], 1u);
+        for (uint32_t i = 0; i < (c >> 8); i++) atomicAdd(&D.cp_rank[F.vbase + D.ev_list[1][st.y + i]], 1u);
+    }
+}
+
+// Step 2: every linked extremum gets its slot run in ev_radj (count first).
+__global__ void __launch_bounds__(CTA) k_ev_alloc(Dev D, uint32_t *radj)
+{
+    for_tile_vertices(D, [&](const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
+        uint32_t deg = 0;
+        uint64_t a = 0;
+        if (in) {
+            a = F.vbase + t;
+            const uint32_t d = D.desc[a];
+            if (!(d & D_CP) && ((d & 15u) == 7u || ((d >> D_DN_SHIFT) & 15u) == 7u)) deg = D.cp_rank[a];
+        }
+        const unsigned long long h = warp_reserve(deg ? deg + 1 : 0u, &D.ls->ev_cursor[2]);
+        if (deg) {
+            radj[h] = 0;
+            D.cp_rank[a] = (uint32_t)h;
+        }
+    });
+}
+
+// Step 3: the saddles of each extremum.
+__global__ void __launch_bounds__(CTA) k_ev_fill(Dev D, uint32_t *radj)
+{
+    const unsigned long long total = D.ls->total_cp;
+    for (unsigned long long q = (unsigned long long)blockIdx.x * CTA + threadIdx.x; q < total;
+         q += (unsigned long long)gridDim.x * CTA) {
+        const uint32_t c = D.ev_cnt[q];
+        if (!c) continue;
+        const FieldDesc &F = D.fields[D.o[q] >> LOCAL_BITS];
+        const uint2 st = D.ev_start[q];
+        for (int up = 0; up < 2; up++) {
+            const uint32_t n = up ? (c >> 8) : (c & 255u);
+            const uint32_t *l = D.ev_list[up] + (up ? st.y : st.x);
+            for (uint32_t i = 0; i < n; i++) {
+                const uint32_t h = D.cp_rank[F.vbase + l[i]];
+                const uint32_t slot = atomicAdd(&radj[h], 1u);
+                radj[h + 1 + slot] = (uint32_t)q;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------ bookkeeping
@@ -1543,6 +1848,27 @@ void launch_pairs_list(const Dev &D, cudaStream_t s)
 void launch_pairs_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s)
 {
     k_pairs<PM_PINNED><<<sms() * 4, CTA, 0, s>>>(D, 0, nullptr, FS.fids, FS.n);
+}
+
+void launch_ev_init(const Dev &D, uint32_t *E, int up, cudaStream_t s)
+{
+    k_ev_init<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, E, up);
+}
+void launch_ev_jump(const Dev &D, uint32_t *E, cudaStream_t s)
+{
+    k_ev_jump<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, E);
+}
+void launch_ev_lists(const Dev &D, const uint32_t *E, int up, int write, uint32_t *list, uint2 *start,
+                     uint16_t *cnt, cudaStream_t s)
+{
+    if (write) k_ev_lists<1><<<sms() * 8, CTA, 0, s>>>(D, E, up, list, start, cnt);
+    else k_ev_lists<0><<<sms() * 8, CTA, 0, s>>>(D, E, up, list, start, cnt);
+}
+void launch_ev_reverse(const Dev &D, uint32_t *radj, cudaStream_t s)
+{
+    k_ev_degree<<<sms() * 8, CTA, 0, s>>>(D);
+    k_ev_alloc<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, radj);
+    k_ev_fill<<<sms() * 8, CTA, 0, s>>>(D, radj);
 }
 
 void launch_apply(const Dev &D, int frontier, cudaStream_t s)
