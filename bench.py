@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--size", type=int, default=0, help="override the cube side (profiling runs)")
     p.add_argument("--rel", type=float, default=0.0, help="override xi / range of the workload")
     p.add_argument("--mode", default="graph", choices=["graph", "frontier", "plain"])
+    p.add_argument("--events", default="reformulated", choices=["reformulated", "original"],
+                   help="event constraints of the timed correction (Sec. 4.3 or Sec. 4.2)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
@@ -210,14 +212,14 @@ def ncu_traffic(kernel: str, workload: str):
     return None
 
 
-def oracle_sample(f, fh, xi, side: int):
+def oracle_sample(f, fh, xi, side: int, events: str = "reformulated"):
     """Run the oracle (plain mode, as it stands) on the side^3 corner crop."""
     import oracle
 
     fc = np.ascontiguousarray(f[:side, :side, :side])
     hc = np.ascontiguousarray(fh[:side, :side, :side])
     t0 = time.perf_counter()
-    r = oracle.correct(fc.reshape(-1), hc.reshape(-1), xi, dims=(side, side, side))
+    r = oracle.correct(fc.reshape(-1), hc.reshape(-1), xi, dims=(side, side, side), events=events == "original")
     return time.perf_counter() - t0, r
 
 
@@ -226,9 +228,9 @@ def omp_threads() -> int:
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
-def choose_side(f, fh, xi, budget_s: float, lo=32, hi=256):
+def choose_side(f, fh, xi, budget_s: float, lo=32, hi=256, events: str = "reformulated"):
     """Pick a crop side whose oracle run takes about budget_s (calibrated on a small crop)."""
-    t, _ = oracle_sample(f, fh, xi, lo)
+    t, _ = oracle_sample(f, fh, xi, lo, events)
     per = t / lo ** 3
     side = int((budget_s / max(per, 1e-12)) ** (1 / 3))
     return max(lo, min(hi, side, min(f.shape)))
@@ -245,22 +247,23 @@ def run_reference(a):
     f, fh, xi = make_fields(c, "cpu")
     f, fh = f.numpy(), fh.numpy()
     budget = max(2.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
-    side = choose_side(f, fh, xi, budget)
+    side = choose_side(f, fh, xi, budget, events=a.events)
     for _ in range(a.warmup):
-        oracle_sample(f, fh, xi, side)
+        oracle_sample(f, fh, xi, side, a.events)
     times = []
     for _ in range(a.steps):
-        t, r = oracle_sample(f, fh, xi, side)
+        t, r = oracle_sample(f, fh, xi, side, a.events)
         times.append(t)
     ms = 1e3 * statistics.mean(times)
     val = 4.0 * side ** 3 / (ms / 1e3) / 1e9
     cores = omp_threads()
     sample = (f"{side}^3 corner crop of the {c['name']} workload ({side ** 3} vertices), plain oracle "
-              f"(full sweep each pass), to fixpoint: {r['iterations']} passes, {r['n_edits']} edits")
+              f"(full sweep each pass, {a.events} event constraints), to fixpoint: {r['iterations']} passes, "
+              f"{r['n_edits']} edits")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": describe(c), "sample": sample},
+            "config": {"workload": describe(c), "events": a.events, "sample": sample},
             "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -294,10 +297,11 @@ def run_ours(a):
     ebuf = torch.empty((cap, 16), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(mode=a.mode, profile=True):
-        return ws.correct([f], [fh], [xi], mode=mode, g_out=[g], edit_bufs=[ebuf], profile=profile)[0]
+    def step(mode=a.mode, profile=True, events=a.events):
+        return ws.correct([f], [fh], [xi], mode=mode, g_out=[g], edit_bufs=[ebuf], profile=profile,
+                          events=events)[0]
 
-    tuning = ws.autotune([f], [fh], [xi], repeats=2) if not a.no_autotune else ws.tuning()
+    tuning = ws.autotune([f], [fh], [xi], repeats=2, events=a.events) if not a.no_autotune else ws.tuning()
 
     for _ in range(max(3, a.warmup)):
         r = step()
@@ -380,6 +384,22 @@ def run_ours(a):
         extras[f"{a.mode}_ms"] = ms
         if "plain_ms" in extras:
             extras["speedup_vs_plain"] = extras["plain_ms"] / ms
+        # the other event-constraint set on the same input (Sec. 4.2 vs 4.3)
+        other = "original" if a.events == "reformulated" else "reformulated"
+        step(a.mode, True, other)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ro = step(a.mode, True, other)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        so = ws.stats()
+        oms = e0.elapsed_time(e1)
+        extras[f"{other}_events"] = {
+            "ms": oms, "gbs": 4.0 * n / (oms / 1e3) / 1e9, "ratio_to_timed": oms / ms,
+            "iterations": ro["iterations"], "status": ro["status_name"], "n_edits": ro["n_edits"],
+            "n_lossless": ro["n_lossless"], "listed_points": so["total_critical"],
+            "stage_ms": so["stage_ms"]}
+        step(a.mode, False)  # leave g and the edit list of the timed configuration
 
     e2e = None
     if not a.no_e2e:
@@ -387,11 +407,12 @@ def run_ours(a):
         hc = fh.cpu().pin_memory()
         gc = torch.empty_like(fc).pin_memory()
         ec = torch.empty((cap, 16), dtype=torch.uint8).pin_memory()
-        ws.correct([fc], [hc], [xi], g_out=[gc], edit_bufs=[ec], host_buffers=True, mode=a.mode)
+        ws.correct([fc], [hc], [xi], g_out=[gc], edit_bufs=[ec], host_buffers=True, mode=a.mode, events=a.events)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(a.steps):
-            rh = ws.correct([fc], [hc], [xi], g_out=[gc], edit_bufs=[ec], host_buffers=True, mode=a.mode)[0]
+            rh = ws.correct([fc], [hc], [xi], g_out=[gc], edit_bufs=[ec], host_buffers=True, mode=a.mode,
+                            events=a.events)[0]
         torch.cuda.synchronize()
         ems = 1e3 * (time.perf_counter() - t0) / a.steps
         e2e = {"value": 4.0 * n / (ems / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
@@ -401,8 +422,8 @@ def run_ours(a):
     cpu = None
     if not a.no_cpu and world == 1:
         fn, hn = f.cpu().numpy(), fh.cpu().numpy()
-        side = choose_side(fn, hn, xi, 15.0)
-        t, ro = oracle_sample(fn, hn, xi, side)
+        side = choose_side(fn, hn, xi, 15.0, events=a.events)
+        t, ro = oracle_sample(fn, hn, xi, side, a.events)
         cpu = {"value": 4.0 * side ** 3 / t / 1e9, "unit": "GB/s", "cores": omp_threads(), "kind": "oracle",
                "sample": f"{side}^3 corner crop of this workload, plain oracle to fixpoint "
                          f"({ro['iterations']} passes, {t:.1f} s)"}
@@ -410,7 +431,8 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
             "warmup": max(3, a.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": describe(c), "mode": a.mode, "l2": "inputs larger than L2 (4n bytes per field)",
+            "config": {"workload": describe(c), "mode": a.mode, "events": a.events,
+                       "l2": "inputs larger than L2 (4n bytes per field)",
                        "parallelism": f"replicas x{world}", "tuning": tuning},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * 1,
             "clocks": clk, "extras": extras}

@@ -74,7 +74,7 @@ extern "C" {
 #define EXACTZ_EVENTS_REFORMULATED 0 /* global order of all critical points (Sec. 4.3) */
 #define EXACTZ_EVENTS_ORIGINAL 1     /* saddle order C2 + extremum-graph merge/split events C3 (Sec. 4.2);
                                         set-up traces the integral paths of f once (pointer jumping);
-                                        every field below 2^32 vertices, the workspace below 2^32 */
+                                        the workspace's fields below 2^31 vertices in all */
 
 typedef struct {
     uint32_t nx, ny, nz;

@@ -316,12 +316,12 @@ typedef struct {
     int events;
     int64_t *so;      /* saddles of f, sorted by the f-order */
     int64_t nso;
-    int64_t *ev_ext;  /* per vertex, up to EV_MAX extrema: minima of a join saddle, then maxima of a split */
+    int64_t *ev_ext;  /* per sorted saddle q, up to EV_MAX extrema: minima of a join saddle, then maxima of a split */
     uint8_t *ev_nmin, *ev_nmax;
-    int64_t *sel_min, *sel_max;  /* EGP selection in f, -1 if none */
+    int64_t *sel_min, *sel_max;  /* per sorted saddle: EGP selection in f, -1 if none */
 } ctx_t;
 
-#define EV_MAX 16
+#define EV_MAX 14 /* the neighbours of a vertex */
 
 static void mark(uint8_t *req, int64_t x)
 {
@@ -365,22 +365,22 @@ static void check_saddle_pair(const ctx_t *C, const float *g, int64_t q, uint8_t
     if (prec(g, b, a)) mark(req, a);
 }
 
-/* C3 at saddle s: the EGP selection among its connected extrema in g. */
-static void check_events(const ctx_t *C, const float *g, int64_t s, uint8_t *req)
+/* C3 at the sorted saddle so[q]: the EGP selection among its connected extrema in g. */
+static void check_events(const ctx_t *C, const float *g, int64_t q, uint8_t *req)
 {
-    const int64_t *e = C->ev_ext + s * EV_MAX;
-    int nm = C->ev_nmin[s], nx = C->ev_nmax[s];
-    if (C->sel_min[s] >= 0) {
+    const int64_t *e = C->ev_ext + q * EV_MAX;
+    int nm = C->ev_nmin[q], nx = C->ev_nmax[q];
+    if (C->sel_min[q] >= 0) {
         int64_t best = e[0];
         for (int j = 1; j < nm; j++)
             if (prec(g, best, e[j])) best = e[j];
-        if (best != C->sel_min[s]) mark(req, best);
+        if (best != C->sel_min[q]) mark(req, best);
     }
-    if (C->sel_max[s] >= 0) {
+    if (C->sel_max[q] >= 0) {
         int64_t best = e[nm];
         for (int j = 1; j < nx; j++)
             if (prec(g, e[nm + j], best)) best = e[nm + j];
-        if (best != C->sel_max[s]) mark(req, C->sel_max[s]);
+        if (best != C->sel_max[q]) mark(req, C->sel_max[q]);
     }
 }
 
@@ -406,16 +406,24 @@ static int64_t check_full(const ctx_t *C, const float *g, uint8_t *req)
 #pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < npairs; q++) check_saddle_pair(C, g, q, req);
 #pragma omp parallel for schedule(static)
-        for (int64_t q = 0; q < C->nso; q++) check_events(C, g, C->so[q], req);
+        for (int64_t q = 0; q < C->nso; q++) check_events(C, g, q, req);
     }
     return count_set(req, C->G.n);
 }
 
-/* Terminal extremum of the integral path from v along the steepest links. */
-static int64_t path_end(const int64_t *step, int64_t v)
+/* Terminal extremum of the integral path from v along the steepest links.
+ * end[] (-1 = not known yet) remembers the terminal of every vertex walked, so
+ * that paths shared by many saddles are walked once. */
+static int64_t path_end(const int64_t *step, int64_t *end, int64_t v)
 {
-    while (step[v] != v) v = step[v];
-    return v;
+    int64_t u = v;
+    while (end[u] < 0 && step[u] != u) u = step[u];
+    const int64_t m = end[u] >= 0 ? end[u] : u;
+    for (int64_t w = v; end[w] < 0; w = step[w]) {
+        end[w] = m;
+        if (w == u) break;
+    }
+    return m;
 }
 
 /* The extremum graph of f at its saddles and its EGP selections (C3), and the
@@ -423,58 +431,70 @@ static int64_t path_end(const int64_t *step, int64_t v)
 static int setup_events(ctx_t *C)
 {
     const int64_t n = C->G.n;
-    C->so = malloc(sizeof(int64_t) * n);
-    C->ev_ext = malloc(sizeof(int64_t) * n * EV_MAX);
-    C->ev_nmin = calloc((size_t)n, 1);
-    C->ev_nmax = calloc((size_t)n, 1);
-    C->sel_min = malloc(sizeof(int64_t) * n);
-    C->sel_max = malloc(sizeof(int64_t) * n);
+    int64_t nso = 0;
+    for (int64_t q = 0; q < C->ncp; q++) nso += (C->tyf[C->o[q]] & (T_JOIN | T_SPLIT)) != 0;
+    const size_t m = (size_t)(nso > 0 ? nso : 1);
+    C->so = malloc(sizeof(int64_t) * m);
+    C->ev_ext = malloc(sizeof(int64_t) * m * EV_MAX);
+    C->ev_nmin = calloc(m, 1);
+    C->ev_nmax = calloc(m, 1);
+    C->sel_min = malloc(sizeof(int64_t) * m);
+    C->sel_max = malloc(sizeof(int64_t) * m);
     if (!C->so || !C->ev_ext || !C->ev_nmin || !C->ev_nmax || !C->sel_min || !C->sel_max) return OR_ENOMEM;
     C->nso = 0;
     for (int64_t q = 0; q < C->ncp; q++)
         if (C->tyf[C->o[q]] & (T_JOIN | T_SPLIT)) C->so[C->nso++] = C->o[q];
-    for (int64_t p = 0; p < n; p++) C->sel_min[p] = C->sel_max[p] = -1;
+    for (int64_t q = 0; q < nso; q++) C->sel_min[q] = C->sel_max[q] = -1;
+    int64_t *end_dn = malloc(sizeof(int64_t) * n), *end_up = malloc(sizeof(int64_t) * n);
+    if (!end_dn || !end_up) {
+        free(end_dn);
+        free(end_up);
+        return OR_ENOMEM;
+    }
+    for (int64_t p = 0; p < n; p++) end_dn[p] = end_up[p] = -1;
     for (int64_t q = 0; q < C->nso; q++) {
         const int64_t s = C->so[q];
         int64_t nb[32];
         int slot[32];
         const int cnt = neighbours(&C->G, s, nb, slot);
-        int64_t *e = C->ev_ext + s * EV_MAX;
+        int64_t *e = C->ev_ext + q * EV_MAX;
         int ne = 0;
         if (C->tyf[s] & T_JOIN) {
             for (int j = 0; j < cnt; j++) {
                 if (!prec(C->f, nb[j], s)) continue;
-                const int64_t m = path_end(C->dnf, nb[j]);
+                const int64_t m = path_end(C->dnf, end_dn, nb[j]);
                 int dup = 0;
                 for (int i = 0; i < ne; i++) dup |= e[i] == m;
                 if (!dup) e[ne++] = m;
             }
-            C->ev_nmin[s] = (uint8_t)ne;
+            C->ev_nmin[q] = (uint8_t)ne;
             if (ne >= 2) {
                 int64_t best = e[0];
                 for (int i = 1; i < ne; i++)
                     if (prec(C->f, best, e[i])) best = e[i];
-                C->sel_min[s] = best;
+                C->sel_min[q] = best;
             }
         }
         const int nm = ne;
         if (C->tyf[s] & T_SPLIT) {
             for (int j = 0; j < cnt; j++) {
                 if (!prec(C->f, s, nb[j])) continue;
-                const int64_t m = path_end(C->upf, nb[j]);
+                const int64_t m = path_end(C->upf, end_up, nb[j]);
                 int dup = 0;
                 for (int i = nm; i < ne; i++) dup |= e[i] == m;
                 if (!dup) e[ne++] = m;
             }
-            C->ev_nmax[s] = (uint8_t)(ne - nm);
+            C->ev_nmax[q] = (uint8_t)(ne - nm);
             if (ne - nm >= 2) {
                 int64_t best = e[nm];
                 for (int i = nm + 1; i < ne; i++)
                     if (prec(C->f, e[i], best)) best = e[i];
-                C->sel_max[s] = best;
+                C->sel_max[q] = best;
             }
         }
     }
+    free(end_dn);
+    free(end_up);
     return 0;
 }
 

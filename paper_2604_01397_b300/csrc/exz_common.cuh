@@ -198,17 +198,17 @@ struct Dev {
     // Original event constraints (Sec. 4.2), events != 0: the sorted list holds
     // the saddles of f only (C2 on its adjacent pairs), and per listed saddle q
     // the extrema its integral paths reach in f (C3): ev_cnt[q] = number of
-    // linked minima | maxima << 8 (a side with fewer than two counts 0),
-    // ev_start[q] = their first positions in ev_list[0] / ev_list[1] (field-local
-    // vertex indices, the f-selection of Extremum Graph Pairing first).  For a
-    // linked extremum e, cp_rank[e] = h > 0 points into ev_radj: ev_radj[h] =
-    // its number of linked saddles, followed by their positions q.  The event
-    // bits of the next pass follow the pair bits in pairbits, from word ev_word0.
+    // linked minima | maxima << 8 (a side with fewer than two counts 0);
+    // ev_list[ev_start[q] ...] holds the minima, then the maxima (field-local
+    // vertex indices, each side's f-selection of Extremum Graph Pairing first).
+    // For a linked extremum e, cp_rank[e] = h > 0 points into ev_radj:
+    // ev_radj[h] = its number of linked saddles, followed by their positions q.
+    // In pairbits, the pair bits are followed by the event bits of the next
+    // pass and the event bits of the residual check, one word range each.
     uint32_t events;
-    uint64_t ev_word0;
-    const uint2 *ev_start;
+    const uint32_t *ev_start;
     const uint16_t *ev_cnt;
-    const uint32_t *ev_list[2];
+    const uint32_t *ev_list;
     const uint32_t *ev_radj;
 };
 

@@ -173,11 +173,14 @@ struct exactz_workspace {
 
     // extremum-graph lists of the original event constraints, grown on demand
     uint32_t *ev_E = nullptr;  // path ends (set-up scratch), one per arena vertex
-    uint2 *ev_start = nullptr;
+    uint32_t *ev_start = nullptr;
     uint16_t *ev_cnt = nullptr;
-    uint32_t *ev_list[2] = {nullptr, nullptr};
+    uint32_t *ev_list = nullptr;
     uint32_t *ev_radj = nullptr;
-    uint64_t ev_cap[6] = {0, 0, 0, 0, 0, 0};  // E, start, cnt, list 0, list 1, radj (elements)
+    uint32_t *ev_room = nullptr;                 // list room per 32 words of the listed-point bitmap
+    unsigned long long *ev_room_off = nullptr;   // its exclusive prefix sums
+    uint8_t *ev_tdone = nullptr;                 // per tile: every path end found
+    uint64_t ev_cap[8] = {};  // E, start, cnt, list, radj, room, room_off, tdone (elements)
 
     std::mutex mu;
 };
@@ -209,7 +212,8 @@ void free_ws(exactz_workspace *ws)
     for (cudaEvent_t e : ws->kev)
         if (e) cudaEventDestroy(e);
     for (void *p : ws->allocs) cudaFree(p);
-    void *ev[6] = {ws->ev_E, ws->ev_start, ws->ev_cnt, ws->ev_list[0], ws->ev_list[1], ws->ev_radj};
+    void *ev[8] = {ws->ev_E,    ws->ev_start, ws->ev_cnt,      ws->ev_list,
+                   ws->ev_radj, ws->ev_room,  ws->ev_room_off, ws->ev_tdone};
     for (void *p : ev)
         if (p) cudaFree(p);
     if (ws->st_f) cudaFree(ws->st_f);
@@ -260,7 +264,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->reqw, W);
     AL(ws->dirty, W);
     AL(ws->gs, C);
-    AL(ws->pairbits, 2 * ((C + 31) / 32) + 1);  // pair bits, then the event bits
+    AL(ws->pairbits, 3 * ((C + 31) / 32) + 1);  // pair bits, then the event and pinned event bits
     AL(ws->apply_flag, T);
     AL(ws->tile_flag, T);
     AL(ws->pin_tile_arena, T);
@@ -332,8 +336,8 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
 int ensure_graph(exactz_workspace *ws, const Dev &D)
 {
     uint64_t evk = D.events;
-    for (const void *p : {(const void *)D.ev_start, (const void *)D.ev_cnt, (const void *)D.ev_list[0],
-                          (const void *)D.ev_list[1], (const void *)D.ev_radj})
+    for (const void *p : {(const void *)D.ev_start, (const void *)D.ev_cnt, (const void *)D.ev_list,
+                          (const void *)D.ev_radj})
         evk = (evk ^ (uint64_t)(uintptr_t)p) * 1099511628211ull;
     const uint64_t key[6] = {D.nfields, D.total_tiles, D.total_v, D.total_w,
                              (uint64_t)(uintptr_t)D.o ^ ((uint64_t)D.tun.stencil_bps << 48) ^
@@ -427,52 +431,50 @@ int ev_grow(exactz_workspace *ws, T *&p, int i, uint64_t need)
 // Extremum graph of f for the original event constraints (Sec. 4.2): per
 // listed saddle the extrema its integral paths reach and their EGP selection,
 // per linked extremum the saddles it is linked to.  Runs after the sort (the
-// listed saddles are in D.o); synchronises the stream to size the lists.
+// listed saddles and their positions are known); synchronises the stream to
+// follow the pointer jumping and to size the lists.
 int event_setup(exactz_workspace *ws, Dev &D, const Layout &L, cudaStream_t s, uint64_t &launches)
 {
     int rc;
     LoopState *dls = ws->d_ls;
-    CK(cudaMemcpyAsync(ws->h_ls, dls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    LoopState *hls = ws->h_ls;
+    CK(cudaMemcpyAsync(hls, dls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const uint64_t nq = ws->h_ls->total_cp;
-    if ((rc = ev_grow(ws, ws->ev_E, 0, L.total_v)) || (rc = ev_grow(ws, ws->ev_start, 1, nq)) ||
-        (rc = ev_grow(ws, ws->ev_cnt, 2, nq)))
+    const uint64_t nq = hls->total_cp;
+    const uint64_t nchunks = (L.total_w + 31) / 32;
+    if ((rc = ev_grow(ws, ws->ev_E, 0, 2 * L.total_v)) || (rc = ev_grow(ws, ws->ev_start, 1, nq)) ||
+        (rc = ev_grow(ws, ws->ev_cnt, 2, nq)) || (rc = ev_grow(ws, ws->ev_room, 5, nchunks)) ||
+        (rc = ev_grow(ws, ws->ev_room_off, 6, nchunks)) || (rc = ev_grow(ws, ws->ev_tdone, 7, L.total_tiles)))
         return rc;
     D.ev_start = ws->ev_start;
     D.ev_cnt = ws->ev_cnt;
-    uint64_t entries = 0;
-    for (int up = 0; up < 2; up++) {
-        launch_ev_init(D, ws->ev_E, up, s);
+    CK(cudaMemsetAsync(ws->ev_tdone, 0, L.total_tiles, s));
+    // room for the lists (no path is followed yet), while the links are set up
+    launch_ev_lists(D, nullptr, 0, ws->ev_room, nullptr, nullptr, nullptr, nullptr, s);
+    launch_scan_u32(ws->ev_room, ws->ev_room_off, nchunks, &dls->ev_cursor[0], s);
+    launch_ev_init(D, ws->ev_E, s);
+    launches += 3;
+    // pointer jumping: each round at least doubles the distance covered, so
+    // every path within a field ends within 64 rounds
+    for (int rounds = 0;; rounds++) {
+        if (rounds == 64) return EXACTZ_ENODEV;
+        CK(cudaMemsetAsync(&dls->ev_changed, 0, sizeof(uint32_t), s));
+        launch_ev_jump(D, ws->ev_E, ws->ev_tdone, s);
         launches++;
-        // pointer jumping: each round at least doubles the distance covered, so
-        // a path of any length within the field ends within 64 rounds
-        int rounds = 0;
-        for (;; rounds++) {
-            if (rounds == 64) return EXACTZ_ENODEV;
-            CK(cudaMemsetAsync(&dls->ev_changed, 0, sizeof(uint32_t), s));
-            launch_ev_jump(D, ws->ev_E, s);
-            launches++;
-            CK(cudaMemcpyAsync(&ws->h_ls->ev_changed, &dls->ev_changed, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                               s));
-            CK(cudaStreamSynchronize(s));
-            if (!ws->h_ls->ev_changed) break;
-        }
-        CK(cudaMemsetAsync(&dls->ev_cursor[up], 0, sizeof(unsigned long long), s));
-        launch_ev_lists(D, ws->ev_E, up, 0, nullptr, ws->ev_start, ws->ev_cnt, s);
-        CK(cudaMemcpyAsync(&ws->h_ls->ev_cursor[up], &dls->ev_cursor[up], sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hls, dls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        const uint64_t len = ws->h_ls->ev_cursor[up];
-        if (len >= (1ull << 32)) return EXACTZ_ESIZE;
-        if ((rc = ev_grow(ws, ws->ev_list[up], 3 + up, len))) return rc;
-        D.ev_list[up] = ws->ev_list[up];
-        CK(cudaMemsetAsync(&dls->ev_cursor[up], 0, sizeof(unsigned long long), s));
-        launch_ev_lists(D, ws->ev_E, up, 1, ws->ev_list[up], ws->ev_start, ws->ev_cnt, s);
-        launches += 2;
-        entries += len;
+        if (!hls->ev_changed) break;
     }
+    const uint64_t room = hls->ev_cursor[0];
+    if (room >= (1ull << 32)) return EXACTZ_ESIZE;
+    if ((rc = ev_grow(ws, ws->ev_list, 3, room))) return rc;
+    D.ev_list = ws->ev_list;
+    launch_ev_lists(D, ws->ev_E, 1, nullptr, ws->ev_room_off, ws->ev_list, ws->ev_start, ws->ev_cnt, s);
+    CK(cudaMemcpyAsync(hls, dls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t entries = hls->ev_cursor[1];
     if (2 * entries + 1 >= (1ull << 32)) return EXACTZ_ESIZE;
-    if ((rc = ev_grow(ws, ws->ev_radj, 5, 2 * entries + 1))) return rc;
+    if ((rc = ev_grow(ws, ws->ev_radj, 4, 2 * entries + 1))) return rc;
     D.ev_radj = ws->ev_radj;
     launch_ev_reverse(D, ws->ev_radj, s);
     launches += 3;
@@ -503,8 +505,8 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     if (nf > ws->cap_nf || L.total_v > ws->cap_v || L.total_w > ws->cap_w || L.total_tiles > ws->cap_tiles ||
         L.total_real > ws->cap_real)
         return EXACTZ_ESIZE;
-    if (events) {  // 32-bit vertex indices in the event lists and path ends
-        if (L.total_v >= (1ull << 32)) return EXACTZ_ESIZE;
+    if (events) {  // 31-bit arena indices in the path ends, 32-bit positions in the event lists
+        if (L.total_v >= (1ull << 31)) return EXACTZ_ESIZE;
     }
     CK(cudaSetDevice(ws->device));
 
@@ -560,7 +562,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemsetAsync(ws->d_ls, 0, sizeof(LoopState), s));
     CK(cudaMemsetAsync(ws->tile_flag, 0, L.total_tiles, s));
     CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
-    CK(cudaMemsetAsync(ws->pairbits, 0, (events ? 2 * ((ws->cap_real + 31) / 32) + 1 : L.total_real / 32 + 1) * 4, s));
+    CK(cudaMemsetAsync(ws->pairbits, 0, (events ? 3 * ((ws->cap_real + 31) / 32) + 1 : L.total_real / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->apply_flag, 0, L.total_tiles, s));
     Dev D = make_dev(ws, L);
     D.events = events ? 1u : 0u;

@@ -946,12 +946,12 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
     const unsigned long long ent = D.o[q];
     const FieldDesc &F = D.fields[ent >> LOCAL_BITS];
     const float *g = F.g;
-    const uint2 st = D.ev_start[q];
+    const uint32_t *lm = D.ev_list + D.ev_start[q];
     const uint32_t nm = c & 255u, nx = c >> 8;
     uint32_t target[2];
     int ntar = 0;
     if (nm) {
-        const uint32_t *l = D.ev_list[0] + st.x;
+        const uint32_t *l = lm;
         const uint32_t sel = l[0];
         uint32_t best = sel;
         float bg = g[sel];
@@ -966,7 +966,7 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
         if (best != sel) target[ntar++] = best;
     }
     if (nx) {
-        const uint32_t *l = D.ev_list[1] + st.y;
+        const uint32_t *l = lm + nm;
         const uint32_t sel = l[0];
         uint32_t best = sel;
         float bg = g[sel];
@@ -998,9 +998,9 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
 // PINNED: the pinned-pair lists of fields fids[0..nf), pinned targets only.
 // Under the original event constraints the listed points are the saddles
 // (the pairs are rule C2) and each mode also evaluates rule C3 at saddles:
-// ALL and PINNED at every listed saddle, LIST at those whose event bit (the
-// bits after the pair bits, set by the apply kernel when a linked extremum
-// changed) is set.
+// ALL at every listed saddle, LIST at those whose event bit (set by the apply
+// kernel when a linked extremum changed) is set, PINNED at those whose pinned
+// event bit (set when a linked extremum was pinned) is set.
 template <int PM>
 __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsigned long long *countp,
                                                const uint32_t *fids, uint32_t nf)
@@ -1027,17 +1027,20 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
         return true;
     };
     const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
-    if (PM == PM_LIST) {
+    const unsigned long long pw = (D.cp_cap + 31) / 32;  // pair-bit words; event bits, pinned event bits follow
+    if (PM == PM_LIST || (PM == PM_PINNED && D.events)) {
         // each warp takes 32 consecutive words of pairbits at a time (one per
-        // lane), clears them, numbers their set bits and checks them 32 at once
-        const unsigned long long pw = (D.cp_cap + 31) / 32;  // pair-bit words; the event bits follow
-        const unsigned long long nwords = D.events ? 2 * pw : pw;
+        // lane), clears them, numbers their set bits and checks them 32 at once.
+        // LIST: the pair and event bits; PINNED: the event bits of saddles
+        // linked to pinned extrema.
+        const unsigned long long w0 = PM == PM_LIST ? 0ull : 2 * pw;
+        const unsigned long long w1 = PM == PM_LIST ? (D.events ? 2 * pw : pw) : 3 * pw;
         const unsigned long long gw = ((unsigned long long)blockIdx.x * CTA + threadIdx.x) >> 5;
         const unsigned long long nw = stride >> 5;
         uint32_t npairs = 0;
-        for (unsigned long long c = gw; c * 32 < nwords; c += nw) {
-            const unsigned long long w = c * 32 + lane;
-            const uint32_t word = w < nwords ? D.pairbits[w] : 0u;
+        for (unsigned long long c = gw; w0 + c * 32 < w1; c += nw) {
+            const unsigned long long w = w0 + c * 32 + lane;
+            const uint32_t word = w < w1 ? D.pairbits[w] : 0u;
             if (!__any_sync(0xffffffffu, word != 0)) continue;
             if (word) D.pairbits[w] = 0;  // taken
             const uint32_t cnt = __popc(word);
@@ -1062,20 +1065,23 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
                 const uint32_t rpre = __shfl_sync(0xffffffffu, excl, src);
                 uint32_t tile = 0;
                 if (k < total) {
-                    const unsigned long long q = (c * 32 + src) * 32 + nth_set_bit(rword, (int)(k - rpre));
-                    if (q < pw * 32) {
-                        if (check(q, tile) && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
+                    const unsigned long long b = (w0 + c * 32 + src) * 32 + nth_set_bit(rword, (int)(k - rpre));
+                    if (b < pw * 32) {
+                        if (check(b, tile) && !D.apply_flag[tile]) D.apply_flag[tile] = 1;
                     } else {
                         uint32_t tl[2];
-                        const int nt = check_events<false>(D, q - pw * 32, tl);
+                        const unsigned long long q = b % (pw * 32);
+                        const int nt = PM == PM_PINNED ? check_events<true>(D, q, tl) : check_events<false>(D, q, tl);
                         for (int u = 0; u < nt; u++)
                             if (!D.apply_flag[tl[u]]) D.apply_flag[tl[u]] = 1;
                     }
                 }
             }
         }
-        if (lane == 0 && npairs) atomicAdd(&D.ls->sum_pairs, (unsigned long long)npairs);
-        return;
+        if (PM == PM_LIST) {
+            if (lane == 0 && npairs) atomicAdd(&D.ls->sum_pairs, (unsigned long long)npairs);
+            return;
+        }
     }
     const uint32_t nouter = PM == PM_PINNED ? nf : 1u;
     for (uint32_t fi = 0; fi < nouter; fi++) {
@@ -1094,12 +1100,11 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
                 D.apply_flag[tile] = 1;
         }
     }
-    if (D.events) {  // rule C3 at every listed saddle
-        const unsigned long long first = PM == PM_ALL ? cp0 : 0ull;
-        const unsigned long long count = PM == PM_ALL ? *countp : D.ls->total_cp;
+    if (PM == PM_ALL && D.events) {  // rule C3 at every listed saddle
+        const unsigned long long count = *countp;
         for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
             uint32_t tl[2];
-            const int nt = check_events<PM == PM_PINNED>(D, first + j, tl);
+            const int nt = check_events<false>(D, cp0 + j, tl);
             for (int u = 0; u < nt; u++)
                 if (!D.apply_flag[tl[u]]) D.apply_flag[tl[u]] = 1;
         }
@@ -1276,14 +1281,16 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                         D.desc[vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
                         pinned = kk == N + 1;
                         atomicOr(&s_cw[row], 1u << lx);
-                        if (AM == AM_FRONTIER && D.events && !(d & D_CP) && rk != 0 &&
+                        if (D.events && (AM == AM_FRONTIER || pinned) && !(d & D_CP) && rk != 0 &&
                             ((d & 15u) == 7u || ((d >> 4) & 15u) == 7u)) {
-                            // an extremum linked to saddles: their rule C3 is checked next pass
+                            // an extremum linked to saddles: their rule C3 is checked
+                            // next pass, and by the residual check if it is pinned
                             const unsigned long long pw = (D.cp_cap + 31) / 32;
                             const uint32_t deg = D.ev_radj[rk];
                             for (uint32_t j = 0; j < deg; j++) {
                                 const uint32_t qq = D.ev_radj[rk + 1 + j];
-                                atomicOr(&D.pairbits[pw + (qq >> 5)], 1u << (qq & 31));
+                                if (AM == AM_FRONTIER) atomicOr(&D.pairbits[pw + (qq >> 5)], 1u << (qq & 31));
+                                if (pinned) atomicOr(&D.pairbits[2 * pw + (qq >> 5)], 1u << (qq & 31));
                             }
                         }
                         if (d & D_CP) {  // value in sorted order; pairs inside the field
@@ -1386,19 +1393,23 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
 // ------------------------------------------------------------ event lists (set-up, Sec. 4.2)
 // The extremum graph of f (Sec. 3.2 Step 1): a join saddle s is linked to the
 // minimum where the steepest-descent path from any neighbour below s ends (split
-// saddles: steepest ascent from the neighbours above, to maxima).  Path ends
-// of all vertices come from pointer jumping on the steepest-neighbour links
-// (E[v] <- E[E[v]] until nothing moves; in place, since every value E[v] ever
-// holds lies on v's path), as arena indices.
+// saddles: steepest ascent from the neighbours above, to maxima).  Path ends of
+// all vertices come from pointer jumping on the steepest-neighbour links,
+// E[v] <- E[E[v]] until nothing moves, both directions at once (E holds the
+// descent links, E + total_v the ascent links, as arena indices).  It runs in
+// place, since every value E[v] ever holds lies on v's path; bit 31 marks an
+// entry that holds its path's end, which later rounds skip.
+constexpr uint32_t EV_DONE = 0x80000000u;
 
-// body(F, t, x, y, z, in) for the vertices of the tiles taken by this block
-// (every lane of every warp calls it the same number of times; `in` is false
-// outside the field).
+// body(fid, F, t, x, y, z, in) for the vertices of the tiles taken by this
+// block, one row of TX vertices per warp at a time (every thread calls it the
+// same number of times; `in` is false outside the field).
 template <class Body>
 __device__ __forceinline__ void for_tile_vertices(const Dev &D, Body body)
 {
     for (uint32_t tile = blockIdx.x; tile < D.total_tiles; tile += gridDim.x) {
-        const FieldDesc &F = D.fields[field_of_tile(D, tile)];
+        const uint32_t fid = field_of_tile(D, tile);
+        const FieldDesc &F = D.fields[fid];
         const uint32_t lt = tile - (uint32_t)F.tbase;
         const uint32_t rest = fdiv(lt, F.div_tnx), tx = lt - rest * F.tnx;
         const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * F.tny;
@@ -1406,7 +1417,7 @@ __device__ __forceinline__ void for_tile_vertices(const Dev &D, Body body)
             const uint32_t x = tx * TX + (uint32_t)(j % TX), y = ty * TY + (uint32_t)((j / TX) % TY);
             const uint32_t z = tz * TZ + (uint32_t)(j / (TX * TY));
             const bool in = x < F.nx && y < F.ny && z < F.nz;
-            body(F, in ? (uint32_t)(((uint64_t)z * F.ny + y) * F.nx + x) : 0u, x, y, z, in);
+            body(fid, F, in ? (uint32_t)(((uint64_t)z * F.ny + y) * F.nx + x) : 0u, x, y, z, in);
         }
     }
 }
@@ -1417,147 +1428,275 @@ __device__ __forceinline__ int64_t rank_offset(const FieldDesc &F, int r)
     return (int64_t)rdx(r) + (int64_t)F.nx * ((int64_t)rdy(r) + (int64_t)F.ny * rdz(r));
 }
 
-// E[v] = steepest-descent (up = 0) or -ascent (up = 1) neighbour of v in f.
-__global__ void __launch_bounds__(CTA) k_ev_init(Dev D, uint32_t *E, int up)
+// c slots from *counter for every thread of the block (all threads call it).
+__device__ __forceinline__ unsigned long long block_reserve(uint32_t c, unsigned long long *counter, uint32_t *sw,
+                                                            unsigned long long *sbase)
 {
-    for_tile_vertices(D, [&](const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
+    uint32_t ex;
+    const uint32_t total = block_excl_scan_n<CTA>(c, ex, sw);
+    if (threadIdx.x == 0) *sbase = total ? atomicAdd(counter, (unsigned long long)total) : 0ull;
+    __syncthreads();
+    const unsigned long long b = *sbase;
+    __syncthreads();
+    return b + ex;
+}
+
+// E[v] = steepest-descent neighbour of v in f, E[total_v + v] = steepest
+// ascent; an extremum links to itself, settled.
+__global__ void __launch_bounds__(CTA) k_ev_init(Dev D, uint32_t *E)
+{
+    for_tile_vertices(D, [&](uint32_t, const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
         if (!in) return;
-        const uint32_t d = D.desc[F.vbase + t];
-        const int r = up ? (int)(d & 15u) : (int)((d >> D_DN_SHIFT) & 15u);
-        E[F.vbase + t] = (uint32_t)((int64_t)(F.vbase + t) + rank_offset(F, r));
+        const uint64_t a = F.vbase + t;
+        const uint32_t d = D.desc[a];
+        const int rd = (int)((d >> D_DN_SHIFT) & 15u), ru = (int)(d & 15u);
+        E[a] = rd == 7 ? ((uint32_t)a | EV_DONE) : (uint32_t)((int64_t)a + rank_offset(F, rd));
+        E[D.total_v + a] = ru == 7 ? ((uint32_t)a | EV_DONE) : (uint32_t)((int64_t)a + rank_offset(F, ru));
     });
 }
 
-// One jump round; sets ls->ev_changed if some path end moved.
-__global__ void __launch_bounds__(CTA) k_ev_jump(Dev D, uint32_t *E)
+// One jump round in both directions; sets ls->ev_changed if an entry changed.
+// Tiles whose entries have all settled are marked in tdone and skipped.
+__global__ void __launch_bounds__(CTA) k_ev_jump(Dev D, uint32_t *E, uint8_t *tdone)
 {
     bool moved = false;
-    for_tile_vertices(D, [&](const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
-        if (!in) return;
-        const uint64_t a = F.vbase + t;
-        const uint32_t e = E[a];
-        const uint32_t e2 = E[e];
-        if (e2 != e) {
-            E[a] = e2;
-            moved = true;
+    for (uint32_t tile = blockIdx.x; tile < D.total_tiles; tile += gridDim.x) {
+        if (tdone[tile]) continue;  // block-uniform
+        const FieldDesc &F = D.fields[field_of_tile(D, tile)];
+        const uint32_t lt = tile - (uint32_t)F.tbase;
+        const uint32_t rest = fdiv(lt, F.div_tnx), tx = lt - rest * F.tnx;
+        const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * F.tny;
+        bool settled = true;
+        for (int j = threadIdx.x; j < TILE_V; j += CTA) {
+            const uint32_t x = tx * TX + (uint32_t)(j % TX), y = ty * TY + (uint32_t)((j / TX) % TY);
+            const uint32_t z = tz * TZ + (uint32_t)(j / (TX * TY));
+            if (x >= F.nx || y >= F.ny || z >= F.nz) continue;
+            const uint64_t a = F.vbase + ((uint64_t)z * F.ny + y) * F.nx + x;
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                uint32_t *Es = E + (side ? D.total_v : 0ull);
+                const uint32_t e = Es[a];
+                if (e & EV_DONE) continue;
+                const uint32_t e2 = Es[e];  // settled: the end of e's path, which is a's
+                if (e2 != e) {
+                    Es[a] = e2;
+                    moved = true;
+                }
+                settled &= (e2 & EV_DONE) != 0;
+            }
         }
-    });
+        if (__syncthreads_and(settled) && threadIdx.x == 0) tdone[tile] = 1;
+    }
     if (__syncthreads_or(moved) && threadIdx.x == 0) D.ls->ev_changed = 1;
 }
 
-// The extrema linked to listed saddle q on side `up` (0: minima through the
-// neighbours below, 1: maxima through those above), distinct, the
-// f-selection first (largest minimum, smallest maximum, ties by index);
-// returns their number, or 0 when fewer than two.
-__device__ __forceinline__ uint32_t linked_extrema(const Dev &D, const uint32_t *E, unsigned long long q, int up,
-                                                   uint32_t *ext)
+// Neighbour slots whose offset has the given component (0: x, 1: y, 2: z) equal to v.
+__host__ __device__ constexpr uint32_t slots_with(int comp, int v)
 {
-    const unsigned long long ent = D.o[q];
-    const FieldDesc &F = D.fields[ent >> LOCAL_BITS];
-    const uint32_t t = (uint32_t)(ent & LOCAL_MASK);
-    const uint32_t row = fdiv(t, F.div_nx), x = t - row * F.nx;
-    const uint32_t z = fdiv(row, F.div_ny), y = row - z * F.ny;
-    uint32_t valid = 0;
-#pragma unroll
+    uint32_t m = 0;
     for (int sl = 0; sl < 14; sl++) {
         const int r = rank_of(sl);
-        const int64_t X = (int64_t)x + rdx(r), Y = (int64_t)y + rdy(r), Z = (int64_t)z + rdz(r);
-        if (X >= 0 && Y >= 0 && Z >= 0 && X < F.nx && Y < F.ny && Z < F.nz) valid |= 1u << sl;
+        const int c = comp == 0 ? rdx(r) : (comp == 1 ? rdy(r) : rdz(r));
+        if (c == v) m |= 1u << sl;
     }
-    const uint32_t L = (D.desc[F.vbase + t] >> D_MASK_SHIFT) & 0x3FFFu;
-    const uint32_t side = up ? (valid & ~L) : L;
-    if (!multi_bit(D.multi, side)) return 0;
-    uint32_t c = 0, bi = 0;
+    return m;
+}
+
+// Neighbour slots of (x, y, z) inside the field.
+__device__ __forceinline__ uint32_t valid_slots(const FieldDesc &F, uint32_t x, uint32_t y, uint32_t z)
+{
+    uint32_t m = 0x3FFFu;
+    if (x == 0) m &= ~slots_with(0, -1);
+    if (x + 1 == F.nx) m &= ~slots_with(0, 1);
+    if (y == 0) m &= ~slots_with(1, -1);
+    if (y + 1 == F.ny) m &= ~slots_with(1, 1);
+    if (z == 0) m &= ~slots_with(2, -1);
+    if (z + 1 == F.nz) m &= ~slots_with(2, 1);
+    return m;
+}
+
+// Slots whose paths the event lists follow: the lower link of a join saddle
+// (descent to minima) and the upper link of a split saddle (ascent to maxima).
+__device__ __forceinline__ void event_sides(const Dev &D, uint32_t d, uint32_t valid, uint32_t &Ls, uint32_t &Us)
+{
+    const uint32_t L = (d >> D_MASK_SHIFT) & 0x3FFFu, U = valid & ~L;
+    Ls = multi_bit(D.multi, L) ? L : 0u;
+    Us = multi_bit(D.multi, U) ? U : 0u;
+}
+
+// Distinct path ends through the slots in `side` (E: the links of that
+// direction), appended to ext[n0 ...]; the f-selection (largest minimum with
+// up = 0, smallest maximum with up = 1, ties by index) is moved to ext[n0].
+// Returns their number, 0 when fewer than two.
+__device__ __forceinline__ uint32_t path_ends(const FieldDesc &F, const uint32_t *E, uint64_t a, uint32_t side,
+                                              const long long *off, int up, uint32_t *ext, uint32_t n0)
+{
+    uint32_t c = 0, bi = 0, b = 0;
     float bf = 0.0f;
     for (uint32_t m = side; m; m &= m - 1) {
-        const int r = rank_of(__ffs(m) - 1);
-        const uint32_t e = E[F.vbase + (uint64_t)((int64_t)t + rank_offset(F, r))] - (uint32_t)F.vbase;
+        const uint32_t e = (E[a + off[__ffs(m) - 1]] & ~EV_DONE) - (uint32_t)F.vbase;
         bool dup = false;
-        for (uint32_t i = 0; i < c; i++) dup |= ext[i] == e;
+        for (uint32_t i = 0; i < c; i++) dup |= ext[n0 + i] == e;
         if (dup) continue;
         const float fe = F.f[e];
-        if (c == 0) {
+        const bool better = c == 0 || (up ? (fe < bf || (fe == bf && e < b)) : (bf < fe || (bf == fe && b < e)));
+        if (better) {
+            bi = c;
             bf = fe;
-        } else {
-            const uint32_t b = ext[bi];
-            const bool better = up ? (fe < bf || (fe == bf && e < b)) : (bf < fe || (bf == fe && b < e));
-            if (better) {
-                bi = c;
-                bf = fe;
-            }
+            b = e;
         }
-        ext[c++] = e;
+        ext[n0 + c++] = e;
     }
     if (c < 2) return 0;
-    const uint32_t s0 = ext[0];
-    ext[0] = ext[bi];
-    ext[bi] = s0;
+    ext[n0 + bi] = ext[n0];
+    ext[n0] = b;
     return c;
 }
 
-// WRITE = 0: add the list lengths of side `up` to ls->ev_cursor[up].
-// WRITE = 1: place the lists in `list` (space reserved from ev_cursor[up]),
-// record their starts and lengths.
-template <int WRITE>
-__global__ void __launch_bounds__(CTA) k_ev_lists(Dev D, const uint32_t *E, int up, uint32_t *list, uint2 *start,
-                                                  uint16_t *cnt)
+// The listed saddles in grid order: a warp takes 32 consecutive words of the
+// listed-point bitmap (chunk ch; a chunk never straddles two fields), numbers
+// their set bits and hands them to its lanes 32 at a time; body(F, fid, x, y,
+// z, t, have) runs for each (every lane calls it the same number of times;
+// `have` is false for an idle lane).  The field's neighbour offsets are in
+// off (per warp, shared memory).
+template <class Body>
+__device__ __forceinline__ void for_listed_saddles(const Dev &D, long long *off, Body body)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned long long total = D.ls->total_cp;
+    const unsigned long long nchunks = (D.total_w + 31) / 32;
     const unsigned long long w0 = ((unsigned long long)blockIdx.x * CTA + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * CTA) >> 5;
-    unsigned long long sum = 0;
-    for (unsigned long long base = w0 * 32; base < total; base += nw * 32) {
-        const unsigned long long q = base + lane;
-        uint32_t ext[14];
-        const uint32_t c = q < total ? linked_extrema(D, E, q, up, ext) : 0u;
-        if (!WRITE) {
-            sum += c;
+    for (unsigned long long ch = w0; ch < nchunks; ch += nw) {
+        const uint64_t w = ch * 32 + lane;
+        const uint32_t word = w < D.total_w ? D.cpwords[w] : 0u;
+        if (!__any_sync(0xffffffffu, word != 0)) {
+            body(ch, (const FieldDesc *)nullptr, 0u, 0u, 0u, 0u, 0u, 0u, false);
             continue;
         }
-        const unsigned long long pos = warp_reserve(c, &D.ls->ev_cursor[up]);
-        if (q < total) {
-            for (uint32_t i = 0; i < c; i++) list[pos + i] = ext[i];
-            reinterpret_cast<uint32_t *>(start)[2 * q + up] = c ? (uint32_t)pos : 0u;
-            cnt[q] = (uint16_t)(up ? (cnt[q] | (c << 8)) : c);
+        const uint32_t fid = field_of_word(D, ch * 32, 0, D.nfields);
+        const FieldDesc &F = D.fields[fid];
+        if (lane < 14) off[lane] = rank_offset(F, rank_of(lane));
+        __syncwarp();
+        const uint32_t cw = __popc(word);
+        uint32_t incl = cw;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-    }
-    if (!WRITE) {
-        sum = __reduce_add_sync(0xffffffffu, (uint32_t)sum);
-        if (lane == 0 && sum) atomicAdd(&D.ls->ev_cursor[up], sum);
+        const uint32_t excl = incl - cw;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t k = base + lane;
+            int src = 0;  // the last lane whose first number is <= k
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t pe = __shfl_sync(0xffffffffu, excl, src + step);
+                if (pe <= k) src += step;
+            }
+            const uint32_t rword = __shfl_sync(0xffffffffu, word, src);
+            const uint32_t rpre = __shfl_sync(0xffffffffu, excl, src);
+            const bool have = k < total;
+            uint32_t x = 0, y = 0, z = 0, t = 0;
+            if (have) {
+                const uint32_t wl = (uint32_t)(ch * 32 + src - F.wbase);
+                const uint32_t row = fdiv(wl, F.div_tnx), wx = wl - row * F.tnx;
+                z = fdiv(row, F.div_ny);
+                y = row - z * F.ny;
+                x = wx * TX + (uint32_t)nth_set_bit(rword, (int)(k - rpre));
+                t = (uint32_t)(((uint64_t)z * F.ny + y) * F.nx + x);
+            }
+            body(ch, &F, fid, x, y, z, t, base, have);
+        }
+        __syncwarp();
     }
 }
 
-// Reverse links, step 1: cp_rank[e] (0 for every extremum after the set-up
-// check) counts the saddles linked to extremum e; ev_cursor[2] = 1 (position 0
-// of ev_radj is never used, so cp_rank 0 means "no linked saddle").
-__global__ void __launch_bounds__(CTA) k_ev_degree(Dev D)
+// Exclusive warp prefix of v; *sum = the warp total.
+__device__ __forceinline__ uint32_t warp_excl(uint32_t v, uint32_t *sum)
 {
-    const unsigned long long total = D.ls->total_cp;
-    if (blockIdx.x == 0 && threadIdx.x == 0) D.ls->ev_cursor[2] = 1;
-    for (unsigned long long q = (unsigned long long)blockIdx.x * CTA + threadIdx.x; q < total;
-         q += (unsigned long long)gridDim.x * CTA) {
-        const uint32_t c = D.ev_cnt[q];
-        if (!c) continue;
-        const FieldDesc &F = D.fields[D.o[q] >> LOCAL_BITS];
-        const uint2 st = D.ev_start[q];
-        for (uint32_t i = 0; i < (c & 255u); i++) atomicAdd(&D.cp_rank[F.vbase + D.ev_list[0][st.x + i]], 1u);
-        for (uint32_t i = 0; i < (c >> 8); i++) atomicAdd(&D.cp_rank[F.vbase + D.ev_list[1][st.y + i]], 1u);
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *sum = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// WRITE = 0: per chunk, the room its saddles' lists may need (the number of
+// slots the lists follow), into room[ch].  WRITE = 1: with room_off the
+// exclusive prefix sums of those numbers, each saddle's list goes to its room
+// (ev_start, ev_cnt at its position q in the sorted order), cp_rank[e] (zero
+// for every extremum after the set-up check) counts the saddles linked to
+// extremum e, and ls->ev_cursor[1] the list entries written.
+template <int WRITE>
+__global__ void __launch_bounds__(CTA) k_ev_lists(Dev D, const uint32_t *E, uint32_t *room,
+                                                  const unsigned long long *room_off, uint32_t *list, uint32_t *start,
+                                                  uint16_t *cnt)
+{
+    __shared__ long long s_off[WARPS][14];
+    const int lane = threadIdx.x & 31;
+    long long *off = s_off[threadIdx.x >> 5];
+    uint32_t run = 0, written = 0;
+    unsigned long long cur = ~0ull;
+    for_listed_saddles(D, off, [&](unsigned long long ch, const FieldDesc *F, uint32_t fid, uint32_t x, uint32_t y,
+                                   uint32_t z, uint32_t t, uint32_t base, bool have) {
+        if (ch != cur) {  // a new chunk (warp-uniform)
+            if (!WRITE && cur != ~0ull && lane == 0) room[cur] = run;
+            cur = ch;
+            run = 0;
+        }
+        if (!F) return;
+        uint32_t d = 0, Ls = 0, Us = 0;
+        if (have) {
+            d = D.desc[F->vbase + t];
+            event_sides(D, d, valid_slots(*F, x, y, z), Ls, Us);
+        }
+        const uint32_t need = __popc(Ls) + __popc(Us);
+        uint32_t tot;
+        const uint32_t ex = warp_excl(need, &tot);
+        if (WRITE && have) {
+            const uint64_t a = F->vbase + t;
+            uint32_t ext[14];
+            const uint32_t c0 = Ls ? path_ends(*F, E, a, Ls, off, 0, ext, 0) : 0u;
+            const uint32_t c1 = Us ? path_ends(*F, E + D.total_v, a, Us, off, 1, ext, c0) : 0u;
+            const unsigned long long q = D.fst[fid].cp_base + D.cp_rank[a];
+            const unsigned long long pos = room_off[ch] + run + ex;
+            for (uint32_t i = 0; i < c0 + c1; i++) {
+                list[pos + i] = ext[i];
+                atomicAdd(&D.cp_rank[F->vbase + ext[i]], 1u);
+            }
+            start[q] = (uint32_t)pos;
+            cnt[q] = (uint16_t)(c0 | (c1 << 8));
+            written += c0 + c1;
+        }
+        run += tot;
+    });
+    if (!WRITE && cur != ~0ull && lane == 0) room[cur] = run;
+    if (WRITE) {
+        const uint32_t v = __reduce_add_sync(0xffffffffu, written);
+        if (lane == 0 && v) atomicAdd(&D.ls->ev_cursor[1], (unsigned long long)v);
     }
 }
 
-// Step 2: every linked extremum gets its slot run in ev_radj (count first).
+// Every extremum with linked saddles gets its run in ev_radj: the count
+// first (a fill cursor until k_ev_fill), then the saddles; cp_rank[e] = the
+// run's position, from 1 on (0 stays "no linked saddle").
 __global__ void __launch_bounds__(CTA) k_ev_alloc(Dev D, uint32_t *radj)
 {
-    for_tile_vertices(D, [&](const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
+    __shared__ uint32_t sw[WARPS];
+    __shared__ unsigned long long sbase;
+    for_tile_vertices(D, [&](uint32_t, const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
         uint32_t deg = 0;
-        uint64_t a = 0;
+        const uint64_t a = F.vbase + t;
         if (in) {
-            a = F.vbase + t;
             const uint32_t d = D.desc[a];
             if (!(d & D_CP) && ((d & 15u) == 7u || ((d >> D_DN_SHIFT) & 15u) == 7u)) deg = D.cp_rank[a];
         }
-        const unsigned long long h = warp_reserve(deg ? deg + 1 : 0u, &D.ls->ev_cursor[2]);
+        const unsigned long long h = 1 + block_reserve(deg ? deg + 1 : 0u, &D.ls->ev_cursor[2], sw, &sbase);
         if (deg) {
             radj[h] = 0;
             D.cp_rank[a] = (uint32_t)h;
@@ -1565,26 +1704,26 @@ __global__ void __launch_bounds__(CTA) k_ev_alloc(Dev D, uint32_t *radj)
     });
 }
 
-// Step 3: the saddles of each extremum.
+// The saddles of each extremum, in grid order of the saddles.
 __global__ void __launch_bounds__(CTA) k_ev_fill(Dev D, uint32_t *radj)
 {
-    const unsigned long long total = D.ls->total_cp;
-    for (unsigned long long q = (unsigned long long)blockIdx.x * CTA + threadIdx.x; q < total;
-         q += (unsigned long long)gridDim.x * CTA) {
+    __shared__ long long s_off[WARPS][14];
+    long long *off = s_off[threadIdx.x >> 5];
+    for_listed_saddles(D, off, [&](unsigned long long, const FieldDesc *F, uint32_t fid, uint32_t, uint32_t,
+                                   uint32_t, uint32_t t, uint32_t, bool have) {
+        if (!have) return;
+        const uint64_t a = F->vbase + t;
+        const unsigned long long q = D.fst[fid].cp_base + D.cp_rank[a];
         const uint32_t c = D.ev_cnt[q];
-        if (!c) continue;
-        const FieldDesc &F = D.fields[D.o[q] >> LOCAL_BITS];
-        const uint2 st = D.ev_start[q];
-        for (int up = 0; up < 2; up++) {
-            const uint32_t n = up ? (c >> 8) : (c & 255u);
-            const uint32_t *l = D.ev_list[up] + (up ? st.y : st.x);
-            for (uint32_t i = 0; i < n; i++) {
-                const uint32_t h = D.cp_rank[F.vbase + l[i]];
-                const uint32_t slot = atomicAdd(&radj[h], 1u);
-                radj[h + 1 + slot] = (uint32_t)q;
-            }
+        if (!c) return;
+        const uint32_t *l = D.ev_list + D.ev_start[q];
+        const uint32_t n = (c & 255u) + (c >> 8);
+        for (uint32_t i = 0; i < n; i++) {
+            const uint32_t h = D.cp_rank[F->vbase + l[i]];
+            const uint32_t slot = atomicAdd(&radj[h], 1u);
+            radj[h + 1 + slot] = (uint32_t)q;
         }
-    }
+    });
 }
 
 // ------------------------------------------------------------ bookkeeping
@@ -1850,23 +1989,28 @@ void launch_pairs_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s)
     k_pairs<PM_PINNED><<<sms() * 4, CTA, 0, s>>>(D, 0, nullptr, FS.fids, FS.n);
 }
 
-void launch_ev_init(const Dev &D, uint32_t *E, int up, cudaStream_t s)
+void launch_ev_init(const Dev &D, uint32_t *E, cudaStream_t s)
 {
-    k_ev_init<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, E, up);
+    k_ev_init<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, E);
 }
-void launch_ev_jump(const Dev &D, uint32_t *E, cudaStream_t s)
+void launch_ev_jump(const Dev &D, uint32_t *E, uint8_t *tdone, cudaStream_t s)
 {
-    k_ev_jump<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, E);
+    k_ev_jump<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, E, tdone);
 }
-void launch_ev_lists(const Dev &D, const uint32_t *E, int up, int write, uint32_t *list, uint2 *start,
-                     uint16_t *cnt, cudaStream_t s)
+void launch_ev_lists(const Dev &D, const uint32_t *E, int write, uint32_t *room,
+                     const unsigned long long *room_off, uint32_t *list, uint32_t *start, uint16_t *cnt,
+                     cudaStream_t s)
 {
-    if (write) k_ev_lists<1><<<sms() * 8, CTA, 0, s>>>(D, E, up, list, start, cnt);
-    else k_ev_lists<0><<<sms() * 8, CTA, 0, s>>>(D, E, up, list, start, cnt);
+    if (write) k_ev_lists<1><<<sms() * 8, CTA, 0, s>>>(D, E, room, room_off, list, start, cnt);
+    else k_ev_lists<0><<<sms() * 8, CTA, 0, s>>>(D, E, room, room_off, list, start, cnt);
+}
+void launch_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n, unsigned long long *total,
+                     cudaStream_t s)
+{
+    k_scan_u32<<<1, 1024, 0, s>>>(in, out, n, total);
 }
 void launch_ev_reverse(const Dev &D, uint32_t *radj, cudaStream_t s)
 {
-    k_ev_degree<<<sms() * 8, CTA, 0, s>>>(D);
     k_ev_alloc<<<grid_for(D.total_tiles, 1, 8), CTA, 0, s>>>(D, radj);
     k_ev_fill<<<sms() * 8, CTA, 0, s>>>(D, radj);
 }

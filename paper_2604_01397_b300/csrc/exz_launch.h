@@ -24,10 +24,14 @@ void launch_pairs_list(const Dev &D, cudaStream_t s);
 void launch_pairs_pinned(const Dev &D, const FieldSet &FS, cudaStream_t s);
 void launch_apply(const Dev &D, int frontier, cudaStream_t s);
 // event lists of the original event constraints (set-up)
-void launch_ev_init(const Dev &D, uint32_t *E, int up, cudaStream_t s);
-void launch_ev_jump(const Dev &D, uint32_t *E, cudaStream_t s);
-void launch_ev_lists(const Dev &D, const uint32_t *E, int up, int write, uint32_t *list, uint2 *start,
-                     uint16_t *cnt, cudaStream_t s);
+void launch_ev_init(const Dev &D, uint32_t *E, cudaStream_t s);
+void launch_ev_jump(const Dev &D, uint32_t *E, uint8_t *tdone, cudaStream_t s);
+void launch_ev_lists(const Dev &D, const uint32_t *E, int write, uint32_t *room,
+                     const unsigned long long *room_off, uint32_t *list, uint32_t *start, uint16_t *cnt,
+                     cudaStream_t s);
+// exclusive scan of n uint32 into uint64 offsets (one block), *total = the sum (may be null)
+void launch_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n, unsigned long long *total,
+                     cudaStream_t s);
 void launch_ev_reverse(const Dev &D, uint32_t *radj, cudaStream_t s);
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);
 void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);

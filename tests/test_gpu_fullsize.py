@@ -5,6 +5,9 @@
   the CUDA-graph loop: the whole correction is compared with the oracle bit for
   bit (the oracle's worklist mode, OpenMP on the host cores, finishes it in a
   few minutes).
+* 512^3 Gaussian bumps under the original event constraints (Sec. 4.2), whose
+  oracle has no worklist form: checked by the properties below, with the
+  oracle's event-mode request set on the final g.
 * 1024^3 multi-octave noise at xi = 1e-4 and 1e-2 of the range: too slow for a
   whole oracle run, so the result is checked by properties that hold at any
   size -- every g value is one of the values the edit rule can produce
@@ -108,6 +111,33 @@ def test_octave1024_fixpoint_properties(rel):
     torch.cuda.empty_cache()
     _replayable(hn, fn, gn, xi, 5)
     req, cnt = oracle.requests(fn, gn, c["dims"])
+    assert cnt == r["residual"]
+    if r["status"] == oracle.CONVERGED:
+        assert cnt == 0
+    else:
+        floor = (fn[req] - np.float32(xi)).astype(np.float32)
+        assert cnt > 0 and np.array_equal(gn[req].view(np.uint32), floor.view(np.uint32))
+
+
+def test_bumps512_original_events_fixpoint_properties():
+    import paper_2604_01397_b300 as ez
+
+    if _host_gib() < 24:
+        pytest.skip("needs about 24 GiB of free host memory for the host-side checks")
+    c = CONFIGS[2]
+    dev = torch.device("cuda")
+    f, fh, xi = synth.make_case(c["kind"], c["dims"], c["seed"], c["rel"], c["fhat"], n_bumps=c["n_bumps"],
+                                sigma=c["sigma"], device=dev)
+    r = ez.correct(f, fh, xi, dims=c["dims"], mode="graph", edits=False, events="original")
+    torch.cuda.synchronize()
+    assert r["status"] in (oracle.CONVERGED, oracle.STUCK)
+    fn = f.cpu().numpy().reshape(-1)
+    hn = fh.cpu().numpy().reshape(-1)
+    gn = r["g"].cpu().numpy().reshape(-1)
+    del f, fh, r["g"]
+    torch.cuda.empty_cache()
+    _replayable(hn, fn, gn, xi, 5)
+    req, cnt = oracle.requests(fn, gn, c["dims"], events=True)
     assert cnt == r["residual"]
     if r["status"] == oracle.CONVERGED:
         assert cnt == 0
