@@ -1442,7 +1442,9 @@ __device__ __forceinline__ unsigned long long block_reserve(uint32_t c, unsigned
 }
 
 // E[v] = steepest-descent neighbour of v in f, E[total_v + v] = steepest
-// ascent; an extremum links to itself, settled.
+// ascent; an extremum links to itself, settled.  (Following the links inside
+// each tile in shared memory first saves about one jump round on the bumps
+// workload but costs as much as it saves.)
 __global__ void __launch_bounds__(CTA) k_ev_init(Dev D, uint32_t *E)
 {
     for_tile_vertices(D, [&](uint32_t, const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
