@@ -362,7 +362,9 @@ def run_ours(a):
             "measured": f"{a.steps} frontier-mode corrections, CUDA events around each launch",
             "loop_kernel_ms_per_correction": {k: v / a.steps for k, v in ker_ms.items()}}
 
-    extras = {"sum_requests": st["sum_requests"], "sum_tiles": st["sum_tiles"], "sum_pairs": st["sum_pairs"],
+    storage = edit_storage(ez, r, n, 5) if not a.no_extras else None
+    extras = {"edit_storage": storage,
+              "sum_requests": st["sum_requests"], "sum_tiles": st["sum_tiles"], "sum_pairs": st["sum_pairs"],
               "iterations": r["iterations"], "status": r["status_name"], "n_edits": r["n_edits"],
               "n_lossless": r["n_lossless"], "n_critical": r["n_critical"], "passes": st["passes"],
               "stage_ms": stages, "mvertices_per_s": n / (ms / 1e3) / 1e6,
@@ -440,6 +442,97 @@ def run_ours(a):
     ws.close()
     if dist:
         dist.destroy_process_group()
+
+
+def edit_storage(ez, r, n: int, N: int) -> dict:
+    """Bytes of the stored form of result r (edit-count bytes plus lossless
+    values, exactz_encode_edits), raw and after ZSTD (level 3) on the host."""
+    st = ez.encode_edits(r["edits"], n, N)
+    kc = st["kcodes"].cpu().numpy()
+    lv = st["lossless"].cpu().numpy()
+    out = {"raw_bytes": int(kc.nbytes + lv.nbytes), "n_lossless": int(lv.size), "edit_ratio": r["n_edits"] / n}
+    z = zstd_size(kc.tobytes()) if kc.size else 0
+    zl = zstd_size(lv.tobytes()) if lv.size else 0
+    if z is None or zl is None:
+        out["zstd_bytes"] = None
+    else:
+        out.update({"zstd_bytes": z + zl, "zstd_bits_per_vertex": 8.0 * (z + zl) / n})
+    return out
+
+
+def zstd_size(data: bytes, level: int = 3):
+    """Size of data after ZSTD (the system libzstd through ctypes, else pyarrow's codec), or None."""
+    import ctypes
+    import ctypes.util
+
+    for name in ("libzstd.so.1", ctypes.util.find_library("zstd")):
+        if not name:
+            continue
+        try:
+            L = ctypes.CDLL(name)
+        except OSError:
+            continue
+        L.ZSTD_compressBound.argtypes = [ctypes.c_size_t]
+        L.ZSTD_compressBound.restype = ctypes.c_size_t
+        L.ZSTD_compress.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int]
+        L.ZSTD_compress.restype = ctypes.c_size_t
+        L.ZSTD_isError.argtypes = [ctypes.c_size_t]
+        L.ZSTD_isError.restype = ctypes.c_uint
+        cap = L.ZSTD_compressBound(len(data))
+        buf = ctypes.create_string_buffer(cap)
+        r = L.ZSTD_compress(buf, cap, data, len(data), level)
+        return None if L.ZSTD_isError(r) else int(r)
+    try:
+        import pyarrow as pa
+
+        return len(pa.Codec("zstd", compression_level=level).compress(data))
+    except Exception:
+        return None
+
+
+def run_nsweep(a):
+    """Appendix C: correction time, passes, edits and stored-edit bytes against N."""
+    import torch
+
+    import paper_2604_01397_b300 as ez
+
+    dev = torch.device("cuda")
+    c = workload_spec("bumps512" if a.workload == "nsweep" else a.workload.split(":")[1], a.size, a.rel)
+    f, fh, xi = make_fields(c, dev)
+    n = f.numel()
+    ws = ez.Workspace([c["dims"]])
+    g = torch.empty_like(f)
+    cap = n if n <= (1 << 26) else n // 4
+    ebuf = torch.empty((cap, 16), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N in (1, 2, 3, 5, 8, 10):
+        def step():
+            return ws.correct([f], [fh], [xi], N_steps=N, g_out=[g], edit_bufs=[ebuf], events=a.events)[0]
+        for _ in range(max(1, a.warmup)):
+            step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        e0.record(stream)
+        for _ in range(a.steps):
+            r = step()
+            launches += ws.stats()["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        row = {"N": N, "ms": ms, "gbs": 4.0 * n / (ms / 1e3) / 1e9, "launches": launches, "iterations": r["iterations"],
+               "status": r["status_name"], "n_edits": r["n_edits"], "n_lossless": r["n_lossless"]}
+        row.update(edit_storage(ez, r, n, N))
+        rows.append(row)
+    at5 = next(x for x in rows if x["N"] == 5)
+    line = {"metric": METRIC, "value": at5["gbs"], "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": max(1, a.warmup), "ms_per_step": at5["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"N sweep on {describe(c)}", "mode": "graph", "events": a.events,
+                       "l2": "inputs larger than L2 (4n bytes per field)"},
+            "sweep": rows, "gpu_launches": at5["launches"]}
+    print(json.dumps(line), flush=True)
+    ws.close()
 
 
 # ---------------------------------------------------------------- many fields
@@ -711,6 +804,8 @@ def main():
         run_batched(a)
     elif a.workload == "serving":
         run_serving(a)
+    elif a.workload == "nsweep" or a.workload.startswith("nsweep:"):
+        run_nsweep(a)
     else:
         run_ours(a)
 

@@ -227,6 +227,30 @@ int exactz_classify(const float *h, exactz_dims d, uint32_t *desc_out, uint8_t *
 int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t *count_out,
                     void *cuda_stream);
 
+/* ---- edit stream: the stored form of a result (Sec. 3.3; storage accounting) ---- */
+
+/* The edits of a result as they are stored next to the base compressor's
+ * output: one edit-count byte per vertex (0..N decrements of Delta, N+1 = the
+ * lossless bound fl(f - xi)) and the lossless values in index order.  From
+ * f_hat, xi and N these reproduce g bit for bit (exactz_decode_edits).
+ *
+ * Encode: edits (DEVICE, n_edits records in strictly ascending idx, as the
+ * correction writes them); kcodes_out (DEVICE, n bytes); lossless_out (DEVICE,
+ * room for lossless_cap floats); *n_lossless_out (HOST) = their number.
+ * Returns EXACTZ_EINVAL for a malformed list (not ascending, idx >= n, k
+ * outside 1..N+1, lossless flag not equal to k == N+1; kcodes_out is then
+ * unspecified) and EXACTZ_ECAP when the lossless values exceed lossless_cap
+ * (none written).  Allocates a few bytes of device scratch per 4096 items. */
+int exactz_encode_edits(const exactz_edit *edits, uint64_t n_edits, uint64_t n, uint32_t N, uint8_t *kcodes_out,
+                        float *lossless_out, uint64_t lossless_cap, uint64_t *n_lossless_out, void *cuda_stream);
+
+/* Decode: g_out (DEVICE, n floats) = f_hat (DEVICE) after k_i steps of
+ * fl(g - Delta), Delta = fl(xi / N), or, where k_i = N+1, the next lossless
+ * value (DEVICE, in index order).  Returns EXACTZ_EINVAL for a code above
+ * N+1, for xi <= 0 or N outside 1..254. */
+int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, const uint8_t *kcodes,
+                        const float *lossless, float *g_out, void *cuda_stream);
+
 /* ---- allocation-free variant for small fields (the paper has no counterpart) ---- */
 
 /* Largest field (in vertices) and the fixed device scratch behind

@@ -17,6 +17,10 @@ Parity status per function (each pin lives under ``tests/``):
                 component counts.
   cp_order      pinned: equals numpy lexsort on (value, index).
   requests      pinned through ``correct`` (R empty at a converged fixpoint).
+  edit_stream, decode_stream
+                pinned: decoding a correction's own stream gives its g bit for
+                bit (hand-derived golden runs, random fields, several N);
+                lossless count and passes follow Appendix C's trade-off in N.
   correct(events=True), requests(events=True)
                 pinned: brute-force extremum graphs, merge and split trees and
                 event selections of converged results, fixpoint invariants
@@ -160,6 +164,35 @@ def correct_rc(f, fhat, xi: float, dims=None, N: int = 5) -> int:
     return lib().oracle_correct(_p(f.reshape(-1)), _p(fhat.reshape(-1)), nx, ny, nz,
                                 ctypes.c_float(np.float32(xi)), int(N), 1 << 30, 0,
                                 _p(g), _p(k), _p(info))
+
+
+def edit_stream(res: dict, N: int = 5):
+    """The stored form of a correction result (Sec. 3.3: step edits plus the
+    lossless values): the edit count k of every vertex (uint8; N + 1 marks the
+    lossless bound) and the lossless values fl(f - xi) in index order."""
+    k = np.asarray(res["k"], np.uint8)
+    return k.copy(), np.asarray(res["g"], np.float32)[k == N + 1].copy()
+
+
+def decode_stream(fhat, kcodes, lossless, xi: float, N: int = 5) -> np.ndarray:
+    """g from the stored form (Sec. 3.3): f_hat after k decrements g <- fl(g - Delta)
+    with Delta = fl(xi / N), or the next lossless value where k = N + 1."""
+    fhat = _f32(fhat).reshape(-1)
+    k = np.asarray(kcodes, np.uint8).reshape(-1)
+    if k.size != fhat.size or np.any(k > N + 1):
+        raise ValueError("one edit count per vertex, each at most N + 1")
+    delta = np.float32(np.float32(xi) / np.float32(N))
+    g = fhat.copy()
+    for step in range(N):
+        m = k > step
+        m &= k <= N
+        g[m] = (g[m] - delta).astype(np.float32)
+    lossless = np.asarray(lossless, np.float32).reshape(-1)
+    sel = np.nonzero(k == N + 1)[0]
+    if lossless.size != sel.size:
+        raise ValueError("one lossless value per vertex with k = N + 1")
+    g[sel] = lossless
+    return g
 
 
 def requests(f, g, dims=None, events: bool = False):

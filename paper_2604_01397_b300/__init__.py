@@ -19,7 +19,9 @@ from .api import (  # noqa: F401
     correct_noalloc,
     cp_order,
     decode_edits,
+    decode_edits_stream,
     dims_of,
+    encode_edits,
     make_opts,
     version,
 )

@@ -84,7 +84,7 @@ EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exa
            "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc",
            "exactz_ws_get_tuning", "exactz_ws_set_tuning", "exactz_ws_autotune", "exactz_server_create",
            "exactz_server_submit", "exactz_server_poll", "exactz_server_wait", "exactz_server_stats",
-           "exactz_server_destroy"]
+           "exactz_server_destroy", "exactz_encode_edits", "exactz_decode_edits"]
 
 _lib = None
 
@@ -135,6 +135,11 @@ def lib():
     L.exactz_correct_noalloc.argtypes = [P, P, Dims, ctypes.c_float, ctypes.POINTER(Opts), P, P,
                                          ctypes.c_uint64, ctypes.POINTER(Result), P]
     L.exactz_correct_noalloc.restype = ctypes.c_int
+    L.exactz_encode_edits.argtypes = [P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, P, P, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_uint64), P]
+    L.exactz_encode_edits.restype = ctypes.c_int
+    L.exactz_decode_edits.argtypes = [P, ctypes.c_uint64, ctypes.c_float, ctypes.c_uint32, P, P, P, P]
+    L.exactz_decode_edits.restype = ctypes.c_int
     L.exactz_server_create.argtypes = [ctypes.POINTER(ServerConfig)]
     L.exactz_server_create.restype = P
     L.exactz_server_submit.argtypes = [P, P, P, Dims, ctypes.c_float, P, P, ctypes.c_uint64,

@@ -265,6 +265,57 @@ def correct_batch(fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "grap
     return out
 
 
+def _edit_records(edits) -> torch.Tensor:
+    """A (count, 16) uint8 tensor of exactz_edit records from decode_edits' dict (or the records themselves)."""
+    if isinstance(edits, torch.Tensor):
+        return edits
+    n = edits["idx"].numel()
+    dev = edits["idx"].device
+    out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
+    if n:
+        out[:, 0:8] = edits["idx"].to(torch.int64).contiguous().view(torch.uint8).reshape(n, 8)
+        out[:, 8:12] = edits["value"].to(torch.float32).contiguous().view(torch.uint8).reshape(n, 4)
+        out[:, 12] = edits["k"].to(torch.uint8)
+        out[:, 13] = edits["lossless"].to(torch.uint8)
+    return out
+
+
+def encode_edits(edits, n: int, N_steps: int = 5, stream=None) -> dict:
+    """The stored form of a result's edits (exactz_encode_edits): "kcodes", one
+    edit-count byte per vertex (0..N steps, N+1 = lossless bound), and
+    "lossless", the lossless values in index order.  edits: the "edits" dict of
+    a correction result (or its (count, 16) uint8 records), on the device."""
+    rec = _edit_records(edits)
+    dev = rec.device
+    kcodes = torch.empty(int(n), dtype=torch.uint8, device=dev)
+    ne = rec.shape[0]
+    lossless = torch.empty(max(ne, 1), dtype=torch.float32, device=dev)
+    nl = ctypes.c_uint64()
+    rc = N.lib().exactz_encode_edits(ctypes.c_void_p(rec.data_ptr() if ne else 0), ne, int(n), int(N_steps),
+                                     ctypes.c_void_p(kcodes.data_ptr()), ctypes.c_void_p(lossless.data_ptr()), ne,
+                                     ctypes.byref(nl), ctypes.c_void_p(_stream(stream)))
+    if rc != N.EXACTZ_OK:
+        raise ExactzError(rc, "exactz_encode_edits")
+    return dict(kcodes=kcodes, lossless=lossless[: nl.value])
+
+
+def decode_edits_stream(fhat: torch.Tensor, kcodes: torch.Tensor, lossless: torch.Tensor, xi: float,
+                        N_steps: int = 5, stream=None) -> torch.Tensor:
+    """g from f_hat and the stored edits (exactz_decode_edits)."""
+    _check(fhat, "fhat")
+    g = torch.empty_like(fhat)
+    n = fhat.numel()
+    if kcodes.numel() != n:
+        raise ValueError("kcodes must hold one byte per vertex")
+    rc = N.lib().exactz_decode_edits(ctypes.c_void_p(fhat.data_ptr()), n, ctypes.c_float(float(np.float32(xi))),
+                                     int(N_steps), ctypes.c_void_p(kcodes.data_ptr()),
+                                     ctypes.c_void_p(lossless.data_ptr() if lossless.numel() else 0),
+                                     ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(_stream(stream)))
+    if rc != N.EXACTZ_OK:
+        raise ExactzError(rc, "exactz_decode_edits")
+    return g
+
+
 def classify(h: torch.Tensor, dims=None, stream=None):
     """Per-vertex descriptor (int32 bit fields, see exactz.h) and type of field h."""
     _check(h, "h")

@@ -965,6 +965,94 @@ const char *exactz_version(void)
     return "exactz-b300 0.1 (sm_103a; tile 32x4x4; stencil/sort/apply kernels; graph while-loop)";
 }
 
+// Scratch of the edit-stream calls: block counts, their offsets, the total
+// and a "malformed" flag; freed on every return.
+struct StreamScratch {
+    uint32_t *blk = nullptr;
+    unsigned long long *off = nullptr, *total = nullptr;
+    int *bad = nullptr;
+    ~StreamScratch()
+    {
+        if (blk) cudaFree(blk);
+        if (off) cudaFree(off);
+        if (total) cudaFree(total);
+        if (bad) cudaFree(bad);
+    }
+    int alloc(uint64_t nb, cudaStream_t s)
+    {
+        CK(cudaMalloc(&blk, 4 * (nb ? nb : 1)));
+        CK(cudaMalloc(&off, 8 * (nb ? nb : 1)));
+        CK(cudaMalloc(&total, 8));
+        CK(cudaMalloc(&bad, sizeof(int)));
+        CK(cudaMemsetAsync(total, 0, 8, s));
+        CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        return EXACTZ_OK;
+    }
+    // the total and the flag, after the stream's work so far
+    int read(cudaStream_t s, unsigned long long &t, int &b)
+    {
+        CK(cudaMemcpyAsync(&t, total, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&b, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return EXACTZ_OK;
+    }
+};
+
+int exactz_encode_edits(const exactz_edit *edits, uint64_t n_edits, uint64_t n, uint32_t N, uint8_t *kcodes_out,
+                        float *lossless_out, uint64_t lossless_cap, uint64_t *n_lossless_out, void *cuda_stream)
+{
+    int rc = check_device();
+    if (rc) return rc;
+    if (!kcodes_out || !n_lossless_out || (n_edits && !edits) || (lossless_cap && !lossless_out) || n == 0 ||
+        N < 1 || N > 254)
+        return EXACTZ_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const EditRec *e = reinterpret_cast<const EditRec *>(edits);
+    const uint64_t nb = stream_blocks(n_edits);
+    StreamScratch S;
+    if ((rc = S.alloc(nb, s))) return rc;
+    CK(cudaMemsetAsync(kcodes_out, 0, n, s));
+    launch_stream_kcodes(e, n_edits, n, N, kcodes_out, S.bad, s);
+    launch_stream_count(e, nullptr, n_edits, N, 0, S.blk, S.bad, s);
+    if (nb) launch_scan_u32(S.blk, S.off, nb, S.total, s);
+    CK(cudaGetLastError());
+    unsigned long long total = 0;
+    int bad = 0;
+    if ((rc = S.read(s, total, bad))) return rc;
+    if (bad) return EXACTZ_EINVAL;
+    *n_lossless_out = total;
+    if (total > lossless_cap) return EXACTZ_ECAP;
+    launch_stream_lossless(e, n_edits, S.off, lossless_out, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return EXACTZ_OK;
+}
+
+int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, const uint8_t *kcodes,
+                        const float *lossless, float *g_out, void *cuda_stream)
+{
+    int rc = check_device();
+    if (rc) return rc;
+    if (!fhat || !kcodes || !g_out || n == 0 || N < 1 || N > 254 || !(xi > 0.0f) || !std::isfinite(xi))
+        return EXACTZ_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const uint64_t nb = stream_blocks(n);
+    StreamScratch S;
+    if ((rc = S.alloc(nb, s))) return rc;
+    launch_stream_count(nullptr, kcodes, n, N, 1, S.blk, S.bad, s);
+    launch_scan_u32(S.blk, S.off, nb, S.total, s);
+    CK(cudaGetLastError());
+    unsigned long long total = 0;
+    int bad = 0;
+    if ((rc = S.read(s, total, bad))) return rc;
+    if (bad || (total && !lossless)) return EXACTZ_EINVAL;
+    const float delta = xi / (float)N;  // binary32 division, Sec. 3.3
+    launch_stream_decode(fhat, kcodes, lossless, n, N, delta, S.off, g_out, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return EXACTZ_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free entry point

@@ -1879,6 +1879,95 @@ __global__ void __launch_bounds__(CTA) k_edit_write(Dev D, FieldSet FS)
     }
 }
 
+// ------------------------------------------------------------ edit stream (Sec. 3.3; storage accounting)
+// The stored form of a result: one edit-count byte per vertex (0..N steps of
+// Delta, N+1 = the lossless bound) and the lossless values in index order.
+// Blocks take SB consecutive items, SPT per thread.
+constexpr int SPT = 16;
+constexpr int SB = CTA * SPT;
+
+// kcodes[idx] = k for every edit (kcodes cleared beforehand).  An edit list
+// that is not strictly ascending, names a vertex outside [0, n), or has a k
+// outside 1..N+1 or a lossless flag that disagrees with k = N+1 sets *bad and
+// writes nothing for that record.
+__global__ void __launch_bounds__(CTA) k_stream_kcodes(const EditRec *edits, uint64_t ne, uint64_t n, uint32_t N,
+                                                       uint8_t *kcodes, int *bad)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * CTA + threadIdx.x; i < ne; i += (uint64_t)gridDim.x * CTA) {
+        const EditRec r = edits[i];
+        const bool ok = r.idx < n && r.k >= 1 && r.k <= N + 1 && (r.lossless != 0) == (r.k == N + 1) &&
+                        (i + 1 == ne || edits[i + 1].idx > r.idx);
+        if (ok) kcodes[r.idx] = r.k;
+        else *bad = 1;
+    }
+}
+
+// Lossless items per block: edits with the lossless flag (from_codes = 0), or
+// vertices whose code is N + 1 (from_codes = 1, also flags codes above N + 1).
+__global__ void __launch_bounds__(CTA) k_stream_count(const EditRec *edits, const uint8_t *kcodes, uint64_t n,
+                                                      uint32_t N, int from_codes, uint32_t *blk, int *bad)
+{
+    __shared__ uint32_t sw[WARPS];
+    const uint64_t b = (uint64_t)blockIdx.x * SB + (uint64_t)threadIdx.x * SPT;
+    uint32_t c = 0;
+    bool wrong = false;
+    for (int j = 0; j < SPT; j++) {
+        const uint64_t i = b + j;
+        if (i >= n) break;
+        if (from_codes) {
+            const uint32_t k = kcodes[i];
+            c += k == N + 1;
+            wrong |= k > N + 1;
+        } else {
+            c += edits[i].lossless != 0;
+        }
+    }
+    if (wrong) *bad = 1;
+    uint32_t ex;
+    const uint32_t tot = block_excl_scan_n<CTA>(c, ex, sw);
+    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+// Encode: the lossless values of the edit list, in its (index) order.
+__global__ void __launch_bounds__(CTA) k_stream_lossless(const EditRec *edits, uint64_t ne,
+                                                         const unsigned long long *blk_off, float *lossless)
+{
+    __shared__ uint32_t sw[WARPS];
+    const uint64_t b = (uint64_t)blockIdx.x * SB + (uint64_t)threadIdx.x * SPT;
+    uint32_t c = 0;
+    for (int j = 0; j < SPT && b + j < ne; j++) c += edits[b + j].lossless != 0;
+    uint32_t ex;
+    block_excl_scan_n<CTA>(c, ex, sw);
+    unsigned long long pos = blk_off[blockIdx.x] + ex;
+    for (int j = 0; j < SPT && b + j < ne; j++)
+        if (edits[b + j].lossless) lossless[pos++] = edits[b + j].value;
+}
+
+// Decode: g_i = f_hat_i after k_i steps of fl(g - Delta), or the next lossless value.
+__global__ void __launch_bounds__(CTA) k_stream_decode(const float *fhat, const uint8_t *kcodes, const float *lossless,
+                                                       uint64_t n, uint32_t N, float delta,
+                                                       const unsigned long long *blk_off, float *g)
+{
+    __shared__ uint32_t sw[WARPS];
+    const uint64_t b = (uint64_t)blockIdx.x * SB + (uint64_t)threadIdx.x * SPT;
+    uint32_t c = 0;
+    for (int j = 0; j < SPT && b + j < n; j++) c += kcodes[b + j] == N + 1;
+    uint32_t ex;
+    block_excl_scan_n<CTA>(c, ex, sw);
+    unsigned long long pos = blk_off[blockIdx.x] + ex;
+    for (int j = 0; j < SPT && b + j < n; j++) {
+        const uint64_t i = b + j;
+        const uint32_t k = kcodes[i];
+        float v = fhat[i];
+        if (k == N + 1) {
+            v = lossless[pos++];
+        } else if (k <= N) {
+            for (uint32_t s = 0; s < k; s++) v = __fsub_rn(v, delta);
+        }
+        g[i] = v;
+    }
+}
+
 // ------------------------------------------------------------ launch wrappers
 static int sms()
 {
@@ -2043,6 +2132,28 @@ void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t 
         k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, FS.nvblk, nullptr);
         k_edit_write<<<nb, CTA, 0, s>>>(D, FS);
     }
+}
+
+unsigned stream_blocks(uint64_t items) { return (unsigned)((items + SB - 1) / SB); }
+void launch_stream_kcodes(const EditRec *edits, uint64_t ne, uint64_t n, uint32_t N, uint8_t *kcodes, int *bad,
+                          cudaStream_t s)
+{
+    if (ne) k_stream_kcodes<<<grid_for(ne, CTA, 8), CTA, 0, s>>>(edits, ne, n, N, kcodes, bad);
+}
+void launch_stream_count(const EditRec *edits, const uint8_t *kcodes, uint64_t n, uint32_t N, int from_codes,
+                         uint32_t *blk, int *bad, cudaStream_t s)
+{
+    if (n) k_stream_count<<<stream_blocks(n), CTA, 0, s>>>(edits, kcodes, n, N, from_codes, blk, bad);
+}
+void launch_stream_lossless(const EditRec *edits, uint64_t ne, const unsigned long long *blk_off, float *lossless,
+                            cudaStream_t s)
+{
+    if (ne) k_stream_lossless<<<stream_blocks(ne), CTA, 0, s>>>(edits, ne, blk_off, lossless);
+}
+void launch_stream_decode(const float *fhat, const uint8_t *kcodes, const float *lossless, uint64_t n, uint32_t N,
+                          float delta, const unsigned long long *blk_off, float *g, cudaStream_t s)
+{
+    if (n) k_stream_decode<<<stream_blocks(n), CTA, 0, s>>>(fhat, kcodes, lossless, n, N, delta, blk_off, g);
 }
 
 }  // namespace exz

@@ -71,6 +71,13 @@ def test_bumps512_bit_exact_against_oracle():
     assert np.array_equal(e["idx"].cpu().numpy(), ref["edit_idx"])
     assert np.array_equal(e["k"].cpu().numpy(), ref["edit_k"])
     assert np.array_equal(e["value"].cpu().numpy().view(np.uint32), ref["edit_value"].view(np.uint32))
+    # the stored form decodes to the same g
+    st = ez.encode_edits(e, n, 5)
+    k_ref, l_ref = oracle.edit_stream(ref, 5)
+    assert np.array_equal(st["kcodes"].cpu().numpy(), k_ref)
+    assert np.array_equal(st["lossless"].cpu().numpy().view(np.uint32), l_ref.view(np.uint32))
+    g2 = ez.decode_edits_stream(fh.reshape(-1), st["kcodes"], st["lossless"], xi, 5)
+    assert torch.equal(g2.view(torch.int32), g.reshape(-1).view(torch.int32))
     ws.close()
 
 

@@ -1,0 +1,65 @@
+"""Pins of the stored form of a result (Sec. 3.3: step edits plus lossless
+values; Appendix C: the trade-off in N).
+
+* decoding a correction's own stream gives its g bit for bit: on the
+  hand-derived golden runs and on random fields, for several N;
+* the trade-off the paper reports for N holds on fixtures: fewer lossless
+  edits and more passes as N grows;
+* malformed streams are refused.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+
+def _golden(name):
+    c = read_golden(name)
+    dims = tuple(int(x) for x in c["dims"])
+    arr = lambda key: np.array([float(x) for x in c[key]], np.float32)  # noqa: E731
+    return dims, float(c["xi"][0]), int(c["N"][0]), arr("f"), arr("fhat")
+
+
+@pytest.mark.parametrize("name", ["cascade_1d.txt", "lossless_1d.txt", "stuck_1d.txt"])
+def test_golden_round_trip(name):
+    dims, xi, N, f, fh = _golden(name)
+    r = oracle.correct(f, fh, xi, dims=dims, N=N)
+    k, lossless = oracle.edit_stream(r, N)
+    assert np.array_equal(k, r["k"])
+    assert lossless.size == r["n_lossless"]
+    g = oracle.decode_stream(fh, k, lossless, xi, N)
+    assert np.array_equal(g.view(np.uint32), r["g"].view(np.uint32))
+
+
+FIXTURES = [((24, 20, 16), 6, "uniform", 2e-2), ((32, 28, 1), 13, "quantised", 5e-2),
+            ((20, 18, 16), 15, "quantised", 3e-2), ((16, 16, 16), 3, "uniform", 1e-2)]
+
+
+@pytest.mark.parametrize("dims,seed,recipe,rel", FIXTURES)
+def test_round_trip_and_trade_off_in_N(dims, seed, recipe, rel):
+    f, fh, xi = synth.make_case("bumps", dims, seed, rel, recipe, n_bumps=8, sigma=(1.5, 3.0))
+    f, fh = f.numpy().reshape(-1), fh.numpy().reshape(-1)
+    lossless, passes = [], []
+    for N in (1, 2, 3, 5, 8, 12):
+        r = oracle.correct(f, fh, xi, dims=dims, N=N)
+        k, lv = oracle.edit_stream(r, N)
+        g = oracle.decode_stream(fh, k, lv, xi, N)
+        assert np.array_equal(g.view(np.uint32), r["g"].view(np.uint32))
+        # every lossless value is the bound fl(f - xi)
+        assert np.array_equal(lv.view(np.uint32), (f[k == N + 1] - np.float32(xi)).astype(np.float32).view(np.uint32))
+        lossless.append(r["n_lossless"])
+        passes.append(r["iterations"])
+    assert all(a >= b for a, b in zip(lossless, lossless[1:])), lossless
+    assert passes[-1] > passes[0], passes
+
+
+def test_malformed_streams_are_refused():
+    fh = np.zeros(8, np.float32)
+    with pytest.raises(ValueError):
+        oracle.decode_stream(fh, np.zeros(7, np.uint8), np.zeros(0, np.float32), 0.1, 5)
+    with pytest.raises(ValueError):
+        oracle.decode_stream(fh, np.full(8, 7, np.uint8), np.zeros(8, np.float32), 0.1, 5)
+    with pytest.raises(ValueError):
+        oracle.decode_stream(fh, np.full(8, 6, np.uint8), np.zeros(3, np.float32), 0.1, 5)
