@@ -70,6 +70,17 @@ extern "C" {
 #define EXACTZ_MODE_FRONTIER 1  /* re-check only tiles touched by last pass's edits, host-driven loop */
 #define EXACTZ_MODE_GRAPH 2     /* frontier passes in a CUDA graph; device-side while-loop exit */
 
+/* Edit direction (opts.direction).  Every rule names the vertex that must be
+ * lower (decreasing edits, Sec. 3.3: g <- fl(g - Delta) down to fl(f - xi)) or
+ * the one that must be higher (increasing edits: g <- fl(g + Delta) up to
+ * fl(f + xi)); the paper's framework allows either and uses decreasing.  The
+ * increasing correction is computed as the decreasing one of the point
+ * reflection x -> (nx-1-x, ny-1-y, nz-1-z) of -f, -f_hat (which maps the mesh
+ * onto itself and reverses the order with its index tie-break), mapped back;
+ * it needs 8 bytes per vertex of extra workspace. */
+#define EXACTZ_EDITS_DECREASING 0
+#define EXACTZ_EDITS_INCREASING 1
+
 /* Event constraints (opts.events). */
 #define EXACTZ_EVENTS_REFORMULATED 0 /* global order of all critical points (Sec. 4.3) */
 #define EXACTZ_EVENTS_ORIGINAL 1     /* saddle order C2 + extremum-graph merge/split events C3 (Sec. 4.2);
@@ -87,7 +98,7 @@ typedef struct {
     uint32_t want_edit_list; /* 0: skip the edit-list compaction */
     uint32_t profile;        /* 1: time the stages with CUDA events (see exactz_ws_stats) */
     uint32_t events;         /* EXACTZ_EVENTS_* (default REFORMULATED) */
-    uint32_t reserved;       /* must be 0 */
+    uint32_t direction;      /* EXACTZ_EDITS_* (default DECREASING) */
 } exactz_opts;
 
 /* One applied edit.  value = g at idx; k = number of decrements applied (1..N)
@@ -245,11 +256,12 @@ int exactz_encode_edits(const exactz_edit *edits, uint64_t n_edits, uint64_t n, 
                         float *lossless_out, uint64_t lossless_cap, uint64_t *n_lossless_out, void *cuda_stream);
 
 /* Decode: g_out (DEVICE, n floats) = f_hat (DEVICE) after k_i steps of
- * fl(g - Delta), Delta = fl(xi / N), or, where k_i = N+1, the next lossless
- * value (DEVICE, in index order).  Returns EXACTZ_EINVAL for a code above
- * N+1, for xi <= 0 or N outside 1..254. */
-int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, const uint8_t *kcodes,
-                        const float *lossless, float *g_out, void *cuda_stream);
+ * fl(g - Delta) (fl(g + Delta) for direction = EXACTZ_EDITS_INCREASING),
+ * Delta = fl(xi / N), or, where k_i = N+1, the next lossless value (DEVICE, in
+ * index order).  Returns EXACTZ_EINVAL for a code above N+1, for xi <= 0, N
+ * outside 1..254 or an unknown direction. */
+int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, uint32_t direction,
+                        const uint8_t *kcodes, const float *lossless, float *g_out, void *cuda_stream);
 
 /* ---- allocation-free variant for small fields (the paper has no counterpart) ---- */
 
@@ -278,8 +290,8 @@ int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, con
  * A GRAPH mode request runs the same passes as FRONTIER driven from the host
  * (identical results); opts->profile is ignored.  EXACTZ_EVENTS_ORIGINAL
  * needs set-up storage sized by the field's extremum graph and is refused
- * (EXACTZ_EINVAL).  Returns EXACTZ_ESIZE for larger fields, otherwise as
- * exactz_correct. */
+ * (EXACTZ_EINVAL), as are increasing edits.  Returns EXACTZ_ESIZE for larger
+ * fields, otherwise as exactz_correct. */
 int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, float xi,
                            const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
                            uint64_t edits_cap, exactz_result *res, void *cuda_stream);
@@ -304,7 +316,7 @@ typedef struct {
     uint32_t max_fields;   /* resident fields at most (1..4096) */
     uint32_t reserved;
     exactz_opts opts;      /* N, max_iters, want_edit_list for every request (N = 0: defaults); mode ignored;
-                              events must be EXACTZ_EVENTS_REFORMULATED */
+                              events and direction must be 0 */
 } exactz_server_config;
 
 typedef struct {

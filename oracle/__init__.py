@@ -21,6 +21,11 @@ Parity status per function (each pin lives under ``tests/``):
                 pinned: decoding a correction's own stream gives its g bit for
                 bit (hand-derived golden runs, random fields, several N);
                 lossless count and passes follow Appendix C's trade-off in N.
+  correct(increasing=True), requests(increasing=True)
+                pinned: the point-reflection / negation identity against the
+                decreasing mode, fixpoint invariants mirrored, brute-force
+                topology of results, planted mistakes
+                (tests/test_oracle_increasing.py).
   correct(events=True), requests(events=True)
                 pinned: brute-force extremum graphs, merge and split trees and
                 event selections of converged results, fixpoint invariants
@@ -59,6 +64,9 @@ def lib():
         L.oracle_requests.argtypes = [P, P, i64, i64, i64, P, P]
         L.oracle_correct_events.argtypes = [P, P, i64, i64, i64, ctypes.c_float, ctypes.c_int, i64, P, P, P]
         L.oracle_requests_events.argtypes = [P, P, i64, i64, i64, P, P]
+        L.oracle_correct_ex.argtypes = [P, P, i64, i64, i64, ctypes.c_float, ctypes.c_int, i64, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, P, P, P]
+        L.oracle_requests_ex.argtypes = [P, P, i64, i64, i64, ctypes.c_int, ctypes.c_int, P, P]
         _lib = L
     return _lib
 
@@ -123,11 +131,13 @@ def cp_order(f, dims=None) -> np.ndarray:
 
 
 def correct(f, fhat, xi: float, dims=None, N: int = 5, max_iters: int = 1 << 30,
-            worklist: bool = False, events: bool = False) -> dict:
+            worklist: bool = False, events: bool = False, increasing: bool = False) -> dict:
     """Run the correction to its fixpoint.  Returns g, k, iterations, residual,
     status, n_edits, n_lossless and the edit list (ascending index).
     events=True: the saddle-ordering and original event constraints replace the
-    reformulated ones (every rule is evaluated in full each pass)."""
+    reformulated ones (every rule is evaluated in full each pass).
+    increasing=True: monotone increasing edits (every rule raises the vertex
+    that must be higher; g <- fl(g + Delta) up to the lossless bound fl(f + xi))."""
     f = _f32(f)
     fhat = _f32(fhat)
     nx, ny, nz = _dims_of(f, dims)
@@ -135,7 +145,11 @@ def correct(f, fhat, xi: float, dims=None, N: int = 5, max_iters: int = 1 << 30,
     g = np.empty(n, np.float32)
     k = np.empty(n, np.uint8)
     info = np.zeros(5, np.int64)
-    if events:
+    if increasing:
+        rc = lib().oracle_correct_ex(_p(f.reshape(-1)), _p(fhat.reshape(-1)), nx, ny, nz,
+                                     ctypes.c_float(np.float32(xi)), int(N), int(max_iters), int(bool(worklist)),
+                                     int(bool(events)), 1, _p(g), _p(k), _p(info))
+    elif events:
         rc = lib().oracle_correct_events(_p(f.reshape(-1)), _p(fhat.reshape(-1)), nx, ny, nz,
                                          ctypes.c_float(np.float32(xi)), int(N), int(max_iters),
                                          _p(g), _p(k), _p(info))
@@ -174,9 +188,10 @@ def edit_stream(res: dict, N: int = 5):
     return k.copy(), np.asarray(res["g"], np.float32)[k == N + 1].copy()
 
 
-def decode_stream(fhat, kcodes, lossless, xi: float, N: int = 5) -> np.ndarray:
+def decode_stream(fhat, kcodes, lossless, xi: float, N: int = 5, increasing: bool = False) -> np.ndarray:
     """g from the stored form (Sec. 3.3): f_hat after k decrements g <- fl(g - Delta)
-    with Delta = fl(xi / N), or the next lossless value where k = N + 1."""
+    (increments with increasing=True) with Delta = fl(xi / N), or the next
+    lossless value where k = N + 1."""
     fhat = _f32(fhat).reshape(-1)
     k = np.asarray(kcodes, np.uint8).reshape(-1)
     if k.size != fhat.size or np.any(k > N + 1):
@@ -186,7 +201,7 @@ def decode_stream(fhat, kcodes, lossless, xi: float, N: int = 5) -> np.ndarray:
     for step in range(N):
         m = k > step
         m &= k <= N
-        g[m] = (g[m] - delta).astype(np.float32)
+        g[m] = ((g[m] + delta) if increasing else (g[m] - delta)).astype(np.float32)
     lossless = np.asarray(lossless, np.float32).reshape(-1)
     sel = np.nonzero(k == N + 1)[0]
     if lossless.size != sel.size:
@@ -195,15 +210,19 @@ def decode_stream(fhat, kcodes, lossless, xi: float, N: int = 5) -> np.ndarray:
     return g
 
 
-def requests(f, g, dims=None, events: bool = False):
+def requests(f, g, dims=None, events: bool = False, increasing: bool = False):
     """Full request set R (bool per vertex) of the edited field g."""
     f = _f32(f)
     g = _f32(g)
     nx, ny, nz = _dims_of(f, dims)
     req = np.empty(f.size, np.uint8)
     cnt = ctypes.c_int64()
-    fn = lib().oracle_requests_events if events else lib().oracle_requests
-    rc = fn(_p(f.reshape(-1)), _p(g.reshape(-1)), nx, ny, nz, _p(req), ctypes.byref(cnt))
+    if increasing:
+        rc = lib().oracle_requests_ex(_p(f.reshape(-1)), _p(g.reshape(-1)), nx, ny, nz, int(bool(events)), 1,
+                                      _p(req), ctypes.byref(cnt))
+    else:
+        fn = lib().oracle_requests_events if events else lib().oracle_requests
+        rc = fn(_p(f.reshape(-1)), _p(g.reshape(-1)), nx, ny, nz, _p(req), ctypes.byref(cnt))
     if rc != 0:
         raise ValueError(f"oracle_requests failed: {rc}")
     return req.astype(bool), int(cnt.value)

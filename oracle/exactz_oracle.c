@@ -312,6 +312,8 @@ typedef struct {
     int64_t *o;       /* critical points of f, sorted by the f-order */
     int64_t ncp;
     int64_t *rank;    /* position of a critical point in o, -1 otherwise */
+    /* increasing edits (inc = 1): every rule raises the vertex that must be higher */
+    int inc;
     /* original event constraints (events = 1) */
     int events;
     int64_t *so;      /* saddles of f, sorted by the f-order */
@@ -335,8 +337,8 @@ static void check_vertex(const ctx_t *C, const float *g, int64_t p, uint8_t *req
     int64_t upg, dng;
     uint8_t tyg;
     classify_vertex(&C->G, g, p, &upg, &dng, &tyg);
-    if (upg != C->upf[p]) mark(req, upg);
-    if (dng != C->dnf[p]) mark(req, C->dnf[p]);
+    if (upg != C->upf[p]) mark(req, C->inc ? C->upf[p] : upg);
+    if (dng != C->dnf[p]) mark(req, C->inc ? dng : C->dnf[p]);
     int saddle_f = (C->tyf[p] & (T_JOIN | T_SPLIT)) != 0;
     int saddle_g = (tyg & (T_JOIN | T_SPLIT)) != 0;
     if (saddle_f || saddle_g) {
@@ -346,7 +348,7 @@ static void check_vertex(const ctx_t *C, const float *g, int64_t p, uint8_t *req
         for (int j = 0; j < cnt; j++) {
             int below_f = prec(C->f, nb[j], p);
             int below_g = prec(g, nb[j], p);
-            if (below_f != below_g) mark(req, below_f ? nb[j] : p);
+            if (below_f != below_g) mark(req, (below_f != C->inc) ? nb[j] : p);
         }
     }
 }
@@ -355,14 +357,14 @@ static void check_vertex(const ctx_t *C, const float *g, int64_t p, uint8_t *req
 static void check_pair(const ctx_t *C, const float *g, int64_t q, uint8_t *req)
 {
     int64_t a = C->o[q], b = C->o[q + 1];
-    if (prec(g, b, a)) mark(req, a);
+    if (prec(g, b, a)) mark(req, C->inc ? b : a);
 }
 
 /* C2 on the sorted saddle pair (so[q], so[q+1]). */
 static void check_saddle_pair(const ctx_t *C, const float *g, int64_t q, uint8_t *req)
 {
     int64_t a = C->so[q], b = C->so[q + 1];
-    if (prec(g, b, a)) mark(req, a);
+    if (prec(g, b, a)) mark(req, C->inc ? b : a);
 }
 
 /* C3 at the sorted saddle so[q]: the EGP selection among its connected extrema in g. */
@@ -374,13 +376,13 @@ static void check_events(const ctx_t *C, const float *g, int64_t q, uint8_t *req
         int64_t best = e[0];
         for (int j = 1; j < nm; j++)
             if (prec(g, best, e[j])) best = e[j];
-        if (best != C->sel_min[q]) mark(req, best);
+        if (best != C->sel_min[q]) mark(req, C->inc ? C->sel_min[q] : best);
     }
     if (C->sel_max[q] >= 0) {
         int64_t best = e[nm];
         for (int j = 1; j < nx; j++)
             if (prec(g, e[nm + j], best)) best = e[nm + j];
-        if (best != C->sel_max[q]) mark(req, C->sel_max[q]);
+        if (best != C->sel_max[q]) mark(req, C->inc ? best : C->sel_max[q]);
     }
 }
 
@@ -508,7 +510,7 @@ int oracle_requests(const float *f, const float *g, int64_t nx, int64_t ny, int6
                     uint8_t *req_out, int64_t *count_out);
 
 static int correct_impl(const float *f, const float *fhat, int64_t nx, int64_t ny, int64_t nz,
-                        float xi, int N, int64_t max_iters, int worklist, int events,
+                        float xi, int N, int64_t max_iters, int worklist, int events, int inc,
                         float *g, uint8_t *k, int64_t *info)
 {
     /* info: [0] iterations, [1] residual, [2] status, [3] n_edits, [4] n_lossless */
@@ -541,6 +543,7 @@ static int correct_impl(const float *f, const float *fhat, int64_t nx, int64_t n
     for (int64_t p = 0; p < n; p++) C.rank[p] = -1;
     for (int64_t q = 0; q < C.ncp; q++) C.rank[C.o[q]] = q;
     C.events = events;
+    C.inc = inc;
     C.so = NULL; C.ev_ext = NULL; C.ev_nmin = C.ev_nmax = NULL; C.sel_min = C.sel_max = NULL;
     if (events) {
         worklist = 0;  /* the event rules are evaluated in full every pass */
@@ -600,14 +603,15 @@ static int correct_impl(const float *f, const float *fhat, int64_t nx, int64_t n
             status = nstar != 0 ? OR_ITER_LIMIT : (nR == 0 ? OR_CONVERGED : OR_STUCK);
             break;
         }
-        /* ApplyBoundedEdits: each requested, unpinned vertex once. */
+        /* ApplyBoundedEdits: each requested, unpinned vertex once (decrements
+         * of Delta down to fl(f - xi); increasing: increments up to fl(f + xi)). */
         for (int64_t x = 0; x < n; x++) {
             changed[x] = 0;
             if (!req[x] || k[x] > N) continue;
-            float floor_x = f[x] - xi;
+            float floor_x = inc ? f[x] + xi : f[x] - xi;
             if (k[x] < N) {
-                float t = g[x] - delta;
-                if (t < floor_x) {
+                float t = inc ? g[x] + delta : g[x] - delta;
+                if (inc ? (t > floor_x) : (t < floor_x)) {
                     g[x] = floor_x;
                     k[x] = (uint8_t)(N + 1);
                 } else {
@@ -643,7 +647,7 @@ int oracle_correct(const float *f, const float *fhat, int64_t nx, int64_t ny, in
                    float xi, int N, int64_t max_iters, int worklist,
                    float *g, uint8_t *k, int64_t *info)
 {
-    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, worklist, 0, g, k, info);
+    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, worklist, 0, 0, g, k, info);
 }
 
 /* Algorithm 1 with the EG constraints, the saddle-ordering constraints and the
@@ -652,27 +656,44 @@ int oracle_correct_events(const float *f, const float *fhat, int64_t nx, int64_t
                           float xi, int N, int64_t max_iters,
                           float *g, uint8_t *k, int64_t *info)
 {
-    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, 0, 1, g, k, info);
+    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, 0, 1, 0, g, k, info);
 }
 
-static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events,
+/* Either constraint set (events) and either edit direction (increasing = 1:
+ * every rule raises the vertex that must be higher, edits add Delta up to the
+ * lossless bound fl(f + xi)). */
+int oracle_correct_ex(const float *f, const float *fhat, int64_t nx, int64_t ny, int64_t nz,
+                      float xi, int N, int64_t max_iters, int worklist, int events, int increasing,
+                      float *g, uint8_t *k, int64_t *info)
+{
+    return correct_impl(f, fhat, nx, ny, nz, xi, N, max_iters, worklist, events, increasing != 0, g, k, info);
+}
+
+static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events, int inc,
                          uint8_t *req_out, int64_t *count_out);
 
 /* The full request set R for a given edited field g (no pinned filter). */
 int oracle_requests(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz,
                     uint8_t *req_out, int64_t *count_out)
 {
-    return requests_impl(f, g, nx, ny, nz, 0, req_out, count_out);
+    return requests_impl(f, g, nx, ny, nz, 0, 0, req_out, count_out);
 }
 
 /* The same with the original event constraints in place of R3. */
 int oracle_requests_events(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz,
                            uint8_t *req_out, int64_t *count_out)
 {
-    return requests_impl(f, g, nx, ny, nz, 1, req_out, count_out);
+    return requests_impl(f, g, nx, ny, nz, 1, 0, req_out, count_out);
 }
 
-static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events,
+/* Either constraint set and either edit direction. */
+int oracle_requests_ex(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events,
+                       int increasing, uint8_t *req_out, int64_t *count_out)
+{
+    return requests_impl(f, g, nx, ny, nz, events, increasing != 0, req_out, count_out);
+}
+
+static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny, int64_t nz, int events, int inc,
                          uint8_t *req_out, int64_t *count_out)
 {
     if (!dims_ok(nx, ny, nz)) return OR_EINVAL;
@@ -693,6 +714,7 @@ static int requests_impl(const float *f, const float *g, int64_t nx, int64_t ny,
     oracle_classify(f, nx, ny, nz, C.upf, C.dnf, C.tyf);
     C.ncp = cp_order(f, C.tyf, n, C.o);
     C.events = events;
+    C.inc = inc;
     C.so = NULL; C.ev_ext = NULL; C.ev_nmin = C.ev_nmax = NULL; C.sel_min = C.sel_max = NULL;
     if (events && setup_events(&C) != 0) {
         free_events(&C);

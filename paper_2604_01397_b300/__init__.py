@@ -9,6 +9,7 @@ from . import _native
 from .api import (  # noqa: F401
     MODES,
     STATUS,
+    DIRECTIONS,
     EVENTS,
     ExactzError,
     Server,

@@ -33,7 +33,7 @@ class Dims(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_iters", ctypes.c_uint64),
                 ("want_edit_list", ctypes.c_uint32), ("profile", ctypes.c_uint32),
-                ("events", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("events", ctypes.c_uint32), ("direction", ctypes.c_uint32)]
 
 
 class Edit(ctypes.Structure):
@@ -138,7 +138,8 @@ def lib():
     L.exactz_encode_edits.argtypes = [P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, P, P, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_uint64), P]
     L.exactz_encode_edits.restype = ctypes.c_int
-    L.exactz_decode_edits.argtypes = [P, ctypes.c_uint64, ctypes.c_float, ctypes.c_uint32, P, P, P, P]
+    L.exactz_decode_edits.argtypes = [P, ctypes.c_uint64, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, P, P, P,
+                                      P]
     L.exactz_decode_edits.restype = ctypes.c_int
     L.exactz_server_create.argtypes = [ctypes.POINTER(ServerConfig)]
     L.exactz_server_create.restype = P

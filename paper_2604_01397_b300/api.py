@@ -19,6 +19,8 @@ MODES = {"plain": N.MODE_PLAIN, "frontier": N.MODE_FRONTIER, "graph": N.MODE_GRA
 # event constraints: the global order of all critical points (Sec. 4.3), or the
 # saddle order and extremum-graph merge / split events (Sec. 4.2)
 EVENTS = {"reformulated": 0, "original": 1}
+# edit direction: monotone decreasing (the paper's choice) or increasing edits
+DIRECTIONS = {"decreasing": 0, "increasing": 1}
 STATUS = {N.CONVERGED: "CONVERGED", N.STUCK: "STUCK", N.ITER_LIMIT: "ITER_LIMIT"}
 
 
@@ -58,7 +60,8 @@ def _check(t: torch.Tensor, name: str, host: bool = False):
 
 
 def make_opts(N_steps: int = 5, mode: str = "graph", max_iters: int = 1_000_000,
-              want_edit_list: bool = True, profile: bool = False, events: str = "reformulated") -> N.Opts:
+              want_edit_list: bool = True, profile: bool = False, events: str = "reformulated",
+              direction: str = "decreasing") -> N.Opts:
     o = N.Opts()
     N.lib().exactz_default_opts(ctypes.byref(o))
     o.N = int(N_steps)
@@ -67,6 +70,7 @@ def make_opts(N_steps: int = 5, mode: str = "graph", max_iters: int = 1_000_000,
     o.want_edit_list = int(bool(want_edit_list))
     o.profile = int(bool(profile))
     o.events = EVENTS[events] if isinstance(events, str) else int(events)
+    o.direction = DIRECTIONS[direction] if isinstance(direction, str) else int(direction)
     return o
 
 
@@ -129,12 +133,12 @@ class Workspace:
             raise ExactzError(rc, "exactz_ws_set_tuning")
 
     def autotune(self, fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "graph", repeats: int = 2,
-                 stream=None, events: str = "reformulated") -> dict:
+                 stream=None, events: str = "reformulated", direction: str = "decreasing") -> dict:
         """Pick the launch schedule for these fields by timing whole corrections."""
         nf = len(fs)
         dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
         t = N.Tuning()
-        o = make_opts(N_steps, mode, 1_000_000, False, events=events)
+        o = make_opts(N_steps, mode, 1_000_000, False, events=events, direction=direction)
         rc = N.lib().exactz_ws_autotune(
             self._h, nf, N.ptr_array([x.data_ptr() for x in fs]), N.ptr_array([x.data_ptr() for x in fhats]),
             (N.Dims * nf)(*[N.Dims(*d) for d in dl]), (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis]),
@@ -163,7 +167,7 @@ class Workspace:
                 max_iters: int = 1_000_000, edits: bool = True, edits_caps=None,
                 g_out: Optional[List[torch.Tensor]] = None, edit_bufs: Optional[List[torch.Tensor]] = None,
                 stream=None, host_buffers: bool = False, raise_on_error: bool = True,
-                profile: bool = False, events: str = "reformulated") -> List[dict]:
+                profile: bool = False, events: str = "reformulated", direction: str = "decreasing") -> List[dict]:
         nf = len(fs)
         dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
         for i in range(nf):
@@ -181,7 +185,7 @@ class Workspace:
         xarr = (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis])
         carr = (ctypes.c_uint64 * nf)(*caps)
         res = (N.Result * nf)()
-        o = make_opts(N_steps, mode, max_iters, edits, profile, events)
+        o = make_opts(N_steps, mode, max_iters, edits, profile, events, direction)
         rc = N.lib().exactz_ws_correct(
             self._h, nf, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
             darr, xarr, ctypes.byref(o), N.ptr_array([t.data_ptr() for t in g_out]),
@@ -204,10 +208,12 @@ class Workspace:
 
 def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: int = 5,
             mode: str = "graph", max_iters: int = 1_000_000, edits: bool = True, edits_cap=None,
-            stream=None, raise_on_error: bool = True, events: str = "reformulated") -> dict:
+            stream=None, raise_on_error: bool = True, events: str = "reformulated",
+            direction: str = "decreasing") -> dict:
     """Correct one field to its fixpoint (exactz_correct).  events: "reformulated"
     (all critical points keep their order) or "original" (saddle order and
-    extremum-graph merge / split events)."""
+    extremum-graph merge / split events); direction: "decreasing" or
+    "increasing" monotone edits."""
     _check(f, "f")
     _check(fhat, "fhat")
     d = dims_of(f, dims)
@@ -215,7 +221,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: 
     cap = default_edits_cap(f.numel()) if edits_cap is None else int(edits_cap)
     buf = torch.empty((cap if edits else 0, 16), dtype=torch.uint8, device=f.device)
     res = N.Result()
-    o = make_opts(N_steps, mode, max_iters, edits, events=events)
+    o = make_opts(N_steps, mode, max_iters, edits, events=events, direction=direction)
     rc = N.lib().exactz_correct(ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(fhat.data_ptr()), N.Dims(*d),
                                 ctypes.c_float(float(np.float32(xi))), ctypes.byref(o),
                                 ctypes.c_void_p(g.data_ptr()),
@@ -234,7 +240,8 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: 
 
 def correct_batch(fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "graph",
                   max_iters: int = 1_000_000, edits: bool = True, edits_caps=None, stream=None,
-                  raise_on_error: bool = True, events: str = "reformulated") -> List[dict]:
+                  raise_on_error: bool = True, events: str = "reformulated",
+                  direction: str = "decreasing") -> List[dict]:
     """Correct many independent fields in one run (exactz_correct_batch)."""
     nf = len(fs)
     dl = [dims_of(fs[i], dims[i] if dims else None) for i in range(nf)]
@@ -245,7 +252,7 @@ def correct_batch(fs, fhats, xis, dims=None, N_steps: int = 5, mode: str = "grap
     caps = [default_edits_cap(f.numel()) if edits_caps is None else int(edits_caps[i]) for i, f in enumerate(fs)]
     bufs = [torch.empty((c if edits else 0, 16), dtype=torch.uint8, device=fs[0].device) for c in caps]
     res = (N.Result * nf)()
-    o = make_opts(N_steps, mode, max_iters, edits, events=events)
+    o = make_opts(N_steps, mode, max_iters, edits, events=events, direction=direction)
     rc = N.lib().exactz_correct_batch(
         nf, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
         (N.Dims * nf)(*[N.Dims(*d) for d in dl]), (ctypes.c_float * nf)(*[float(np.float32(x)) for x in xis]),
@@ -300,7 +307,7 @@ def encode_edits(edits, n: int, N_steps: int = 5, stream=None) -> dict:
 
 
 def decode_edits_stream(fhat: torch.Tensor, kcodes: torch.Tensor, lossless: torch.Tensor, xi: float,
-                        N_steps: int = 5, stream=None) -> torch.Tensor:
+                        N_steps: int = 5, stream=None, direction: str = "decreasing") -> torch.Tensor:
     """g from f_hat and the stored edits (exactz_decode_edits)."""
     _check(fhat, "fhat")
     g = torch.empty_like(fhat)
@@ -308,7 +315,7 @@ def decode_edits_stream(fhat: torch.Tensor, kcodes: torch.Tensor, lossless: torc
     if kcodes.numel() != n:
         raise ValueError("kcodes must hold one byte per vertex")
     rc = N.lib().exactz_decode_edits(ctypes.c_void_p(fhat.data_ptr()), n, ctypes.c_float(float(np.float32(xi))),
-                                     int(N_steps), ctypes.c_void_p(kcodes.data_ptr()),
+                                     int(N_steps), DIRECTIONS[direction], ctypes.c_void_p(kcodes.data_ptr()),
                                      ctypes.c_void_p(lossless.data_ptr() if lossless.numel() else 0),
                                      ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(_stream(stream)))
     if rc != N.EXACTZ_OK:

@@ -104,7 +104,8 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
 struct FieldDesc {
     uint32_t nx, ny, nz, N;
     uint64_t n;
-    uint32_t tnx, tny, tnz, pad0;  // tiles per axis (tnx = cp-bitmap words per row)
+    uint32_t tnx, tny, tnz;        // tiles per axis (tnx = cp-bitmap words per row)
+    uint32_t mirror;               // 1: the field is the point reflection of -f (increasing edits)
     uint64_t tbase;                // first global tile id
     uint64_t vbase;                // arena offset (vertices): k, desc, cp_rank, request bits
     uint64_t wbase;                // cp-bitmap offset (words)

@@ -180,7 +180,8 @@ struct exactz_workspace {
     uint32_t *ev_room = nullptr;                 // list room per 32 words of the listed-point bitmap
     unsigned long long *ev_room_off = nullptr;   // its exclusive prefix sums
     uint8_t *ev_tdone = nullptr;                 // per tile: every path end found
-    uint64_t ev_cap[8] = {};  // E, start, cnt, list, radj, room, room_off, tdone (elements)
+    float *refl = nullptr;                       // increasing edits: the reflected -f and -f_hat
+    uint64_t ev_cap[9] = {};  // E, start, cnt, list, radj, room, room_off, tdone, refl (elements)
 
     std::mutex mu;
 };
@@ -212,8 +213,8 @@ void free_ws(exactz_workspace *ws)
     for (cudaEvent_t e : ws->kev)
         if (e) cudaEventDestroy(e);
     for (void *p : ws->allocs) cudaFree(p);
-    void *ev[8] = {ws->ev_E,    ws->ev_start, ws->ev_cnt,      ws->ev_list,
-                   ws->ev_radj, ws->ev_room,  ws->ev_room_off, ws->ev_tdone};
+    void *ev[9] = {ws->ev_E,    ws->ev_start, ws->ev_cnt,      ws->ev_list, ws->ev_radj,
+                   ws->ev_room, ws->ev_room_off, ws->ev_tdone, ws->refl};
     for (void *p : ev)
         if (p) cudaFree(p);
     if (ws->st_f) cudaFree(ws->st_f);
@@ -491,9 +492,10 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     exactz_default_opts(&opt);
     if (o) opt = *o;
     if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH || opt.events > EXACTZ_EVENTS_ORIGINAL ||
-        opt.reserved != 0)
+        opt.direction > EXACTZ_EDITS_INCREASING)
         return EXACTZ_EINVAL;
     const bool events = opt.events == EXACTZ_EVENTS_ORIGINAL;
+    const bool inc = opt.direction == EXACTZ_EDITS_INCREASING;
     if (!f || !fhat || !d || !xi || !g_out || !res) return EXACTZ_EINVAL;
     Layout L;
     int rc = make_layout(nf, d, L);
@@ -519,6 +521,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     if (host) {
         if ((rc = grow_staging(ws, L.total_v, ecap_total)) != EXACTZ_OK) return rc;
     }
+    if (inc && (rc = ev_grow(ws, ws->refl, 8, 2 * L.total_v)) != EXACTZ_OK) return rc;
     for (uint32_t i = 0; i < nf; i++) {
         FieldDesc &F = L.fd[i];
         F.N = opt.N;
@@ -542,6 +545,14 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
             F.fhat = fhat[i];
             F.g = g_out[i];
             F.edits = has_edits ? reinterpret_cast<EditRec *>(edits_out[i]) : nullptr;
+        }
+        if (inc) {  // correct the reflection of -f, -f_hat with decreasing edits
+            float *rf = ws->refl + F.vbase, *rh = ws->refl + L.total_v + F.vbase;
+            launch_reflect_in(F.f, rf, F.n, s);
+            launch_reflect_in(F.fhat, rh, F.n, s);
+            F.f = rf;
+            F.fhat = rh;
+            F.mirror = 1;
         }
     }
     uint64_t hsh = 1469598103934665603ull ^ nf;
@@ -631,8 +642,10 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     launch_finish(D, FS, s);
     mark(6);
     launch_edit_list(D, FS, opt.want_edit_list ? 1 : 0, s);
+    if (inc)  // g back in the caller's coordinates and sign
+        for (uint32_t i = 0; i < nf; i++) launch_reflect_out(L.fd[i].g, ws->desc + L.fd[i].vbase, L.fd[i].n, s);
     mark(7);
-    launches += 4 + (opt.want_edit_list ? 3 : 1);
+    launches += 4 + (opt.want_edit_list ? 3 : 1) + (inc ? 3 * nf : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ws->h_fst, ws->d_fst, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -711,7 +724,7 @@ void exactz_default_opts(exactz_opts *o)
     o->want_edit_list = 1;
     o->profile = 0;
     o->events = EXACTZ_EVENTS_REFORMULATED;
-    o->reserved = 0;
+    o->direction = EXACTZ_EDITS_DECREASING;
 }
 
 exactz_workspace *exactz_workspace_create(uint32_t nfields, const exactz_dims *dims)
@@ -1028,12 +1041,13 @@ int exactz_encode_edits(const exactz_edit *edits, uint64_t n_edits, uint64_t n, 
     return EXACTZ_OK;
 }
 
-int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, const uint8_t *kcodes,
-                        const float *lossless, float *g_out, void *cuda_stream)
+int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, uint32_t direction,
+                        const uint8_t *kcodes, const float *lossless, float *g_out, void *cuda_stream)
 {
     int rc = check_device();
     if (rc) return rc;
-    if (!fhat || !kcodes || !g_out || n == 0 || N < 1 || N > 254 || !(xi > 0.0f) || !std::isfinite(xi))
+    if (!fhat || !kcodes || !g_out || n == 0 || N < 1 || N > 254 || !(xi > 0.0f) || !std::isfinite(xi) ||
+        direction > EXACTZ_EDITS_INCREASING)
         return EXACTZ_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const uint64_t nb = stream_blocks(n);
@@ -1047,7 +1061,8 @@ int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, con
     if ((rc = S.read(s, total, bad))) return rc;
     if (bad || (total && !lossless)) return EXACTZ_EINVAL;
     const float delta = xi / (float)N;  // binary32 division, Sec. 3.3
-    launch_stream_decode(fhat, kcodes, lossless, n, N, delta, S.off, g_out, s);
+    launch_stream_decode(fhat, kcodes, lossless, n, N, delta, direction == EXACTZ_EDITS_INCREASING, S.off, g_out,
+                         s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     return EXACTZ_OK;
@@ -1146,7 +1161,9 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     int rc = check_device();
     if (rc) return rc;
     if (!f || !fhat || !g_out || !res) return EXACTZ_EINVAL;
-    if (opts && opts->events != EXACTZ_EVENTS_REFORMULATED) return EXACTZ_EINVAL;  // its lists are allocated
+    // the event lists and the reflected fields need allocated storage
+    if (opts && (opts->events != EXACTZ_EVENTS_REFORMULATED || opts->direction != EXACTZ_EDITS_DECREASING))
+        return EXACTZ_EINVAL;
     Layout L;
     if ((rc = make_layout(1, &d, L)) != EXACTZ_OK) return rc;
     if (L.total_real > EXACTZ_NOALLOC_MAX_VERTICES) return EXACTZ_ESIZE;

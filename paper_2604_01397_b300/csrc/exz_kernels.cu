@@ -47,6 +47,16 @@ static_assert(WBLOCK % CTA == 0 && VBLOCK % (4 * CTA) == 0, "compaction and edit
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
+// A value of the reflected field back in the caller's sign.  The increasing
+// edit computes fl(g + Delta) or fl(f + xi), which are never -0 for positive
+// Delta and xi, while the negated reflection of an exact zero is -0: edited
+// values (k > 0) are given as +0 then.
+__device__ __forceinline__ float unreflect(float v, uint32_t k)
+{
+    const float w = -v;
+    return (k != 0 && w == 0.0f) ? 0.0f : w;
+}
+
 // ------------------------------------------------------------ requests
 // A request is a bit in the row-word bitmap reqw (one 32-bit word per tile row,
 // bit = x mod 32); setting it twice is harmless, which deduplicates requests.
@@ -1861,21 +1871,46 @@ __global__ void __launch_bounds__(CTA) k_edit_write(Dev D, FieldSet FS)
     const unsigned long long fbase = D.blk_off[F.vbase / VBLOCK - vblk0];
     unsigned long long pos = D.blk_off[blockIdx.x] + ex - fbase;
     if (!c) return;
+    // a reflected field (increasing edits): its records in the caller's
+    // coordinates and order
+    const unsigned long long ne = F.mirror ? D.fst[fid].n_edits : 0ull;
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
         const uint32_t kk = kks[j];
         if (!kk) continue;
-        if (pos < F.edits_cap) {
+        const unsigned long long at = F.mirror ? ne - 1 - pos : pos;
+        if (at < F.edits_cap) {
             const uint64_t t = b + j - F.vbase;
             EditRec r;
-            r.idx = t;
-            r.value = F.g[t];
+            r.idx = F.mirror ? F.n - 1 - t : t;
+            r.value = F.mirror ? unreflect(F.g[t], kk) : F.g[t];
             r.k = (uint8_t)kk;
             r.lossless = kk == N + 1;
             r.reserved = 0;
-            F.edits[pos] = r;
+            F.edits[at] = r;
         }
         pos++;
+    }
+}
+
+// Increasing edits by reflection: dst[v] = -src[n-1-v].
+__global__ void __launch_bounds__(CTA) k_reflect_in(const float *src, float *dst, uint64_t n)
+{
+    for (uint64_t v = (uint64_t)blockIdx.x * CTA + threadIdx.x; v < n; v += (uint64_t)gridDim.x * CTA)
+        dst[v] = -src[n - 1 - v];
+}
+
+// The result back in the caller's coordinates, in place: g[v] <-> -g[n-1-v];
+// an edited value never becomes -0 (see unreflect).
+__global__ void __launch_bounds__(CTA) k_reflect_out(float *g, const uint32_t *desc, uint64_t n)
+{
+    const uint64_t half = (n + 1) / 2;
+    for (uint64_t i = (uint64_t)blockIdx.x * CTA + threadIdx.x; i < half; i += (uint64_t)gridDim.x * CTA) {
+        const uint64_t j = n - 1 - i;
+        const float a = g[i], b = g[j];
+        const uint32_t ki = desc[j] >> D_K_SHIFT, kj = desc[i] >> D_K_SHIFT;  // k of caller vertices i and j
+        g[i] = unreflect(b, ki);
+        if (j != i) g[j] = unreflect(a, kj);
     }
 }
 
@@ -1943,9 +1978,10 @@ __global__ void __launch_bounds__(CTA) k_stream_lossless(const EditRec *edits, u
         if (edits[b + j].lossless) lossless[pos++] = edits[b + j].value;
 }
 
-// Decode: g_i = f_hat_i after k_i steps of fl(g - Delta), or the next lossless value.
+// Decode: g_i = f_hat_i after k_i steps of fl(g - Delta) (fl(g + Delta) with
+// inc), or the next lossless value.
 __global__ void __launch_bounds__(CTA) k_stream_decode(const float *fhat, const uint8_t *kcodes, const float *lossless,
-                                                       uint64_t n, uint32_t N, float delta,
+                                                       uint64_t n, uint32_t N, float delta, int inc,
                                                        const unsigned long long *blk_off, float *g)
 {
     __shared__ uint32_t sw[WARPS];
@@ -1962,7 +1998,7 @@ __global__ void __launch_bounds__(CTA) k_stream_decode(const float *fhat, const 
         if (k == N + 1) {
             v = lossless[pos++];
         } else if (k <= N) {
-            for (uint32_t s = 0; s < k; s++) v = __fsub_rn(v, delta);
+            for (uint32_t s = 0; s < k; s++) v = inc ? __fadd_rn(v, delta) : __fsub_rn(v, delta);
         }
         g[i] = v;
     }
@@ -2151,9 +2187,18 @@ void launch_stream_lossless(const EditRec *edits, uint64_t ne, const unsigned lo
     if (ne) k_stream_lossless<<<stream_blocks(ne), CTA, 0, s>>>(edits, ne, blk_off, lossless);
 }
 void launch_stream_decode(const float *fhat, const uint8_t *kcodes, const float *lossless, uint64_t n, uint32_t N,
-                          float delta, const unsigned long long *blk_off, float *g, cudaStream_t s)
+                          float delta, int inc, const unsigned long long *blk_off, float *g, cudaStream_t s)
 {
-    if (n) k_stream_decode<<<stream_blocks(n), CTA, 0, s>>>(fhat, kcodes, lossless, n, N, delta, blk_off, g);
+    if (n) k_stream_decode<<<stream_blocks(n), CTA, 0, s>>>(fhat, kcodes, lossless, n, N, delta, inc, blk_off, g);
+}
+
+void launch_reflect_in(const float *src, float *dst, uint64_t n, cudaStream_t s)
+{
+    k_reflect_in<<<grid_for(n, CTA, 8), CTA, 0, s>>>(src, dst, n);
+}
+void launch_reflect_out(float *g, const uint32_t *desc, uint64_t n, cudaStream_t s)
+{
+    k_reflect_out<<<grid_for((n + 1) / 2, CTA, 8), CTA, 0, s>>>(g, desc, n);
 }
 
 }  // namespace exz

@@ -37,6 +37,9 @@ void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cuda
 void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);
 void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s);
 void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s);
+// increasing edits by reflection of the field
+void launch_reflect_in(const float *src, float *dst, uint64_t n, cudaStream_t s);
+void launch_reflect_out(float *g, const uint32_t *desc, uint64_t n, cudaStream_t s);
 // edit stream (storage form of a result)
 unsigned stream_blocks(uint64_t items);
 void launch_stream_kcodes(const EditRec *edits, uint64_t ne, uint64_t n, uint32_t N, uint8_t *kcodes, int *bad,
@@ -46,6 +49,6 @@ void launch_stream_count(const EditRec *edits, const uint8_t *kcodes, uint64_t n
 void launch_stream_lossless(const EditRec *edits, uint64_t ne, const unsigned long long *blk_off, float *lossless,
                             cudaStream_t s);
 void launch_stream_decode(const float *fhat, const uint8_t *kcodes, const float *lossless, uint64_t n, uint32_t N,
-                          float delta, const unsigned long long *blk_off, float *g, cudaStream_t s);
+                          float delta, int inc, const unsigned long long *blk_off, float *g, cudaStream_t s);
 
 }  // namespace exz

@@ -491,7 +491,8 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
     exactz_opts o;
     exactz_default_opts(&o);
     if (cfg->opts.N) o = cfg->opts;
-    if (o.N < 1 || o.N > 254 || o.events != EXACTZ_EVENTS_REFORMULATED || o.reserved != 0) return nullptr;
+    if (o.N < 1 || o.N > 254 || o.events != EXACTZ_EVENTS_REFORMULATED || o.direction != EXACTZ_EDITS_DECREASING)
+        return nullptr;
     exactz_server *S = new (std::nothrow) exactz_server();
     if (!S) return nullptr;
     cudaGetDevice(&S->device);

@@ -18,11 +18,12 @@ def k_from_edits(r, n):
     return k
 
 
-def gpu_run(f, fh, xi, dims, mode="graph", N=5, max_iters=1_000_000, events="reformulated"):
+def gpu_run(f, fh, xi, dims, mode="graph", N=5, max_iters=1_000_000, events="reformulated",
+            direction="decreasing"):
     import paper_2604_01397_b300 as ez
 
     r = ez.correct(to_dev(f, dims), to_dev(fh, dims), xi, N_steps=N, mode=mode, max_iters=max_iters,
-                   events=events)
+                   events=events, direction=direction)
     torch.cuda.synchronize()
     return r
 
@@ -43,5 +44,6 @@ def assert_same(r, ref, n, N=5, check_edits=True):
         assert np.array_equal(e["value"].cpu().numpy().view(np.uint32), ref["edit_value"].view(np.uint32))
 
 
-def oracle_run(f, fh, xi, dims, N=5, max_iters=1 << 30, worklist=False, events=False):
-    return oracle.correct(f, fh, xi, dims=dims, N=N, max_iters=max_iters, worklist=worklist, events=events)
+def oracle_run(f, fh, xi, dims, N=5, max_iters=1 << 30, worklist=False, events=False, increasing=False):
+    return oracle.correct(f, fh, xi, dims=dims, N=N, max_iters=max_iters, worklist=worklist, events=events,
+                          increasing=increasing)

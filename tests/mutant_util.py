@@ -11,7 +11,8 @@ import oracle
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "exactz_oracle.c")
 ENTRY_POINTS = ("oracle_mesh", "oracle_classify", "oracle_cp_order", "oracle_correct",
-                "oracle_requests", "oracle_correct_events", "oracle_requests_events")
+                "oracle_requests", "oracle_correct_events", "oracle_requests_events", "oracle_correct_ex",
+                "oracle_requests_ex")
 
 
 @contextlib.contextmanager

@@ -59,7 +59,7 @@ def test_default_opts():
     o = ez._native.Opts()
     ez._native.lib().exactz_default_opts(ctypes.byref(o))
     assert (o.N, o.mode, o.max_iters, o.want_edit_list) == (5, 2, 1000000, 1)
-    assert (o.events, o.reserved) == (ez.EVENTS["reformulated"], 0)
+    assert (o.events, o.direction) == (ez.EVENTS["reformulated"], ez.DIRECTIONS["decreasing"])
 
 
 def test_oracle_and_library_share_no_code():

@@ -169,25 +169,24 @@ def test_fhat_equal_f_needs_no_pass():
 # ------------------------------------------------------------ planted mistakes
 
 EVENT_MUTANTS = {
-    "C3-join-dropped": ("        if (best != C->sel_min[q]) mark(req, best);",
-                        "        if (0 && best != C->sel_min[q]) mark(req, best);"),
-    "C3-join-targets-f-selection": ("        if (best != C->sel_min[q]) mark(req, best);",
-                                    "        if (best != C->sel_min[q]) mark(req, C->sel_min[q]);"),
-    "C3-split-dropped": ("        if (best != C->sel_max[q]) mark(req, C->sel_max[q]);",
-                         "        if (0 && best != C->sel_max[q]) mark(req, C->sel_max[q]);"),
-    "C3-split-targets-g-selection": ("        if (best != C->sel_max[q]) mark(req, C->sel_max[q]);",
-                                     "        if (best != C->sel_max[q]) mark(req, best);"),
-    "C2-dropped": ("    if (prec(g, b, a)) mark(req, a);\n}\n\n/* C3",
-                   "    if (0 && prec(g, b, a)) mark(req, a);\n}\n\n/* C3"),
+    "C3-join-dropped": ("        if (best != C->sel_min[q]) mark(req, C->inc ? C->sel_min[q] : best);",
+                        "        if (0 && best != C->sel_min[q]) mark(req, C->inc ? C->sel_min[q] : best);"),
+    "C3-join-targets-f-selection": ("mark(req, C->inc ? C->sel_min[q] : best);",
+                                    "mark(req, C->inc ? C->sel_min[q] : C->sel_min[q]);"),
+    "C3-split-dropped": ("        if (best != C->sel_max[q]) mark(req, C->inc ? best : C->sel_max[q]);",
+                         "        if (0 && best != C->sel_max[q]) mark(req, C->inc ? best : C->sel_max[q]);"),
+    "C3-split-targets-g-selection": ("mark(req, C->inc ? best : C->sel_max[q]);", "mark(req, C->inc ? best : best);"),
+    "C2-dropped": ("    if (prec(g, b, a)) mark(req, C->inc ? b : a);\n}\n\n/* C3",
+                   "    if (0 && prec(g, b, a)) mark(req, C->inc ? b : a);\n}\n\n/* C3"),
     "EGP-selects-smallest-minimum": (
         "                    if (prec(C->f, best, e[i])) best = e[i];\n                C->sel_min[q] = best;",
         "                    if (prec(C->f, e[i], best)) best = e[i];\n                C->sel_min[q] = best;"),
     "EG-join-paths-ascend": ("const int64_t m = path_end(C->dnf, end_dn, nb[j]);",
                              "const int64_t m = path_end(C->upf, end_dn, nb[j]);"),
-    "EG-path-memo-keeps-first-step": ("        end[w] = m;\n        if (w == u) break;",
-                                      "        end[w] = step[w];\n        if (w == u) break;"),
     "EG-split-paths-from-below": ("                if (!prec(C->f, s, nb[j])) continue;",
                                   "                if (!prec(C->f, nb[j], s)) continue;"),
+    "EG-path-memo-keeps-first-step": ("        end[w] = m;\n        if (w == u) break;",
+                                      "        end[w] = step[w];\n        if (w == u) break;"),
 }
 
 

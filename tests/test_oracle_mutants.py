@@ -16,18 +16,17 @@ from fixpoint import check_fixpoint
 from mutant_util import mutant
 
 MUTANTS = {
-    "R1-down-targets-g-min": ("if (dng != C->dnf[p]) mark(req, C->dnf[p]);",
-                              "if (dng != C->dnf[p]) mark(req, dng);"),
-    "R1-up-targets-f-max": ("if (upg != C->upf[p]) mark(req, upg);",
-                            "if (upg != C->upf[p]) mark(req, C->upf[p]);"),
-    "R2-raises-wrong-end": ("mark(req, below_f ? nb[j] : p);", "mark(req, below_f ? p : nb[j]);"),
+    "R1-down-targets-g-min": ("mark(req, C->inc ? dng : C->dnf[p]);", "mark(req, C->inc ? dng : dng);"),
+    "R1-up-targets-f-max": ("mark(req, C->inc ? C->upf[p] : upg);", "mark(req, C->inc ? C->upf[p] : C->upf[p]);"),
+    "R2-raises-wrong-end": ("mark(req, (below_f != C->inc) ? nb[j] : p);",
+                            "mark(req, (below_f != C->inc) ? p : nb[j]);"),
     "R2-only-f-saddles": ("if (saddle_f || saddle_g) {", "if (saddle_f) {"),
-    "R3-wrong-target": ("C->o[q + 1];\n    if (prec(g, b, a)) mark(req, a);",
-                        "C->o[q + 1];\n    if (prec(g, b, a)) mark(req, b);"),
-    "R3-dropped": ("C->o[q + 1];\n    if (prec(g, b, a)) mark(req, a);",
-                   "C->o[q + 1];\n    if (0 && prec(g, b, a)) mark(req, a);"),
+    "R3-wrong-target": ("C->o[q + 1];\n    if (prec(g, b, a)) mark(req, C->inc ? b : a);",
+                        "C->o[q + 1];\n    if (prec(g, b, a)) mark(req, C->inc ? b : b);"),
+    "R3-dropped": ("C->o[q + 1];\n    if (prec(g, b, a)) mark(req, C->inc ? b : a);",
+                   "C->o[q + 1];\n    if (0 && prec(g, b, a)) mark(req, C->inc ? b : a);"),
     "SoS-reversed": ("(h[a] == h[b] && a < b)", "(h[a] == h[b] && a > b)"),
-    "floor-wrong": ("float floor_x = f[x] - xi;", "float floor_x = f[x] - 2.0f * xi;"),
+    "floor-wrong": ("float floor_x = inc ? f[x] + xi : f[x] - xi;", "float floor_x = inc ? f[x] + xi : f[x] - 2.0f * xi;"),
     "delta-wrong": ("const float delta = xi / (float)N;", "const float delta = xi / (float)(N + 1);"),
     "mesh-wrong-cube-corner": ("int c[3] = {-(s & 1), -((s >> 1) & 1), -((s >> 2) & 1)};",
                                "int c[3] = {-(s & 1), -((s >> 1) & 1), -((s >> 1) & 1)};"),
