@@ -79,13 +79,13 @@ def default_edits_cap(n: int) -> int:
 
 
 def decode_edits(buf: torch.Tensor, count: int) -> Dict[str, torch.Tensor]:
-    """Split a (cap, 16) uint8 record buffer into idx / value / k / lossless."""
+    """Split a (cap, 16) uint8 record buffer into idx / value / k / lossless
+    (strided views into buf, no copies: they change when buf is reused) and
+    the records themselves."""
     count = min(int(count), buf.shape[0])
     b = buf[:count]
-    return dict(idx=b[:, 0:8].contiguous().view(torch.int64).reshape(-1),
-                value=b[:, 8:12].contiguous().view(torch.float32).reshape(-1),
-                k=b[:, 12].contiguous(),
-                lossless=b[:, 13].contiguous().to(torch.bool))
+    return dict(idx=b.view(torch.int64)[:, 0], value=b.view(torch.float32)[:, 2], k=b[:, 12],
+                lossless=b[:, 13].view(torch.bool), records=b)
 
 
 def _result_dict(r: N.Result) -> dict:
@@ -276,6 +276,8 @@ def _edit_records(edits) -> torch.Tensor:
     """A (count, 16) uint8 tensor of exactz_edit records from decode_edits' dict (or the records themselves)."""
     if isinstance(edits, torch.Tensor):
         return edits
+    if "records" in edits:
+        return edits["records"]
     n = edits["idx"].numel()
     dev = edits["idx"].device
     out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
