@@ -125,7 +125,7 @@ class Workspace:
         N.lib().exactz_ws_get_tuning(self._h, ctypes.byref(t))
         return {k: getattr(t, k) for k, _ in N.Tuning._fields_}
 
-    def set_tuning(self, stencil_blocks_per_sm=12, apply_blocks_per_sm=16, pairs_blocks_per_sm=8,
+    def set_tuning(self, stencil_blocks_per_sm=48, apply_blocks_per_sm=32, pairs_blocks_per_sm=8,
                    chunked_schedule=0):
         t = N.Tuning(stencil_blocks_per_sm, apply_blocks_per_sm, pairs_blocks_per_sm, chunked_schedule, 0.0)
         rc = N.lib().exactz_ws_set_tuning(self._h, ctypes.byref(t))

@@ -162,7 +162,7 @@ struct LoopState {
 // warp) takes a contiguous chunk of the tile bitmap's words (1) or every
 // grid-th word (0).
 struct Tuning {
-    uint32_t stencil_bps = 12, apply_bps = 16, pairs_bps = 8, chunked = 0;
+    uint32_t stencil_bps = 48, apply_bps = 32, pairs_bps = 8, chunked = 0;
 };
 
 // All device pointers of one workspace, passed to kernels by value.
