@@ -62,24 +62,9 @@ __device__ __forceinline__ float unreflect(float v, uint32_t k)
 // bit = x mod 32); setting it twice is harmless, which deduplicates requests.
 // Every tile holding a requested vertex is queued once in the apply list.
 //
-// Inside the check kernel a tile first collects its targets as bits of its
-// halo rows in shared memory (34 cells per row: x0-1 .. x0+32), then commits
-// each halo row with at most three word ORs and queues the tiles they fall in.
-struct TileTargets {
-    unsigned long long row[HY * HZ];
-    uint32_t nb;  // 27-bit set of neighbouring tiles (ox, oy, oz in -1..1) holding targets
-};
-
-// Record the closed-star ranks in m of the tile vertex (lx, ly, lz).
-__device__ __forceinline__ void tile_targets_add(TileTargets &T, int lx, int ly, int lz, uint32_t m)
-{
-    while (m) {
-        const int r = __ffs(m) - 1;
-        m &= m - 1;
-        const int row = (lz + 1 + rdz(r)) * HY + (ly + 1 + rdy(r));
-        atomicOr(&T.row[row], 1ull << (lx + 1 + rdx(r)));
-    }
-}
+// The check kernel requests each target where it finds it: one atomic OR into
+// the target's row word and a byte store of its tile's apply flag (both
+// idempotent), with no per-tile collection and so no block barrier.
 
 __device__ __forceinline__ int nb_index(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
@@ -96,53 +81,24 @@ __device__ __forceinline__ void warp_mark_nb_tiles(uint32_t nb, uint32_t tile, u
     }
 }
 
-// Commit the tile's targets (after a barrier); resets T.  PINNED keeps only
-// targets already at the lossless bound (the residual count).
+// Request the closed-star ranks in m of vertex (x, y, z) of field F (every
+// rank in m names a vertex of the field).  PINNED keeps only targets already
+// at the lossless bound (the residual count).
 template <bool PINNED>
-__device__ __forceinline__ void tile_targets_commit(TileTargets &T, const Dev &D, const FieldDesc &F, uint32_t tile,
-                                                    uint32_t tx, int y0, int z0, uint32_t tnx, uint32_t tny)
+__device__ __forceinline__ void emit_targets(const Dev &D, const FieldDesc &F, uint32_t x, uint32_t y, uint32_t z,
+                                             uint32_t m)
 {
-    for (int row = threadIdx.x; row < HY * HZ; row += blockDim.x) {
-        unsigned long long m = T.row[row];
-        if (!m) continue;
-        T.row[row] = 0;
-        const int hz = row / HY, hy = row - hz * HY;
-        const uint32_t Y = (uint32_t)(y0 - 1 + hy), Z = (uint32_t)(z0 - 1 + hz);
-        const uint64_t rw = F.wbase + ((uint64_t)Z * F.ny + Y) * tnx;  // word of tile column 0 in this row
-        if (PINNED) {  // drop targets that are not pinned
-            unsigned long long keep = 0, mm = m;
-            const uint64_t rb = ((uint64_t)Z * F.ny + Y) * F.nx;
-            while (mm) {
-                const int hx = __ffsll(mm) - 1;
-                mm &= mm - 1;
-                const uint64_t t = rb + (uint64_t)((int)(tx * TX) - 1 + hx);
-                if ((D.desc[F.vbase + t] >> D_K_SHIFT) > F.N) keep |= 1ull << hx;
-            }
-            m = keep;
-            if (!m) continue;
-        }
-        const int oy = hy == 0 ? -1 : (hy == TY + 1 ? 1 : 0), oz = hz == 0 ? -1 : (hz == TZ + 1 ? 1 : 0);
-        uint32_t nb = 0;
-        if (m & 1ull) {
-            atomicOr(&D.reqw[rw + tx - 1], 0x80000000u);
-            nb |= 1u << nb_index(-1, oy, oz);
-        }
-        const uint32_t mid = (uint32_t)(m >> 1);
-        if (mid) {
-            atomicOr(&D.reqw[rw + tx], mid);
-            nb |= 1u << nb_index(0, oy, oz);
-        }
-        if ((m >> 33) & 1ull) {
-            atomicOr(&D.reqw[rw + tx + 1], 1u);
-            nb |= 1u << nb_index(1, oy, oz);
-        }
-        atomicOr(&T.nb, nb);
+    while (m) {
+        const int r = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t X = (uint32_t)((int)x + rdx(r)), Y = (uint32_t)((int)y + rdy(r)),
+                       Z = (uint32_t)((int)z + rdz(r));
+        const uint64_t row = (uint64_t)Z * F.ny + Y;
+        if (PINNED && (D.desc[F.vbase + row * F.nx + X] >> D_K_SHIFT) <= F.N) continue;
+        atomicOr(&D.reqw[F.wbase + row * F.tnx + (X >> 5)], 1u << (X & 31));
+        const uint32_t tile = (uint32_t)(F.tbase + (X >> 5) + (uint64_t)F.tnx * (Y / TY + (uint64_t)F.tny * (Z / TZ)));
+        if (!D.apply_flag[tile]) D.apply_flag[tile] = 1;
     }
-    __syncthreads();
-    const uint32_t nb = T.nb;
-    if (threadIdx.x < 32) warp_mark_nb_tiles(nb, tile, tnx, tny, D.apply_flag);
-    __syncthreads();
-    if (threadIdx.x == 0) T.nb = 0;
 }
 
 // Request vertex t of field F from outside a tile (the CP-pair check): set its
@@ -287,7 +243,6 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
     __shared__ __align__(16) float sa[NB][HALO_N];
     __shared__ __align__(16) float sb[MODE == SM_SETUP ? NB : 1][MODE == SM_SETUP ? HALO_N : 4];
     __shared__ uint32_t smulti[512];
-    __shared__ TileTargets tt;
     __shared__ uint32_t s_err, s_ncp;
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
     __shared__ uint8_t s_vis[MODE == SM_CHECK_LIST ? STWARPS : 1][TY * TX];  // a warp's dirty vertices (ly << 5 | lx)
@@ -295,9 +250,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
     __shared__ TileGeo s_geo[NB];         // its position
 
     for (int j = threadIdx.x; j < 512; j += SCTA) smulti[j] = D.multi[j];
-    for (int w = threadIdx.x; w < HY * HZ; w += SCTA) tt.row[w] = 0;
     if (threadIdx.x == 0) {
-        tt.nb = 0;
         s_err = 0;
         s_ncp = 0;
     }
@@ -382,7 +335,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
         const uint32_t fid = G.fid, tx = G.tx;
         const int x0 = G.x0, y0 = G.y0, z0 = G.z0;
         const FieldDesc &F = D.fields[fid];
-        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny;
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx;
         const uint64_t vbase = F.vbase;
         const float *S = sa[b];
         const uint32_t *RW = s_rw[b];
@@ -469,7 +422,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
                     req = request_mask(smulti, d, sg);
                 }
             }
-            if (MODE != SM_CLASSIFY && req) tile_targets_add(tt, lx, ly, lz, req);
+            if (MODE != SM_CLASSIFY && req) emit_targets<MODE == SM_PINNED>(D, F, x, y, z, req);
             if (MODE == SM_SETUP) {
                 const uint32_t w = __ballot_sync(0xffffffffu, listed);
                 if (lane == 0 && y < ny && z < nz)
@@ -480,8 +433,7 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
                 }
             }
         }
-        __syncthreads();
-        if (MODE != SM_CLASSIFY) tile_targets_commit<MODE == SM_PINNED>(tt, D, F, tile, tx, y0, z0, tnx, tny);
+        if (MODE == SM_SETUP || MODE == SM_CLASSIFY) __syncthreads();  // the block's error and CP counts
         if (MODE == SM_SETUP && threadIdx.x == 0 && s_err) {
             atomicOr(&D.fst[fid].err, s_err);
             s_err = 0;
