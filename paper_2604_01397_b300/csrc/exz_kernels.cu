@@ -202,7 +202,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 constexpr uint32_t NO_TILE = 0xFFFFFFFFu;
 
@@ -546,12 +546,11 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
             const uint32_t t = next_tile();
             if (lane == 0) s_tile[b ^ 1] = t;
         }
-        __syncthreads();  // s_tile[b ^ 1] is set; buffer b ^ 1 is free
+        cp_async_wait_all();  // this thread's copies of `cur`, the only ones in flight, have landed
+        __syncthreads();      // everyone's have; s_tile[b ^ 1] is set; buffer b ^ 1 is free
         const uint32_t nxt = s_tile[b ^ 1];
-        if (nxt != NO_TILE) stage(nxt, b ^ 1);
+        if (nxt != NO_TILE) stage(nxt, b ^ 1);  // lands while `cur` is checked
         cp_async_commit();
-        cp_async_wait_prev();  // this thread's copies of `cur` have landed
-        __syncthreads();       // everyone's have
         process(cur, b);
     }
     if (MODE == SM_CHECK_LIST && threadIdx.x == 0 && src.ntiles) atomicAdd(&D.ls->sum_tiles, src.ntiles);
