@@ -161,7 +161,8 @@ struct exactz_workspace {
     FieldState *h_fst = nullptr;  // pinned host copy
     LoopState *h_ls = nullptr;
 
-    cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;  // graph capture: the pass body forks in two
+    cudaEvent_t cap_fork = nullptr, cap_join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[6] = {0, 0, 0, 0, 0, 0};
@@ -208,6 +209,9 @@ void free_ws(exactz_workspace *ws)
     if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
     if (ws->graph) cudaGraphDestroy(ws->graph);
     if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
+    if (ws->cap_stream2) cudaStreamDestroy(ws->cap_stream2);
+    if (ws->cap_fork) cudaEventDestroy(ws->cap_fork);
+    if (ws->cap_join) cudaEventDestroy(ws->cap_join);
     for (cudaEvent_t e : ws->ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ws->kev)
@@ -293,6 +297,9 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     CK(cudaMallocHost(&ws->h_fst, sizeof(FieldState) * L.nfields));
     CK(cudaMallocHost(&ws->h_ls, sizeof(LoopState)));
     CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ws->cap_stream2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ws->cap_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ws->cap_join, cudaEventDisableTiming));
     for (cudaEvent_t &e : ws->ev) CK(cudaEventCreate(&e));
     for (cudaEvent_t &e : ws->kev) CK(cudaEventCreate(&e));
     return EXACTZ_OK;
@@ -380,8 +387,14 @@ int ensure_graph(exactz_workspace *ws, const Dev &D)
     CK(cudaStreamEndCapture(cs, &g));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    // the vertex check and the CP-pair check read nothing the other writes
+    // (both only OR request bits and set apply flags): they run side by side
+    CK(cudaEventRecord(ws->cap_fork, cs));
+    CK(cudaStreamWaitEvent(ws->cap_stream2, ws->cap_fork, 0));
+    launch_pairs_list(D, ws->cap_stream2);
+    CK(cudaEventRecord(ws->cap_join, ws->cap_stream2));
     launch_check_list(D, cs);
-    launch_pairs_list(D, cs);
+    CK(cudaStreamWaitEvent(cs, ws->cap_join, 0));
     launch_apply(D, 1, cs);
     launch_book(D, h, 1, cs);
     CK(cudaStreamEndCapture(cs, &body));
