@@ -171,8 +171,10 @@ int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const
 /* Statistics of the last exactz_ws_correct on a workspace.  stage_ms holds
  * CUDA-event times on the call's stream when opts.profile was 1 (else 0):
  * [0] set-up stencil kernel, [1] critical-point compaction, [2] radix sort
- * (with EXACTZ_EVENTS_ORIGINAL also the extremum-graph set-up), [3] first pass (pair check, apply, bookkeeping), [4] the loop,
- * [5] residual and status, [6] edit list, [7] whole call on the device. */
+ * (with EXACTZ_EVENTS_ORIGINAL also the extremum-graph set-up), [3] first
+ * pass (pair check, apply, bookkeeping), [4] the loop, [5] residual and
+ * status, [6] the edit list's time beyond [5] (it runs beside the residual
+ * check) and the reflection of increasing edits, [7] whole call on the device. */
 typedef struct {
     uint64_t kernel_launches; /* kernels the call executed (graph bodies counted per pass) */
     uint64_t passes;          /* edit passes run for the slowest field, including the last check */

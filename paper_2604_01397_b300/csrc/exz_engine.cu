@@ -163,6 +163,8 @@ struct exactz_workspace {
 
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;  // graph capture: the pass body forks in two
     cudaEvent_t cap_fork = nullptr, cap_join = nullptr;
+    cudaStream_t aux = nullptr;  // the edit list, beside the residual check
+    cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[6] = {0, 0, 0, 0, 0, 0};
@@ -212,6 +214,9 @@ void free_ws(exactz_workspace *ws)
     if (ws->cap_stream2) cudaStreamDestroy(ws->cap_stream2);
     if (ws->cap_fork) cudaEventDestroy(ws->cap_fork);
     if (ws->cap_join) cudaEventDestroy(ws->cap_join);
+    if (ws->aux) cudaStreamDestroy(ws->aux);
+    if (ws->aux_fork) cudaEventDestroy(ws->aux_fork);
+    if (ws->aux_join) cudaEventDestroy(ws->aux_join);
     for (cudaEvent_t e : ws->ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ws->kev)
@@ -300,6 +305,9 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     CK(cudaStreamCreateWithFlags(&ws->cap_stream2, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ws->cap_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ws->cap_join, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&ws->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ws->aux_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ws->aux_join, cudaEventDisableTiming));
     for (cudaEvent_t &e : ws->ev) CK(cudaEventCreate(&e));
     for (cudaEvent_t &e : ws->kev) CK(cudaEventCreate(&e));
     return EXACTZ_OK;
@@ -649,12 +657,23 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         }
     }
     mark(5);
-    // residual violations on pinned vertices, status, edit list
+    // residual violations on pinned vertices and status; beside them the edit
+    // list (the edit counts are final; the residual check writes only request
+    // bits, flags and counters the edit list does not read)
+    cudaStream_t es = ws->aux ? ws->aux : s;
+    if (es != s) {
+        CK(cudaEventRecord(ws->aux_fork, s));
+        CK(cudaStreamWaitEvent(es, ws->aux_fork, 0));
+    }
+    launch_edit_list(D, FS, opt.want_edit_list ? 1 : 0, es);
     launch_check_pinned(D, FS, s);
     launch_pairs_pinned(D, FS, s);
     launch_finish(D, FS, s);
     mark(6);
-    launch_edit_list(D, FS, opt.want_edit_list ? 1 : 0, s);
+    if (es != s) {
+        CK(cudaEventRecord(ws->aux_join, es));
+        CK(cudaStreamWaitEvent(s, ws->aux_join, 0));
+    }
     if (inc)  // g back in the caller's coordinates and sign
         for (uint32_t i = 0; i < nf; i++) launch_reflect_out(L.fd[i].g, ws->desc + L.fd[i].vbase, L.fd[i].n, s);
     mark(7);
