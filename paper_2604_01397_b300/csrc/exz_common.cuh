@@ -10,6 +10,7 @@
 // over ranks in that order therefore implements the index tie-break.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace exz {
@@ -19,17 +20,18 @@ constexpr int TX = 32;   // tile width: one warp per tile row, one cp-bitmap wor
 constexpr int TY = 4;
 constexpr int TZ = 4;
 constexpr int TILE_V = TX * TY * TZ;
-// Halo tile in shared memory: HY x HZ rows of HXP floats.  Slot XOFF + j of a
-// row holds x = x0 + j, so x0 - 1 .. x0 + TX sit at slots XOFF - 1 .. XOFF + TX
-// and the TX tile values start on a 16-byte boundary.  The last slot of a row,
-// XOFF + TX = HXP, is the first (padding) slot of the next row; one spare float
-// after the last row holds it there.
+// Halo tile in shared memory: HY x HZ rows of HXP floats.  Slot j of a row
+// holds x = x0 - XOFF + j, so x0 - 1 .. x0 + TX sit at slots XOFF - 1 .. XOFF + TX
+// and the TX tile values start on a 16-byte boundary.  The whole halo is the
+// box of one TMA tile load (cp.async.bulk.tensor) whose x coordinate, x0 - XOFF,
+// is 16-byte aligned; cells outside the field read as NaN.
 constexpr int XOFF = 4;
-constexpr int HXP = TX + XOFF;
+constexpr int HXP = TX + 2 * XOFF;
 constexpr int HY = TY + 2;
 constexpr int HZ = TZ + 2;
-constexpr int HALO_N = (HXP * HY * HZ + 1 + 3) / 4 * 4;  // rounded to 16 bytes
-static_assert(HXP % 4 == 0 && XOFF >= 1, "halo rows start and tile values sit on 16-byte boundaries");
+constexpr int HALO_N = HXP * HY * HZ;
+static_assert(HXP % 4 == 0 && XOFF >= 1 && XOFF % 4 == 0, "halo rows, tile values and the TMA x coordinate on 16 bytes");
+static_assert((HALO_N * 4) % 128 == 0, "consecutive halo buffers keep the 128-byte alignment of TMA destinations");
 constexpr int CTA = 256;
 constexpr int WARPS = CTA / 32;
 constexpr int ROWS = TY * TZ;
@@ -106,6 +108,8 @@ struct FieldDesc {
     uint64_t n;
     uint32_t tnx, tny, tnz;        // tiles per axis (tnx = cp-bitmap words per row)
     uint32_t mirror;               // 1: the field is the point reflection of -f (increasing edits)
+    uint32_t tma;                  // 1: halos are loaded with the tensor maps Dev::tmaps[3 * field slot ..]
+    uint32_t pad1;
     uint64_t tbase;                // first global tile id
     uint64_t vbase;                // arena offset (vertices): k, desc, cp_rank, request bits
     uint64_t wbase;                // cp-bitmap offset (words)
@@ -153,7 +157,7 @@ struct LoopState {
     unsigned long long ev_cursor[3];  // event-list set-up: minima and maxima list ends, saddle-list end
     uint32_t any_active;
     uint32_t pass;
-    uint32_t overflow;
+    uint32_t fault;  // a bounded wait ran out (the call reports EXACTZ_ENODEV)
     uint32_t ev_changed;  // event-list set-up: a path end moved in the last jump round
 };
 
@@ -206,6 +210,9 @@ struct Dev {
     // ev_radj[h] = its number of linked saddles, followed by their positions q.
     // In pairbits, the pair bits are followed by the event bits of the next
     // pass and the event bits of the residual check, one word range each.
+    // TMA tensor maps of each field's f, f_hat and g (3 per field slot; used
+    // where FieldDesc::tma is set)
+    const CUtensorMap *tmaps;
     uint32_t events;
     const uint32_t *ev_start;
     const uint16_t *ev_cnt;

@@ -21,6 +21,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "exactz.h"
 #include "exz_common.cuh"
 #include "exz_launch.h"
@@ -145,6 +147,7 @@ struct exactz_workspace {
     uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
     uint32_t *pin_pair_arena = nullptr;
     uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
+    CUtensorMap *d_tmaps = nullptr;  // TMA maps of each field's f, f_hat, g (3 per field slot)
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
     uint32_t *blk = nullptr;
@@ -281,6 +284,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->pin_tile_bits, T / 32 + 1);
     AL(ws->pin_pair_arena, 2 * C);
     AL(ws->fids, L.nfields);
+    AL(ws->d_tmaps, 3ull * L.nfields);
     AL(ws->cp_key[0], C);
     AL(ws->cp_key[1], C);
     AL(ws->cp_ent[0], C);
@@ -317,6 +321,7 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
 {
     Dev D{};
     D.fields = ws->d_fields;
+    D.tmaps = ws->d_tmaps;
     D.fst = ws->d_fst;
     D.ls = ws->d_ls;
     D.nfields = L.nfields;
@@ -432,6 +437,43 @@ int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
         ws->st_cap_edits = E;
     }
     return EXACTZ_OK;
+}
+
+// TMA tensor maps of the halo loads (one 3D tile box of HXP x HY x HZ floats,
+// NaN outside the field).  The box's x coordinate is always 16-byte aligned
+// (x0 - XOFF); the map needs rows of a multiple of 16 bytes (nx % 4 == 0) and a
+// 16-byte aligned base.  Returns false (the field keeps the cp.async halo
+// loads) where a map cannot be made.
+bool make_halo_map(CUtensorMap *map, const float *base, const FieldDesc &F)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else if (getenv("EXACTZ_DEBUG"))
+            fprintf(stderr, "exactz: cuTensorMapEncodeTiled not found (%d, %d)\n", (int)e, (int)q);
+        cudaGetLastError();
+    });
+    if (!encode || !base || (F.nx % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) {
+        if (getenv("EXACTZ_DEBUG"))
+            fprintf(stderr, "exactz: no halo map (encoder %s, nx %u, base %p)\n", encode ? "found" : "missing", F.nx,
+                    (const void *)base);
+        return false;
+    }
+    const cuuint64_t dims[3] = {F.nx, F.ny, F.nz};
+    const cuuint64_t strides[2] = {4ull * F.nx, 4ull * F.nx * F.ny};
+    const cuuint32_t box[3] = {(cuuint32_t)HXP, (cuuint32_t)HY, (cuuint32_t)HZ};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
+                              elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA);
+    if (r != CUDA_SUCCESS && getenv("EXACTZ_DEBUG"))
+        fprintf(stderr, "exactz: halo map encoding failed (%d) for %u x %u x %u\n", (int)r, F.nx, F.ny, F.nz);
+    return r == CUDA_SUCCESS;
 }
 
 // Grow one event buffer (index i of ws->ev_cap) to `need` elements; contents are not kept.
@@ -576,6 +618,16 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
             F.mirror = 1;
         }
     }
+    if (ws->d_tmaps) {  // halo loads by TMA where the fields allow it
+        std::vector<CUtensorMap> maps(3ull * nf);
+        for (uint32_t i = 0; i < nf; i++) {
+            FieldDesc &F = L.fd[i];
+            F.tma = make_halo_map(&maps[3ull * i], F.f, F) && make_halo_map(&maps[3ull * i + 1], F.fhat, F) &&
+                    make_halo_map(&maps[3ull * i + 2], F.g, F);
+            if (getenv("EXACTZ_DEBUG")) fprintf(stderr, "exactz: field %u halo loads by %s\n", i, F.tma ? "TMA" : "cp.async");
+        }
+        CK(cudaMemcpyAsync(ws->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, s));
+    }
     uint64_t hsh = 1469598103934665603ull ^ nf;
     for (uint32_t i = 0; i < nf; i++) {
         const uint64_t v[3] = {d[i].nx, d[i].ny, d[i].nz};
@@ -640,7 +692,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
                     loop_ms[k] += t;
                 }
             }
-            if (!ws->h_ls->any_active) break;
+            if (!ws->h_ls->any_active || ws->h_ls->fault) break;
             if (prof) cudaEventRecord(ws->kev[0], s);
             if (opt.mode == EXACTZ_MODE_PLAIN) launch_check_all(D, s);
             else launch_check_list(D, s);
@@ -682,6 +734,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemcpyAsync(ws->h_fst, ws->d_fst, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (ws->h_ls->fault) return EXACTZ_ENODEV;  // a halo load never completed
     std::memset(&ws->stats, 0, sizeof(ws->stats));
     ws->stats.passes = ws->h_ls->pass;
     ws->stats.total_critical = ws->h_ls->total_cp;

@@ -204,6 +204,45 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// TMA tile loads completing on an mbarrier (transaction count in bytes).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Wait for the completion of phase `parity`, a bounded number of tries;
+// false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < (1u << 22); i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// Order this thread's earlier shared-memory accesses before later TMA writes.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// The box of tensor map `map` at (x, y, z) into shared memory at dst (128-byte aligned).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
 constexpr uint32_t NO_TILE = 0xFFFFFFFFu;
 
 // Position of a tile in its field.
@@ -240,8 +279,9 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
                                                       uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
     constexpr int NB = 2;
-    __shared__ __align__(16) float sa[NB][HALO_N];
-    __shared__ __align__(16) float sb[MODE == SM_SETUP ? NB : 1][MODE == SM_SETUP ? HALO_N : 4];
+    __shared__ __align__(128) float sa[NB][HALO_N];
+    __shared__ __align__(128) float sb[MODE == SM_SETUP ? NB : 1][MODE == SM_SETUP ? HALO_N : 32];
+    __shared__ __align__(8) uint64_t s_mbar[NB];  // completion of each buffer's TMA loads
     __shared__ uint32_t smulti[512];
     __shared__ uint32_t s_err, s_ncp;
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
@@ -253,7 +293,11 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
     if (threadIdx.x == 0) {
         s_err = 0;
         s_ncp = 0;
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+        mbar_init_fence();
     }
+    uint32_t tma_pending = 0, tma_phase = 0;  // per buffer: a TMA load in flight; the parity it completes
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float qnan = __int_as_float(0x7fc00000);
 
@@ -268,6 +312,18 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
             const uint32_t y = (uint32_t)G.y0 + threadIdx.x % TY, z = (uint32_t)G.z0 + threadIdx.x / TY;
             if (y < ny && z < nz) cp_async4(&s_rw[b][threadIdx.x], D.dirty + F.wbase + ((uint64_t)z * ny + y) * F.tnx + G.tx);
             else s_rw[b][threadIdx.x] = 0;
+        }
+        if (F.tma) {  // the whole halo (NaN outside the field) in one TMA load per array
+            tma_pending |= 1u << b;
+            if (threadIdx.x == 0) {
+                const CUtensorMap *maps = D.tmaps + 3ull * G.fid;
+                fence_proxy_async();  // the buffer's earlier reads come first
+                mbar_expect_tx(&s_mbar[b], (MODE == SM_SETUP ? 2u : 1u) * (uint32_t)(HALO_N * sizeof(float)));
+                tma_load_3d(sa[b], maps + ((MODE == SM_SETUP || MODE == SM_CLASSIFY) ? 0 : 2), G.x0 - XOFF, G.y0 - 1,
+                            G.z0 - 1, &s_mbar[b]);
+                if (MODE == SM_SETUP) tma_load_3d(sb[b], maps + 1, G.x0 - XOFF, G.y0 - 1, G.z0 - 1, &s_mbar[b]);
+            }
+            return;
         }
         const float *A = (MODE == SM_SETUP || MODE == SM_CLASSIFY) ? F.f : F.g;
         const float *B = F.fhat;
@@ -547,7 +603,18 @@ __global__ void __launch_bounds__(SCTA, 12) k_stencil(Dev D, uint32_t *desc_out,
             if (lane == 0) s_tile[b ^ 1] = t;
         }
         cp_async_wait_all();  // this thread's copies of `cur`, the only ones in flight, have landed
-        __syncthreads();      // everyone's have; s_tile[b ^ 1] is set; buffer b ^ 1 is free
+        bool ok = true;
+        if (tma_pending & (1u << b)) {  // and the tile's TMA load
+            ok = mbar_wait(&s_mbar[b], (tma_phase >> b) & 1u);
+            tma_phase ^= 1u << b;
+            tma_pending &= ~(1u << b);
+        }
+        // everyone's have landed; s_tile[b ^ 1] is set; buffer b ^ 1 is free
+        if (__syncthreads_or(!ok)) {  // a load that never completed: report, give it one more bounded wait, stop
+            if (threadIdx.x == 0) atomicOr(&D.ls->fault, 1u);
+            if (!ok) mbar_wait(&s_mbar[b], ((tma_phase >> b) & 1u) ^ 1u);
+            break;
+        }
         const uint32_t nxt = s_tile[b ^ 1];
         if (nxt != NO_TILE) stage(nxt, b ^ 1);  // lands while `cur` is checked
         cp_async_commit();
