@@ -920,7 +920,7 @@ int exactz_ws_autotune(exactz_workspace *ws, uint32_t nfields, const float *cons
     float best = 0.f;
     if (!rc) rc = time_one(best);  // also warms the graph and caches
     if (!rc) rc = time_one(best);
-    // candidates per knob: blocks per SM of the check (12 resident), apply (4
+    // candidates per knob: blocks per SM of the check (10 resident), apply (4
     // resident) and pair kernels, and the schedule
     static const uint32_t cands[4][5] = {{6, 12, 24, 36, 48}, {4, 8, 16, 32, 0}, {2, 4, 8, 16, 0}, {0, 1, 0, 0, 0}};
     static const int ncand[4] = {5, 4, 4, 2};

@@ -275,7 +275,7 @@ __device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
 // The next tile is staged with cp.async into a second buffer while the
 // current one is checked.
 template <int MODE>
-__global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : 12) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
+__global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHECK_LIST || MODE == SM_PINNED) ? 10 : 12)) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
                                                       uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
     constexpr int NB = 2;
