@@ -32,6 +32,7 @@ constexpr int HZ = TZ + 2;
 constexpr int HALO_N = HXP * HY * HZ;
 static_assert(HXP % 4 == 0 && XOFF >= 1 && XOFF % 4 == 0, "halo rows, tile values and the TMA x coordinate on 16 bytes");
 static_assert((HALO_N * 4) % 128 == 0, "consecutive halo buffers keep the 128-byte alignment of TMA destinations");
+constexpr int TMAPS = 4;  // tensor maps per field: f, f_hat, g, descriptors
 constexpr int CTA = 256;
 constexpr int WARPS = CTA / 32;
 constexpr int ROWS = TY * TZ;
@@ -108,7 +109,7 @@ struct FieldDesc {
     uint64_t n;
     uint32_t tnx, tny, tnz;        // tiles per axis (tnx = cp-bitmap words per row)
     uint32_t mirror;               // 1: the field is the point reflection of -f (increasing edits)
-    uint32_t tma;                  // 1: halos are loaded with the tensor maps Dev::tmaps[3 * field slot ..]
+    uint32_t tma;                  // 1: tiles are loaded with the tensor maps Dev::tmaps[TMAPS * field slot ..]
     uint32_t pad1;
     uint64_t tbase;                // first global tile id
     uint64_t vbase;                // arena offset (vertices): k, desc, cp_rank, request bits
@@ -210,8 +211,8 @@ struct Dev {
     // ev_radj[h] = its number of linked saddles, followed by their positions q.
     // In pairbits, the pair bits are followed by the event bits of the next
     // pass and the event bits of the residual check, one word range each.
-    // TMA tensor maps of each field's f, f_hat and g (3 per field slot; used
-    // where FieldDesc::tma is set)
+    // TMA tensor maps of each field's f, f_hat, g (halo boxes) and descriptors
+    // (tile boxes), TMAPS per field slot; used where FieldDesc::tma is set
     const CUtensorMap *tmaps;
     uint32_t events;
     const uint32_t *ev_start;

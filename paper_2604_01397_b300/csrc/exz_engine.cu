@@ -147,7 +147,7 @@ struct exactz_workspace {
     uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
     uint32_t *pin_pair_arena = nullptr;
     uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
-    CUtensorMap *d_tmaps = nullptr;  // TMA maps of each field's f, f_hat, g (3 per field slot)
+    CUtensorMap *d_tmaps = nullptr;  // TMA maps of each field's f, f_hat, g, descriptors (TMAPS per field slot)
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
     uint32_t *blk = nullptr;
@@ -284,7 +284,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->pin_tile_bits, T / 32 + 1);
     AL(ws->pin_pair_arena, 2 * C);
     AL(ws->fids, L.nfields);
-    AL(ws->d_tmaps, 3ull * L.nfields);
+    AL(ws->d_tmaps, (uint64_t)TMAPS * L.nfields);
     AL(ws->cp_key[0], C);
     AL(ws->cp_key[1], C);
     AL(ws->cp_ent[0], C);
@@ -439,12 +439,12 @@ int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
     return EXACTZ_OK;
 }
 
-// TMA tensor maps of the halo loads (one 3D tile box of HXP x HY x HZ floats,
-// NaN outside the field).  The box's x coordinate is always 16-byte aligned
+// TMA tensor maps of the tile loads: a halo box of HXP x HY x HZ floats (NaN
+// outside the field) of f, f_hat or g, or the tile's TX x TY x TZ descriptors.  The box's x coordinate is always 16-byte aligned
 // (x0 - XOFF); the map needs rows of a multiple of 16 bytes (nx % 4 == 0) and a
 // 16-byte aligned base.  Returns false (the field keeps the cp.async halo
 // loads) where a map cannot be made.
-bool make_halo_map(CUtensorMap *map, const float *base, const FieldDesc &F)
+bool make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
@@ -466,11 +466,13 @@ bool make_halo_map(CUtensorMap *map, const float *base, const FieldDesc &F)
     }
     const cuuint64_t dims[3] = {F.nx, F.ny, F.nz};
     const cuuint64_t strides[2] = {4ull * F.nx, 4ull * F.nx * F.ny};
-    const cuuint32_t box[3] = {(cuuint32_t)HXP, (cuuint32_t)HY, (cuuint32_t)HZ};
+    const cuuint32_t box[3] = {halo ? (cuuint32_t)HXP : (cuuint32_t)TX, halo ? (cuuint32_t)HY : (cuuint32_t)TY,
+                               halo ? (cuuint32_t)HZ : (cuuint32_t)TZ};
     const cuuint32_t elem[3] = {1, 1, 1};
-    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
-                              elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA);
+    const CUresult r = encode(map, halo ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                              const_cast<void *>(base), dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              halo ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS && getenv("EXACTZ_DEBUG"))
         fprintf(stderr, "exactz: halo map encoding failed (%d) for %u x %u x %u\n", (int)r, F.nx, F.ny, F.nz);
     return r == CUDA_SUCCESS;
@@ -618,12 +620,13 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
             F.mirror = 1;
         }
     }
-    if (ws->d_tmaps) {  // halo loads by TMA where the fields allow it
-        std::vector<CUtensorMap> maps(3ull * nf);
+    if (ws->d_tmaps) {  // tile loads by TMA where the fields allow it
+        std::vector<CUtensorMap> maps((uint64_t)TMAPS * nf);
         for (uint32_t i = 0; i < nf; i++) {
             FieldDesc &F = L.fd[i];
-            F.tma = make_halo_map(&maps[3ull * i], F.f, F) && make_halo_map(&maps[3ull * i + 1], F.fhat, F) &&
-                    make_halo_map(&maps[3ull * i + 2], F.g, F);
+            CUtensorMap *m = &maps[(uint64_t)TMAPS * i];
+            F.tma = make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) && make_map(m + 2, F.g, F, true) &&
+                    make_map(m + 3, ws->desc + F.vbase, F, false);
             if (getenv("EXACTZ_DEBUG")) fprintf(stderr, "exactz: field %u halo loads by %s\n", i, F.tma ? "TMA" : "cp.async");
         }
         CK(cudaMemcpyAsync(ws->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, s));

@@ -282,6 +282,8 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     __shared__ __align__(128) float sa[NB][HALO_N];
     __shared__ __align__(128) float sb[MODE == SM_SETUP ? NB : 1][MODE == SM_SETUP ? HALO_N : 32];
     __shared__ __align__(8) uint64_t s_mbar[NB];  // completion of each buffer's TMA loads
+    constexpr bool CHECK = MODE == SM_CHECK_ALL || MODE == SM_CHECK_LIST || MODE == SM_PINNED;
+    __shared__ __align__(128) uint32_t s_desc[NB][CHECK ? TILE_V : 32];  // the tile's descriptors (TMA fields)
     __shared__ uint32_t smulti[512];
     __shared__ uint32_t s_err, s_ncp;
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
@@ -316,12 +318,14 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
         if (F.tma) {  // the whole halo (NaN outside the field) in one TMA load per array
             tma_pending |= 1u << b;
             if (threadIdx.x == 0) {
-                const CUtensorMap *maps = D.tmaps + 3ull * G.fid;
+                const CUtensorMap *maps = D.tmaps + (uint64_t)TMAPS * G.fid;
                 fence_proxy_async();  // the buffer's earlier reads come first
-                mbar_expect_tx(&s_mbar[b], (MODE == SM_SETUP ? 2u : 1u) * (uint32_t)(HALO_N * sizeof(float)));
+                mbar_expect_tx(&s_mbar[b], (MODE == SM_SETUP ? 2u : 1u) * (uint32_t)(HALO_N * sizeof(float)) +
+                                               (CHECK ? (uint32_t)(TILE_V * sizeof(uint32_t)) : 0u));
                 tma_load_3d(sa[b], maps + ((MODE == SM_SETUP || MODE == SM_CLASSIFY) ? 0 : 2), G.x0 - XOFF, G.y0 - 1,
                             G.z0 - 1, &s_mbar[b]);
                 if (MODE == SM_SETUP) tma_load_3d(sb[b], maps + 1, G.x0 - XOFF, G.y0 - 1, G.z0 - 1, &s_mbar[b]);
+                if (CHECK) tma_load_3d(s_desc[b], maps + 3, G.x0, G.y0, G.z0, &s_mbar[b]);
             }
             return;
         }
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
                         req = request_mask(smulti, d, sg);
                     }
                 } else {
-                    const uint32_t d = __ldg(&D.desc[vbase + i]);
+                    const uint32_t d = F.tma ? s_desc[b][(lz * TY + ly) * TX + lx] : __ldg(&D.desc[vbase + i]);
                     Stn sg = interior ? stencil15<true>(S, c) : stencil15<false>(S, c);
                     req = request_mask(smulti, d, sg);
                 }
