@@ -439,45 +439,6 @@ int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
     return EXACTZ_OK;
 }
 
-// TMA tensor maps of the tile loads: a halo box of HXP x HY x HZ floats (NaN
-// outside the field) of f, f_hat or g, or the tile's TX x TY x TZ descriptors.  The box's x coordinate is always 16-byte aligned
-// (x0 - XOFF); the map needs rows of a multiple of 16 bytes (nx % 4 == 0) and a
-// 16-byte aligned base.  Returns false (the field keeps the cp.async halo
-// loads) where a map cannot be made.
-bool make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
-            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-        else if (getenv("EXACTZ_DEBUG"))
-            fprintf(stderr, "exactz: cuTensorMapEncodeTiled not found (%d, %d)\n", (int)e, (int)q);
-        cudaGetLastError();
-    });
-    if (!encode || !base || (F.nx % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) {
-        if (getenv("EXACTZ_DEBUG"))
-            fprintf(stderr, "exactz: no halo map (encoder %s, nx %u, base %p)\n", encode ? "found" : "missing", F.nx,
-                    (const void *)base);
-        return false;
-    }
-    const cuuint64_t dims[3] = {F.nx, F.ny, F.nz};
-    const cuuint64_t strides[2] = {4ull * F.nx, 4ull * F.nx * F.ny};
-    const cuuint32_t box[3] = {halo ? (cuuint32_t)HXP : (cuuint32_t)TX, halo ? (cuuint32_t)HY : (cuuint32_t)TY,
-                               halo ? (cuuint32_t)HZ : (cuuint32_t)TZ};
-    const cuuint32_t elem[3] = {1, 1, 1};
-    const CUresult r = encode(map, halo ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
-                              const_cast<void *>(base), dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              halo ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS && getenv("EXACTZ_DEBUG"))
-        fprintf(stderr, "exactz: halo map encoding failed (%d) for %u x %u x %u\n", (int)r, F.nx, F.ny, F.nz);
-    return r == CUDA_SUCCESS;
-}
-
 // Grow one event buffer (index i of ws->ev_cap) to `need` elements; contents are not kept.
 template <class T>
 int ev_grow(exactz_workspace *ws, T *&p, int i, uint64_t need)
@@ -798,6 +759,45 @@ const uint32_t *exz::host_multi_table()
 {
     std::call_once(g_multi_once, build_multi_table);
     return g_multi_host;
+}
+
+// TMA tensor maps of the tile loads: a halo box of HXP x HY x HZ floats (NaN
+// outside the field) of f, f_hat or g, or the tile's TX x TY x TZ descriptors.  The box's x coordinate is always 16-byte aligned
+// (x0 - XOFF); the map needs rows of a multiple of 16 bytes (nx % 4 == 0) and a
+// 16-byte aligned base.  Returns false (the field keeps the cp.async halo
+// loads) where a map cannot be made.
+bool exz::make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else if (getenv("EXACTZ_DEBUG"))
+            fprintf(stderr, "exactz: cuTensorMapEncodeTiled not found (%d, %d)\n", (int)e, (int)q);
+        cudaGetLastError();
+    });
+    if (!encode || !base || (F.nx % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) {
+        if (getenv("EXACTZ_DEBUG"))
+            fprintf(stderr, "exactz: no halo map (encoder %s, nx %u, base %p)\n", encode ? "found" : "missing", F.nx,
+                    (const void *)base);
+        return false;
+    }
+    const cuuint64_t dims[3] = {F.nx, F.ny, F.nz};
+    const cuuint64_t strides[2] = {4ull * F.nx, 4ull * F.nx * F.ny};
+    const cuuint32_t box[3] = {halo ? (cuuint32_t)HXP : (cuuint32_t)TX, halo ? (cuuint32_t)HY : (cuuint32_t)TY,
+                               halo ? (cuuint32_t)HZ : (cuuint32_t)TZ};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    const CUresult r = encode(map, halo ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                              const_cast<void *>(base), dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              halo ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS && getenv("EXACTZ_DEBUG"))
+        fprintf(stderr, "exactz: halo map encoding failed (%d) for %u x %u x %u\n", (int)r, F.nx, F.ny, F.nz);
+    return r == CUDA_SUCCESS;
 }
 
 // ---------------------------------------------------------------- C ABI

@@ -10,6 +10,8 @@ void launch_fill_u32(uint32_t *p, uint32_t v, uint64_t n, cudaStream_t s);
 int device_sms();
 // 2^14-bit link-component table (host copy, built on first use; see exz_engine.cu)
 const uint32_t *host_multi_table();
+// TMA map of a field's halo box (halo) or descriptor tile; false where the field cannot be mapped
+bool make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo);
 
 void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s);
 void launch_check_all(const Dev &D, cudaStream_t s);

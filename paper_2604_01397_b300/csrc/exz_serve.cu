@@ -130,9 +130,11 @@ struct exactz_server {
     uint32_t *hist = nullptr;
     uint32_t sort_blocks = 0;
     uint32_t *d_retire = nullptr;
+    CUtensorMap *d_tmaps = nullptr;  // TMA maps of each slot's f, f_hat, g, descriptors (TMAPS per slot)
 
     FieldState *h_fst = nullptr;
     FieldDesc *h_fd = nullptr;
+    CUtensorMap *h_tmaps = nullptr;
     uint32_t *h_retire = nullptr;
     cudaStream_t cs = nullptr, xs = nullptr;  // compute, copy
     cudaEvent_t in_ev = nullptr;               // inputs landed (re-recorded per admission)
@@ -168,6 +170,7 @@ void free_server(exactz_server *S)
     for (void *p : S->allocs) cudaFree(p);
     if (S->h_fst) cudaFreeHost(S->h_fst);
     if (S->h_fd) cudaFreeHost(S->h_fd);
+    if (S->h_tmaps) cudaFreeHost(S->h_tmaps);
     if (S->h_retire) cudaFreeHost(S->h_retire);
     for (auto &kv : S->reqs) delete kv.second;
     delete S;
@@ -220,6 +223,7 @@ Dev server_dev(const exactz_server *S)
     D.hist = S->hist;
     D.sort_blocks = S->sort_blocks;
     D.tile_field = S->tile_field;
+    D.tmaps = S->d_tmaps;
     D.tun = Tuning{};  // default launch schedule
     return D;
 }
@@ -336,12 +340,19 @@ int start_request(exactz_server *S, const Dev &D, Req *r)
     F.edits_cap = r->ne;
     F.pin_tiles = S->pin_tile_arena + r->t0;
     F.pin_pairs = S->pin_pair_arena + 2 * r->c0;
+    // tile loads by TMA where the room's arrays can be mapped (else cp.async)
+    CUtensorMap *m = S->h_tmaps + (uint64_t)TMAPS * slot;
+    F.tma = make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) && make_map(m + 2, F.g, F, true) &&
+            make_map(m + 3, S->desc + r->v0, F, false);
     S->h_fd[slot] = F;
     SK(cudaMemcpyAsync(S->f + r->v0, r->f, r->n * 4, cudaMemcpyHostToDevice, S->xs));
     SK(cudaMemcpyAsync(S->fhat + r->v0, r->fhat, r->n * 4, cudaMemcpyHostToDevice, S->xs));
     SK(cudaEventRecord(S->in_ev, S->xs));
     // meanwhile clear the room on the compute stream (it may hold an earlier field's state)
     SK(cudaMemcpyAsync(S->d_fields + slot, &S->h_fd[slot], sizeof(FieldDesc), cudaMemcpyHostToDevice, S->cs));
+    if (F.tma)
+        SK(cudaMemcpyAsync(S->d_tmaps + (uint64_t)TMAPS * slot, m, sizeof(CUtensorMap) * TMAPS, cudaMemcpyHostToDevice,
+                           S->cs));
     SK(cudaMemsetAsync(S->d_fst + slot, 0, sizeof(FieldState), S->cs));
     SK(cudaMemsetAsync(S->desc + r->v0, 0, r->nv * 4, S->cs));
     SK(cudaMemsetAsync(S->cpwords + r->w0, 0, r->nw * 4, S->cs));
@@ -521,9 +532,11 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
               salloc(S, S->cp_ent[0], C) && salloc(S, S->cp_ent[1], C) && salloc(S, S->gs, C) &&
               salloc(S, S->pairbits, C / 32 + 1) && salloc(S, S->pin_pair_arena, 2 * C) &&
               salloc(S, S->edits, S->E) && salloc(S, S->blk, nblk) && salloc(S, S->blk_off, nblk) &&
-              salloc(S, S->hist, 256ull * S->sort_blocks) && salloc(S, S->d_retire, S->slots);
+              salloc(S, S->hist, 256ull * S->sort_blocks) && salloc(S, S->d_retire, S->slots) &&
+              salloc(S, S->d_tmaps, (uint64_t)TMAPS * S->slots);
     ok = ok && cudaMallocHost(&S->h_fst, sizeof(FieldState) * S->slots) == cudaSuccess &&
          cudaMallocHost(&S->h_fd, sizeof(FieldDesc) * S->slots) == cudaSuccess &&
+         cudaMallocHost(&S->h_tmaps, sizeof(CUtensorMap) * TMAPS * S->slots) == cudaSuccess &&
          cudaMallocHost(&S->h_retire, 4ull * S->slots) == cudaSuccess &&
          cudaStreamCreateWithFlags(&S->cs, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&S->xs, cudaStreamNonBlocking) == cudaSuccess &&

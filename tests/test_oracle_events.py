@@ -11,8 +11,9 @@ branch decomposition used to check them.
   pairs is left alone (while the reformulated constraints of Sec. 4.3 request
   it);
 * corrections: every field converges, the fixpoint invariants hold with the
-  saddle order in place of the full critical-point order, and the brute-force
-  merge trees, extremum graph and branch decompositions of f and g agree;
+  saddle order in place of the full critical-point order, the brute-force
+  merge trees and extremum graphs of f and g agree, and so does the extremum
+  each saddle selects over the extremum graph of f;
 * planted mistakes in the event rules each fail one of the above.
 """
 import numpy as np
