@@ -297,9 +297,9 @@ def run_ours(a):
     ebuf = torch.empty((cap, 16), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(mode=a.mode, profile=True, events=a.events):
+    def step(mode=a.mode, profile=True, events=a.events, direction="decreasing"):
         return ws.correct([f], [fh], [xi], mode=mode, g_out=[g], edit_bufs=[ebuf], profile=profile,
-                          events=events)[0]
+                          events=events, direction=direction)[0]
 
     tuning = ws.autotune([f], [fh], [xi], repeats=2, events=a.events) if not a.no_autotune else ws.tuning()
 
@@ -401,6 +401,17 @@ def run_ours(a):
             "iterations": ro["iterations"], "status": ro["status_name"], "n_edits": ro["n_edits"],
             "n_lossless": ro["n_lossless"], "listed_points": so["total_critical"],
             "stage_ms": so["stage_ms"]}
+        # monotone increasing edits on the same input (the reflected field through the same kernels)
+        step(a.mode, True, a.events, "increasing")
+        e0.record(stream)
+        ri = step(a.mode, True, a.events, "increasing")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ims = e0.elapsed_time(e1)
+        extras["increasing_edits"] = {
+            "ms": ims, "gbs": 4.0 * n / (ims / 1e3) / 1e9, "ratio_to_timed": ims / ms,
+            "iterations": ri["iterations"], "status": ri["status_name"], "n_edits": ri["n_edits"],
+            "n_lossless": ri["n_lossless"], "stage_ms": ws.stats()["stage_ms"]}
         step(a.mode, False)  # leave g and the edit list of the timed configuration
 
     e2e = None
