@@ -369,6 +369,22 @@ def run_ours(a):
               "n_lossless": r["n_lossless"], "n_critical": r["n_critical"], "passes": st["passes"],
               "stage_ms": stages, "mvertices_per_s": n / (ms / 1e3) / 1e6,
               "workspace_gib": ws.nbytes / 2 ** 30}
+    # Whole-correction HBM fraction: the algorithmic bytes of the schedule that
+    # ran (from the correction's counters) over the step time at the copy peak.
+    # Set-up: f and f_hat read, descriptor and g written; CP list: row bits
+    # read, key and index written; sort: 4 passes of key + entry read and
+    # written, then rank scatter and value gather; check: per checked tile its
+    # g values, descriptors and dirty words; pairs: two sorted values; apply:
+    # descriptor and g read-modify-write, f and CP rank read per request; edit
+    # list: descriptors scanned, 16-byte records plus g and descriptor read per
+    # edit.  (The residual check on pinned stars is left out.)
+    ncp = float(r["n_critical"])
+    terms = {"setup": 16.0 * n, "cp_list": n / 8 + 12.0 * ncp, "sort": (4 * 24 + 8) * ncp,
+             "check": float(st["sum_tiles"]) * (TILE_V * 8 + 16 * 4), "pairs": 8.0 * st["sum_pairs"],
+             "apply": 24.0 * st["sum_requests"], "edit_list": 4.0 * n + 24.0 * r["n_edits"]}
+    tot = sum(terms.values())
+    extras["step_hbm"] = {"bytes": tot, "gbs": tot / (ms / 1e3) / 1e9, "frac": tot / (ms / 1e3) / 1e9 / peak,
+                          "peak": peak, "terms_bytes": terms}
     if not a.no_extras:
         for mode in ("plain", "frontier"):
             if mode == a.mode:
@@ -427,10 +443,27 @@ def run_ours(a):
             rh = ws.correct([fc], [hc], [xi], g_out=[gc], edit_bufs=[ec], host_buffers=True, mode=a.mode,
                             events=a.events)[0]
         torch.cuda.synchronize()
+        sms = 1e3 * (time.perf_counter() - t0) / a.steps
+        seq_same = bool(torch.equal(gc.view(torch.int32), g.cpu().view(torch.int32)))
+        # The K steps through the sequence entry point (exactz_ws_correct_sequence):
+        # step i+1's inputs are copied in and step i-1's results copied out while
+        # step i is corrected.  Every step still copies its f and f_hat in and its
+        # g and edit records out inside the timed region.
+        ws.correct_sequence([fc] * 2, [hc] * 2, [xi] * 2, [gc] * 2, [ec] * 2, mode=a.mode, events=a.events)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = ws.correct_sequence([fc] * a.steps, [hc] * a.steps, [xi] * a.steps, [gc] * a.steps, [ec] * a.steps,
+                                 mode=a.mode, events=a.events)
+        torch.cuda.synchronize()
         ems = 1e3 * (time.perf_counter() - t0) / a.steps
+        same = bool(torch.equal(gc.view(torch.int32), g.cpu().view(torch.int32))) and \
+            all(x["n_edits"] == r["n_edits"] and x["iterations"] == r["iterations"] for x in rs)
         e2e = {"value": 4.0 * n / (ems / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
-               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 16 * min(rh["n_edits"], cap) + 48,
-               "same_result": bool(torch.equal(gc.view(torch.int32), g.cpu().view(torch.int32)))}
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 16 * min(rs[-1]["n_edits"], cap) + 48,
+               "api": f"Workspace.correct_sequence over the {a.steps} steps (host buffers)",
+               "same_result": same and seq_same,
+               "sequential": {"value": 4.0 * n / (sms / 1e3) / 1e9, "ms_per_step": sms,
+                              "api": "Workspace.correct(host_buffers=True), one step after another"}}
 
     cpu = None
     if not a.no_cpu and world == 1:

@@ -168,6 +168,31 @@ int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const
                       exactz_edit *const *edits_out, const uint64_t *edits_cap,
                       exactz_result *res, void *cuda_stream, int host_buffers);
 
+/* Correct a sequence of nitems host-resident fields of one shape d, one after
+ * another on the workspace, each as exactz_correct would alone (Alg. 1 to
+ * its fixpoint; opts for all, xi[i] per field), with the copies of the
+ * neighbouring fields overlapping each correction: while field i runs on
+ * cuda_stream, field i+1's f and f_hat are copied in on a copy-in stream and
+ * field i-1's g and edit records copied out on a copy-out stream (two device
+ * slots of inputs and outputs, held by the workspace, grown on first use).
+ *   f[i], fhat[i]  HOST arrays of d.nx*d.ny*d.nz floats (pinned for overlap; read)
+ *   g_out[i]       HOST array of as many floats (written)
+ *   edits_out[i]   HOST array of edits_cap[i] records, or NULL (edits_out and
+ *                  edits_cap may be NULL: no edit lists)
+ *   res[i]         per-field result (zeroed for fields not reached)
+ * The copy-in stream starts after the work queued on cuda_stream before the
+ * call; the call returns with every copy landed.  Output arrays may be shared
+ * between fields (the copies out run in field order: the last one stays).
+ * Errors: EXACTZ_EINVAL (a null pointer, xi[i] <= 0 or not finite, bad dims
+ * or opts) before any copy; otherwise the first error of a field stops the
+ * sequence there (earlier fields' results are complete) and is returned;
+ * EXACTZ_ECAP as for exactz_correct (the sequence goes on). */
+int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const float *const *f,
+                               const float *const *fhat, exactz_dims d, const float *xi,
+                               const exactz_opts *opts, float *const *g_out,
+                               exactz_edit *const *edits_out, const uint64_t *edits_cap,
+                               exactz_result *res, void *cuda_stream);
+
 /* Statistics of the last exactz_ws_correct on a workspace.  stage_ms holds
  * CUDA-event times on the call's stream when opts.profile was 1 (else 0):
  * [0] set-up stencil kernel, [1] critical-point compaction, [2] radix sort

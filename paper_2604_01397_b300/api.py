@@ -205,6 +205,57 @@ class Workspace:
             out.append(d)
         return out
 
+    def correct_sequence(self, fs: Sequence[torch.Tensor], fhats: Sequence[torch.Tensor], xis: Sequence[float],
+                         g_outs: Sequence[torch.Tensor], edit_bufs: Optional[Sequence[torch.Tensor]] = None,
+                         dims=None, N_steps: int = 5, mode: str = "graph", max_iters: int = 1_000_000,
+                         stream=None, raise_on_error: bool = True, profile: bool = False,
+                         events: str = "reformulated", direction: str = "decreasing") -> List[dict]:
+        """Correct host-resident fields of one shape one after another
+        (exactz_ws_correct_sequence): field i+1 is copied in and field i-1
+        copied out while field i is corrected.  fs, fhats: pinned host float32
+        tensors; g_outs[i] (and edit_bufs[i], records of 16 bytes) pinned host
+        outputs, which fields may share (the last field written stays).
+        Returns one result dict per field ("g" and "edits" view its buffers)."""
+        n = len(fs)
+        if not (len(fhats) == len(xis) == len(g_outs) == n) or (edit_bufs is not None and len(edit_bufs) != n):
+            raise ValueError("fs, fhats, xis, g_outs (and edit_bufs) must have one entry per field")
+        for i in range(n):
+            _check(fs[i], "f", True)
+            _check(fhats[i], "fhat", True)
+        d = dims_of(fs[0], dims) if n else (1, 1, 1)
+        nv = d[0] * d[1] * d[2]
+        for i in range(n):
+            if fs[i].numel() != nv or fhats[i].numel() != nv or g_outs[i].numel() != nv:
+                raise ValueError(f"field {i}: f, fhat and g_out must hold {nv} values")
+            if g_outs[i].is_cuda or g_outs[i].dtype != torch.float32 or not g_outs[i].is_contiguous():
+                raise ValueError(f"field {i}: g_out must be a contiguous float32 host tensor")
+            if edit_bufs is not None:
+                b = edit_bufs[i]
+                if b.is_cuda or b.dtype != torch.uint8 or b.dim() != 2 or b.shape[1] != 16 or not b.is_contiguous():
+                    raise ValueError(f"field {i}: edit buffer must be a contiguous (cap, 16) uint8 host tensor")
+        xarr = (ctypes.c_float * max(n, 1))(*[float(np.float32(x)) for x in xis])
+        caps = [b.shape[0] for b in edit_bufs] if edit_bufs is not None else [0] * n
+        carr = (ctypes.c_uint64 * max(n, 1))(*caps)
+        res = (N.Result * max(n, 1))()
+        o = make_opts(N_steps, mode, max_iters, edit_bufs is not None, profile, events, direction)
+        rc = N.lib().exactz_ws_correct_sequence(
+            self._h, n, N.ptr_array([t.data_ptr() for t in fs]), N.ptr_array([t.data_ptr() for t in fhats]),
+            N.Dims(*d), xarr, ctypes.byref(o), N.ptr_array([t.data_ptr() for t in g_outs]),
+            N.ptr_array([b.data_ptr() for b in edit_bufs] if edit_bufs is not None else [0] * n), carr, res,
+            ctypes.c_void_p(_stream(stream)))
+        if rc not in (N.EXACTZ_OK, N.EXACTZ_ECAP) and raise_on_error:
+            raise ExactzError(rc, "exactz_ws_correct_sequence")
+        out = []
+        for i in range(n):
+            r = _result_dict(res[i])
+            r["rc"] = rc
+            r["g"] = g_outs[i]
+            if edit_bufs is not None:
+                r["edits"] = decode_edits(edit_bufs[i], r["n_edits"])
+                r["edits_truncated"] = r["n_edits"] > caps[i]
+            out.append(r)
+        return out
+
 
 def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: int = 5,
             mode: str = "graph", max_iters: int = 1_000_000, edits: bool = True, edits_cap=None,

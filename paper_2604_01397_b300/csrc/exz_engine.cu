@@ -160,6 +160,13 @@ struct exactz_workspace {
     uint64_t st_cap_v = 0;
     EditRec *st_edits = nullptr;
     uint64_t st_cap_edits = 0;
+    // sequence staging (exactz_ws_correct_sequence): two slots of inputs and
+    // outputs, a copy-in and a copy-out stream, grown on first use
+    float *sq_f[2] = {}, *sq_fhat[2] = {}, *sq_g[2] = {};
+    EditRec *sq_edits[2] = {};
+    uint64_t sq_cap_v = 0, sq_cap_edits = 0;
+    cudaStream_t sq_in = nullptr, sq_out = nullptr;
+    cudaEvent_t sq_start = nullptr, sq_in_ev[2] = {}, sq_out_ev[2] = {};
 
     FieldState *h_fst = nullptr;  // pinned host copy
     LoopState *h_ls = nullptr;
@@ -233,6 +240,17 @@ void free_ws(exactz_workspace *ws)
     if (ws->st_fhat) cudaFree(ws->st_fhat);
     if (ws->st_g) cudaFree(ws->st_g);
     if (ws->st_edits) cudaFree(ws->st_edits);
+    if (ws->sq_in) cudaStreamSynchronize(ws->sq_in);
+    if (ws->sq_out) cudaStreamSynchronize(ws->sq_out);
+    for (int b = 0; b < 2; b++) {
+        for (void *p : {(void *)ws->sq_f[b], (void *)ws->sq_fhat[b], (void *)ws->sq_g[b], (void *)ws->sq_edits[b]})
+            if (p) cudaFree(p);
+        if (ws->sq_in_ev[b]) cudaEventDestroy(ws->sq_in_ev[b]);
+        if (ws->sq_out_ev[b]) cudaEventDestroy(ws->sq_out_ev[b]);
+    }
+    if (ws->sq_start) cudaEventDestroy(ws->sq_start);
+    if (ws->sq_in) cudaStreamDestroy(ws->sq_in);
+    if (ws->sq_out) cudaStreamDestroy(ws->sq_out);
     if (ws->h_fst) cudaFreeHost(ws->h_fst);
     if (ws->h_ls) cudaFreeHost(ws->h_ls);
     delete ws;
@@ -435,6 +453,46 @@ int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
         ws->st_cap_edits = 0;
         CK(cudaMalloc(&ws->st_edits, E * sizeof(EditRec)));
         ws->st_cap_edits = E;
+    }
+    return EXACTZ_OK;
+}
+
+// Two slots of sequence staging for fields of V vertices and E edit records,
+// plus the copy streams and their events (created once).
+int grow_sequence(exactz_workspace *ws, uint64_t V, uint64_t E)
+{
+    if (!ws->sq_in) {
+        CK(cudaStreamCreateWithFlags(&ws->sq_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&ws->sq_out, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ws->sq_start, cudaEventDisableTiming));
+        for (int b = 0; b < 2; b++) {
+            CK(cudaEventCreateWithFlags(&ws->sq_in_ev[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ws->sq_out_ev[b], cudaEventDisableTiming));
+        }
+    }
+    if (V > ws->sq_cap_v) {
+        for (int b = 0; b < 2; b++) {
+            for (float **p : {&ws->sq_f[b], &ws->sq_fhat[b], &ws->sq_g[b]}) {
+                if (*p) cudaFree(*p);
+                *p = nullptr;
+            }
+        }
+        ws->sq_cap_v = 0;
+        for (int b = 0; b < 2; b++) {
+            CK(cudaMalloc(&ws->sq_f[b], V * 4));
+            CK(cudaMalloc(&ws->sq_fhat[b], V * 4));
+            CK(cudaMalloc(&ws->sq_g[b], V * 4));
+        }
+        ws->sq_cap_v = V;
+    }
+    if (E > ws->sq_cap_edits) {
+        for (int b = 0; b < 2; b++) {
+            if (ws->sq_edits[b]) cudaFree(ws->sq_edits[b]);
+            ws->sq_edits[b] = nullptr;
+        }
+        ws->sq_cap_edits = 0;
+        for (int b = 0; b < 2; b++) CK(cudaMalloc(&ws->sq_edits[b], E * sizeof(EditRec)));
+        ws->sq_cap_edits = E;
     }
     return EXACTZ_OK;
 }
@@ -852,6 +910,87 @@ int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const
     std::lock_guard<std::mutex> lk(ws->mu);
     return run(ws, nfields, f, fhat, d, xi, opts, g_out, edits_out, edits_cap, res,
                static_cast<cudaStream_t>(cuda_stream), host_buffers);
+}
+
+int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const float *const *f,
+                               const float *const *fhat, exactz_dims d, const float *xi,
+                               const exactz_opts *opts, float *const *g_out, exactz_edit *const *edits_out,
+                               const uint64_t *edits_cap, exactz_result *res, void *cuda_stream)
+{
+    if (!ws || !f || !fhat || !xi || !g_out || !res) return EXACTZ_EINVAL;
+    exactz_opts opt;
+    exactz_default_opts(&opt);
+    if (opts) opt = *opts;
+    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH || opt.events > EXACTZ_EVENTS_ORIGINAL ||
+        opt.direction > EXACTZ_EDITS_INCREASING)
+        return EXACTZ_EINVAL;
+    Layout L;
+    if (int rc = make_layout(1, &d, L)) return rc;
+    const uint64_t n = L.fd[0].n;
+    uint64_t ecap = 0;
+    for (uint32_t i = 0; i < nitems; i++) {
+        if (!f[i] || !fhat[i] || !g_out[i]) return EXACTZ_EINVAL;
+        if (!(xi[i] > 0.0f) || !std::isfinite(xi[i])) return EXACTZ_EINVAL;
+        if (edits_out && edits_out[i] && edits_cap) ecap = std::max<uint64_t>(ecap, edits_cap[i]);
+    }
+    std::memset(res, 0, sizeof(exactz_result) * nitems);
+    if (nitems == 0) return EXACTZ_OK;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    CK(cudaSetDevice(ws->device));
+    if (int rc = grow_sequence(ws, n, opt.want_edit_list ? ecap : 0)) return rc;
+    const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the copies in start after the caller's earlier work on its stream
+    CK(cudaEventRecord(ws->sq_start, s));
+    CK(cudaStreamWaitEvent(ws->sq_in, ws->sq_start, 0));
+    auto copy_in = [&](uint32_t i) -> bool {
+        const int b = (int)(i & 1u);
+        return cudaMemcpyAsync(ws->sq_f[b], f[i], n * 4, cudaMemcpyHostToDevice, ws->sq_in) == cudaSuccess &&
+               cudaMemcpyAsync(ws->sq_fhat[b], fhat[i], n * 4, cudaMemcpyHostToDevice, ws->sq_in) == cudaSuccess &&
+               cudaEventRecord(ws->sq_in_ev[b], ws->sq_in) == cudaSuccess;
+    };
+    int ret = copy_in(0) ? EXACTZ_OK : EXACTZ_ENODEV;
+    for (uint32_t i = 0; i < nitems && (ret == EXACTZ_OK || ret == EXACTZ_ECAP); i++) {
+        const int b = (int)(i & 1u);
+        // the next field's inputs go to the other slot, whose field (i - 1) is finished
+        if (i + 1 < nitems && !copy_in(i + 1)) {
+            ret = EXACTZ_ENODEV;
+            break;
+        }
+        // this slot's inputs have landed and its outputs (field i - 2) have left
+        if (cudaStreamWaitEvent(s, ws->sq_in_ev[b], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ws->sq_out_ev[b], 0) != cudaSuccess) {
+            ret = EXACTZ_ENODEV;
+            break;
+        }
+        const float *fi = ws->sq_f[b], *hi = ws->sq_fhat[b];
+        float *gi = ws->sq_g[b];
+        const bool want = opt.want_edit_list && edits_out && edits_out[i] && edits_cap && edits_cap[i] > 0;
+        exactz_edit *ei = want ? reinterpret_cast<exactz_edit *>(ws->sq_edits[b]) : nullptr;
+        const uint64_t ci = want ? edits_cap[i] : 0;
+        const int rc = run(ws, 1, &fi, &hi, &d, &xi[i], &opt, &gi, &ei, &ci, &res[i], s, 0);
+        if (rc != EXACTZ_OK && rc != EXACTZ_ECAP) {
+            ret = rc;
+            break;
+        }
+        if (rc == EXACTZ_ECAP) ret = rc;
+        // run() returned with the field finished: its results leave on the copy-out stream
+        bool ok = cudaMemcpyAsync(g_out[i], gi, n * 4, cudaMemcpyDeviceToHost, ws->sq_out) == cudaSuccess;
+        const uint64_t ne = want ? std::min<uint64_t>(res[i].n_edits, ci) : 0;
+        if (ok && ne)
+            ok = cudaMemcpyAsync(edits_out[i], ei, ne * sizeof(EditRec), cudaMemcpyDeviceToHost, ws->sq_out) ==
+                 cudaSuccess;
+        if (!ok || cudaEventRecord(ws->sq_out_ev[b], ws->sq_out) != cudaSuccess) {
+            ret = EXACTZ_ENODEV;
+            break;
+        }
+    }
+    const bool drained =
+        cudaStreamSynchronize(ws->sq_in) == cudaSuccess && cudaStreamSynchronize(ws->sq_out) == cudaSuccess;
+    if (!drained) {
+        cudaGetLastError();
+        if (ret == EXACTZ_OK || ret == EXACTZ_ECAP) ret = EXACTZ_ENODEV;
+    }
+    return ret;
 }
 
 int exactz_ws_get_tuning(const exactz_workspace *ws, exactz_tuning *out)
