@@ -72,16 +72,11 @@ def parse():
 
 # ---------------------------------------------------------------- workloads
 def workload_spec(name: str, size: int = 0, rel: float = 0.0):
-    from synth.fields import CONFIGS
+    from synth.fields import WORKLOADS
 
-    if name == "bumps512":
-        c = dict(CONFIGS[2])
-    elif name == "bumps64":
-        c = dict(CONFIGS[1])
-    elif name == "octave1024":
-        c = dict(CONFIGS[3])
-    else:
+    if name not in WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
+    c = dict(WORKLOADS[name])
     if size:
         vol = float(np.prod(c["dims"]))
         c["dims"] = (size, size, size)

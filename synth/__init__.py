@@ -15,5 +15,5 @@ from .fields import (  # noqa: F401
     make_case,
     batched_specs,
     serving_requests,
-    CONFIGS,
+    WORKLOADS,
 )

@@ -37,14 +37,15 @@ import torch
 
 Dims = Tuple[int, int, int]
 
-# The five workloads (x fastest).  Config 4 and 5 are generated per field /
-# per request by ``batched_specs`` and ``serving_requests``.
-CONFIGS: Dict[int, dict] = {
-    1: dict(name="bumps64", kind="bumps", dims=(64, 64, 64), n_bumps=32,
+# The single-field workloads by name (x fastest).  The batched and serving
+# workloads are generated per field / per request by ``batched_specs`` and
+# ``serving_requests``.
+WORKLOADS: Dict[str, dict] = {
+    "bumps64": dict(name="bumps64", kind="bumps", dims=(64, 64, 64), n_bumps=32,
             sigma=(2.0, 8.0), seed=0, rel=1e-3, fhat="quantised"),
-    2: dict(name="bumps512", kind="bumps", dims=(512, 512, 512), n_bumps=4096,
+    "bumps512": dict(name="bumps512", kind="bumps", dims=(512, 512, 512), n_bumps=4096,
             sigma=(2.0, 16.0), seed=1, rel=1e-4, fhat="uniform"),
-    3: dict(name="octave1024", kind="octave", dims=(1024, 1024, 1024),
+    "octave1024": dict(name="octave1024", kind="octave", dims=(1024, 1024, 1024),
             seed=2, rel=1e-4, rels=(1e-2, 1e-3, 1e-4), fhat="quantised"),
 }
 
@@ -168,9 +169,9 @@ def make_case(kind: str, dims: Dims, seed: int, rel: float, fhat: str,
     return f, fh, xi
 
 
-def config_case(cfg: int, device="cpu", rel: float | None = None):
-    """(f, f_hat, xi) of workload 1, 2 or 3 (optionally overriding rel)."""
-    c = CONFIGS[cfg]
+def workload_case(name: str, device="cpu", rel: float | None = None):
+    """(f, f_hat, xi) of the named workload (optionally overriding rel)."""
+    c = WORKLOADS[name]
     return make_case(c["kind"], c["dims"], c["seed"], c["rel"] if rel is None else rel,
                      c["fhat"], n_bumps=c.get("n_bumps"), sigma=c.get("sigma", (2.0, 8.0)),
                      device=device)

@@ -86,7 +86,7 @@ def test_iteration_cap(mode):
 
 @pytest.mark.parametrize("mode", MODES)
 def test_workload_64(mode):
-    f, fh, xi = synth.fields.config_case(1)
+    f, fh, xi = synth.fields.workload_case("bumps64")
     f, fh = f.numpy().reshape(-1), fh.numpy().reshape(-1)
     assert_same(gpu_run(f, fh, xi, (64, 64, 64), mode, events="original"),
                 oracle_run(f, fh, xi, (64, 64, 64), events=True), f.size)

@@ -23,7 +23,7 @@ import torch
 
 import oracle
 import synth
-from synth.fields import CONFIGS
+from synth.fields import WORKLOADS
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -48,7 +48,7 @@ def _host_gib():
 def test_bumps512_bit_exact_against_oracle():
     import paper_2604_01397_b300 as ez
 
-    c = CONFIGS[2]
+    c = WORKLOADS["bumps512"]
     dev = torch.device("cuda")
     f, fh, xi = synth.make_case(c["kind"], c["dims"], c["seed"], c["rel"], c["fhat"], n_bumps=c["n_bumps"],
                                 sigma=c["sigma"], device=dev)
@@ -105,7 +105,7 @@ def test_octave1024_fixpoint_properties(rel):
 
     if _host_gib() < 48:
         pytest.skip("needs about 48 GiB of free host memory for the host-side checks")
-    c = CONFIGS[3]
+    c = WORKLOADS["octave1024"]
     dev = torch.device("cuda")
     f, fh, xi = synth.make_case(c["kind"], c["dims"], c["seed"], rel, c["fhat"], device=dev)
     r = ez.correct(f, fh, xi, dims=c["dims"], mode="graph", edits=False)
@@ -131,7 +131,7 @@ def test_bumps512_original_events_fixpoint_properties():
 
     if _host_gib() < 24:
         pytest.skip("needs about 24 GiB of free host memory for the host-side checks")
-    c = CONFIGS[2]
+    c = WORKLOADS["bumps512"]
     dev = torch.device("cuda")
     f, fh, xi = synth.make_case(c["kind"], c["dims"], c["seed"], c["rel"], c["fhat"], n_bumps=c["n_bumps"],
                                 sigma=c["sigma"], device=dev)

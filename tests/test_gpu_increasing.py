@@ -67,7 +67,7 @@ def test_heavy_ties_and_caps():
 def test_workload_64_and_stream():
     import paper_2604_01397_b300 as ez
 
-    f, fh, xi = synth.fields.config_case(1)
+    f, fh, xi = synth.fields.workload_case("bumps64")
     f, fh = f.numpy().reshape(-1), fh.numpy().reshape(-1)
     dims = (64, 64, 64)
     ref = oracle_run(f, fh, xi, dims, increasing=True)
