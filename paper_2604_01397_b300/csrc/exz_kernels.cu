@@ -1477,16 +1477,96 @@ __device__ __forceinline__ unsigned long long block_reserve(uint32_t c, unsigned
 // ascent; an extremum links to itself, settled.  (Following the links inside
 // each tile in shared memory first saves about one jump round on the bumps
 // workload but costs as much as it saves.)
+// Path ends inside a tile: each block takes whole tiles and follows the
+// steepest links of their vertices in shared memory (synchronous pointer
+// jumping, at most log2(TILE_V) rounds, since a path visits a vertex at most
+// once), so that E starts at the first vertex of each path outside its tile,
+// or at the path's extremum (settled); the global rounds then jump between
+// tiles.  Both directions at once.
 __global__ void __launch_bounds__(CTA) k_ev_init(Dev D, uint32_t *E)
 {
-    for_tile_vertices(D, [&](uint32_t, const FieldDesc &F, uint32_t t, uint32_t, uint32_t, uint32_t, bool in) {
-        if (!in) return;
-        const uint64_t a = F.vbase + t;
-        const uint32_t d = D.desc[a];
-        const int rd = (int)((d >> D_DN_SHIFT) & 15u), ru = (int)(d & 15u);
-        E[a] = rd == 7 ? ((uint32_t)a | EV_DONE) : (uint32_t)((int64_t)a + rank_offset(F, rd));
-        E[D.total_v + a] = ru == 7 ? ((uint32_t)a | EV_DONE) : (uint32_t)((int64_t)a + rank_offset(F, ru));
-    });
+    constexpr int PER = TILE_V / CTA;
+    constexpr uint16_t OUT = 0xFFFFu;  // the link leaves the tile (or the vertex is settled)
+    static_assert(TILE_V % CTA == 0 && TILE_V < OUT, "tile-local path slots");
+    __shared__ uint16_t s_loc[2][TILE_V];  // next vertex inside the tile, or OUT
+    __shared__ uint32_t s_end[2][TILE_V];  // with OUT: the arena value E takes
+    for (uint32_t tile = blockIdx.x; tile < D.total_tiles; tile += gridDim.x) {
+        const FieldDesc &F = D.fields[field_of_tile(D, tile)];
+        const uint32_t lt = tile - (uint32_t)F.tbase;
+        const uint32_t rest = fdiv(lt, F.div_tnx), tx = lt - rest * F.tnx;
+        const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * F.tny;
+        uint64_t av[PER];
+        bool open = false;
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int j = threadIdx.x + q * CTA;
+            const int lx = j % TX, ly = (j / TX) % TY, lz = j / (TX * TY);
+            const uint32_t x = tx * TX + (uint32_t)lx, y = ty * TY + (uint32_t)ly, z = tz * TZ + (uint32_t)lz;
+            av[q] = ~0ull;
+            if (x >= F.nx || y >= F.ny || z >= F.nz) {  // no vertex here: no link points to it
+                s_loc[0][j] = s_loc[1][j] = OUT;
+                s_end[0][j] = s_end[1][j] = 0;
+                continue;
+            }
+            const uint64_t a = F.vbase + ((uint64_t)z * F.ny + y) * F.nx + x;
+            av[q] = a;
+            const uint32_t d = D.desc[a];
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const int r = side ? (int)(d & 15u) : (int)((d >> D_DN_SHIFT) & 15u);
+                if (r == 7) {  // an extremum of this direction: its own end
+                    s_loc[side][j] = OUT;
+                    s_end[side][j] = (uint32_t)a | EV_DONE;
+                    continue;
+                }
+                const int nx = lx + rdx(r), ny = ly + rdy(r), nz = lz + rdz(r);
+                if (nx >= 0 && nx < TX && ny >= 0 && ny < TY && nz >= 0 && nz < TZ) {
+                    s_loc[side][j] = (uint16_t)(nx + TX * (ny + TY * nz));
+                    s_end[side][j] = 0;
+                    open = true;
+                } else {
+                    s_loc[side][j] = OUT;
+                    s_end[side][j] = (uint32_t)((int64_t)a + rank_offset(F, r));
+                }
+            }
+        }
+        // jump until every path has left the tile or ended (block-uniform test;
+        // 10 rounds reach 2^10 > TILE_V steps, the bound only guards a corrupt descriptor)
+        for (int round = 0; round < 12 && __syncthreads_or(open); round++) {
+            uint16_t nl[PER][2];
+            uint32_t ne[PER][2];
+            open = false;
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                const int j = threadIdx.x + q * CTA;
+#pragma unroll
+                for (int side = 0; side < 2; side++) {
+                    const uint16_t l = s_loc[side][j];
+                    nl[q][side] = l == OUT ? OUT : s_loc[side][l];
+                    ne[q][side] = l == OUT ? s_end[side][j] : s_end[side][l];
+                    open |= nl[q][side] != OUT;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                const int j = threadIdx.x + q * CTA;
+#pragma unroll
+                for (int side = 0; side < 2; side++) {
+                    s_loc[side][j] = nl[q][side];
+                    s_end[side][j] = ne[q][side];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (av[q] == ~0ull) continue;
+            const int j = threadIdx.x + q * CTA;
+            E[av[q]] = s_end[0][j];
+            E[D.total_v + av[q]] = s_end[1][j];
+        }
+        __syncthreads();  // the next tile reuses the shared arrays
+    }
 }
 
 // One jump round in both directions; sets ls->ev_changed if an entry changed.
