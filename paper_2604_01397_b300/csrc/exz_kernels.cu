@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(RADIX) k_sort_hist(Dev D, int pass, const uint
 
 // One LSD pass, tile by tile: each block owns a contiguous chunk of the input
 // (the same chunk its histogram counted) and takes it SORT_TILE elements at a
-// time.  Warp w ranks the w-th 256-element slice of the tile by itself, 32
+// time.  Warp w ranks the w-th 384-element slice of the tile by itself, 32
 // elements per round (warp match for the rank within a round, a running count
 // per digit in the warp's shared counters); then the warps' counts are
 // prefixed per digit and the digits' tile counts scanned, which places every
@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(RADIX) k_sort_hist(Dev D, int pass, const uint
 // last != 0: this is the final pass; also record each critical point's rank
 // within its field (cp_rank), which the frontier uses to find its CP pairs,
 // and its value in sorted order (gs).
-constexpr int SORT_ROUNDS = 8;
+constexpr int SORT_ROUNDS = 12;
 constexpr int SORT_TILE = RADIX * SORT_ROUNDS;
 
 __global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const uint32_t *ksrc,
