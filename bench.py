@@ -207,6 +207,25 @@ def ncu_traffic(kernel: str, workload: str):
     return None
 
 
+def ncu_limiter(kernel: str):
+    """Issue, ALU-pipe and DRAM utilisation of `kernel` from the committed full
+    ncu capture, if it was taken on the current kernel source (null otherwise):
+    the counters that show what bounds it when DRAM does not."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        m = re.match(r"\|\s*(\S+)\s*\|\s*(\S+)\s*\|\s*(\S+)\s*\|\s*([0-9.]+)\s*\|\s*([0-9.]+)\s*\|\s*([0-9.]+)\s*\|\s*$",
+                     line)
+        if m and m.group(1) == kernel and m.group(3) == src:
+            return {"issue_active_pct": float(m.group(4)), "alu_pipe_pct": float(m.group(5)),
+                    "dram_pct": float(m.group(6)),
+                    "source": f"ncu --set full, one dense launch, workload {m.group(2)} "
+                              "(profiles/k_stencil_check_bumps256.md)"}
+    return None
+
+
 def oracle_sample(f, fh, xi, side: int, events: str = "reformulated"):
     """Run the oracle (plain mode, as it stands) on the side^3 corner crop."""
     import oracle
@@ -353,6 +372,7 @@ def run_ours(a):
     roof = {"bound": "hbm", "kernel": "k_stencil<CHECK_LIST> (frontier vertex check)", "achieved": achieved,
             "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": ncu_traffic("k_stencil<CHECK_LIST>", c["name"]), "algorithmic_bytes": alg_bytes,
+            "limiter": ncu_limiter("k_stencil<CHECK_LIST>"),
             "launch_ms": launch_ms, "launches": int(chk_launches),
             "measured": f"{a.steps} frontier-mode corrections, CUDA events around each launch",
             "loop_kernel_ms_per_correction": {k: v / a.steps for k, v in ker_ms.items()}}
