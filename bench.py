@@ -243,11 +243,16 @@ def omp_threads() -> int:
 
 
 def choose_side(f, fh, xi, budget_s: float, lo=32, hi=256, events: str = "reformulated"):
-    """Pick a crop side whose oracle run takes about budget_s (calibrated on a small crop)."""
-    t, _ = oracle_sample(f, fh, xi, lo, events)
-    per = t / lo ** 3
-    side = int((budget_s / max(per, 1e-12)) ** (1 / 3))
-    return max(lo, min(hi, side, min(f.shape)))
+    """Pick a crop side whose oracle run takes about budget_s: calibrated on a
+    small crop, then once more on the first estimate (the cost per vertex of a
+    small crop overstates that of a large one: the host threads are not full)."""
+    cap = min(hi, min(f.shape))
+    side, t = lo, oracle_sample(f, fh, xi, lo, events)[0]
+    new = max(lo, min(cap, int(side * (budget_s / max(t, 1e-9)) ** (1 / 3))))
+    if new <= side:
+        return side
+    side, t = new, oracle_sample(f, fh, xi, new, events)[0]
+    return max(lo, min(cap, int(side * (budget_s / max(t, 1e-9)) ** (1 / 3))))
 
 
 # ---------------------------------------------------------------- reference arm

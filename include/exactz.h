@@ -343,8 +343,8 @@ typedef struct {
     uint64_t budget_bytes; /* device memory for the arena (>= 64 MiB) */
     uint32_t max_fields;   /* resident fields at most (1..4096) */
     uint32_t reserved;
-    exactz_opts opts;      /* N, max_iters, want_edit_list for every request (N = 0: defaults); mode ignored;
-                              events and direction must be 0 */
+    exactz_opts opts;      /* N, max_iters, want_edit_list and direction (decreasing or increasing
+                              edits) for every request (N = 0: defaults); mode ignored; events must be 0 */
 } exactz_server_config;
 
 typedef struct {

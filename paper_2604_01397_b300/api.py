@@ -446,11 +446,11 @@ class Server:
     """
 
     def __init__(self, budget_bytes: int, max_fields: int = 64, N_steps: int = 5,
-                 max_iters: int = 1_000_000, edits: bool = True):
+                 max_iters: int = 1_000_000, edits: bool = True, direction: str = "decreasing"):
         cfg = N.ServerConfig()
         cfg.budget_bytes = int(budget_bytes)
         cfg.max_fields = int(max_fields)
-        cfg.opts = make_opts(N_steps, "frontier", max_iters, edits)
+        cfg.opts = make_opts(N_steps, "frontier", max_iters, edits, direction=direction)
         self._h = N.lib().exactz_server_create(ctypes.byref(cfg))
         if not self._h:
             raise ExactzError(N.EXACTZ_ENOMEM, "exactz_server_create")

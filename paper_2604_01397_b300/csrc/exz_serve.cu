@@ -138,6 +138,7 @@ struct exactz_server {
     uint32_t *h_retire = nullptr;
     cudaStream_t cs = nullptr, xs = nullptr;  // compute, copy
     cudaEvent_t in_ev = nullptr;               // inputs landed (re-recorded per admission)
+    cudaEvent_t refl_ev = nullptr;             // increasing edits: the room's g is free for the next input
 
     // guarded by mu
     Arena av, aw, at, ac, ae;
@@ -167,6 +168,7 @@ void free_server(exactz_server *S)
     if (S->cs) cudaStreamDestroy(S->cs);
     if (S->xs) cudaStreamDestroy(S->xs);
     if (S->in_ev) cudaEventDestroy(S->in_ev);
+    if (S->refl_ev) cudaEventDestroy(S->refl_ev);
     for (void *p : S->allocs) cudaFree(p);
     if (S->h_fst) cudaFreeHost(S->h_fst);
     if (S->h_fd) cudaFreeHost(S->h_fd);
@@ -340,13 +342,32 @@ int start_request(exactz_server *S, const Dev &D, Req *r)
     F.edits_cap = r->ne;
     F.pin_tiles = S->pin_tile_arena + r->t0;
     F.pin_pairs = S->pin_pair_arena + 2 * r->c0;
+    const bool inc = S->opts.direction == EXACTZ_EDITS_INCREASING;
+    F.mirror = inc ? 1u : 0u;  // increasing edits: the room holds the reflection of -f, -f_hat
     // tile loads by TMA where the room's arrays can be mapped (else cp.async)
     CUtensorMap *m = S->h_tmaps + (uint64_t)TMAPS * slot;
     F.tma = make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) && make_map(m + 2, F.g, F, true) &&
             make_map(m + 3, S->desc + r->v0, F, false);
     S->h_fd[slot] = F;
-    SK(cudaMemcpyAsync(S->f + r->v0, r->f, r->n * 4, cudaMemcpyHostToDevice, S->xs));
-    SK(cudaMemcpyAsync(S->fhat + r->v0, r->fhat, r->n * 4, cudaMemcpyHostToDevice, S->xs));
+    if (!inc) {
+        SK(cudaMemcpyAsync(S->f + r->v0, r->f, r->n * 4, cudaMemcpyHostToDevice, S->xs));
+        SK(cudaMemcpyAsync(S->fhat + r->v0, r->fhat, r->n * 4, cudaMemcpyHostToDevice, S->xs));
+    } else {
+        // each input lands in the room's g (free until the set-up) and is
+        // reflected from there into f or f_hat, v -> n-1-v with negation
+        float *stage = S->g + r->v0;
+        SK(cudaMemcpyAsync(stage, r->f, r->n * 4, cudaMemcpyHostToDevice, S->xs));
+        SK(cudaEventRecord(S->in_ev, S->xs));
+        SK(cudaStreamWaitEvent(S->cs, S->in_ev, 0));
+        launch_reflect_in(stage, S->f + r->v0, r->n, S->cs);
+        SK(cudaEventRecord(S->refl_ev, S->cs));
+        SK(cudaStreamWaitEvent(S->xs, S->refl_ev, 0));
+        SK(cudaMemcpyAsync(stage, r->fhat, r->n * 4, cudaMemcpyHostToDevice, S->xs));
+        SK(cudaEventRecord(S->in_ev, S->xs));
+        SK(cudaStreamWaitEvent(S->cs, S->in_ev, 0));
+        launch_reflect_in(stage, S->fhat + r->v0, r->n, S->cs);
+        S->launches += 2;
+    }
     SK(cudaEventRecord(S->in_ev, S->xs));
     // meanwhile clear the room on the compute stream (it may hold an earlier field's state)
     SK(cudaMemcpyAsync(S->d_fields + slot, &S->h_fd[slot], sizeof(FieldDesc), cudaMemcpyHostToDevice, S->cs));
@@ -392,6 +413,10 @@ int retire(exactz_server *S, const Dev &D, const std::vector<Req *> &fin)
         const FieldSet one{S->d_retire + i, 1, r->v0 / VBLOCK, r->nv / VBLOCK, r->slot, r->slot + 1};
         launch_edit_list(D, one, r->ne ? 1 : 0, S->cs);
         S->launches += r->ne ? 3 : 1;
+        if (S->opts.direction == EXACTZ_EDITS_INCREASING) {  // g back in the caller's coordinates and sign
+            launch_reflect_out(S->g + r->v0, S->desc + r->v0, r->n, S->cs);
+            S->launches += 1;
+        }
     }
     S->launches += 4;  // pinned checks, pinned pairs, residual count, status
     SK(cudaGetLastError());
@@ -502,7 +527,7 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
     exactz_opts o;
     exactz_default_opts(&o);
     if (cfg->opts.N) o = cfg->opts;
-    if (o.N < 1 || o.N > 254 || o.events != EXACTZ_EVENTS_REFORMULATED || o.direction != EXACTZ_EDITS_DECREASING)
+    if (o.N < 1 || o.N > 254 || o.events != EXACTZ_EVENTS_REFORMULATED || o.direction > EXACTZ_EDITS_INCREASING)
         return nullptr;
     exactz_server *S = new (std::nothrow) exactz_server();
     if (!S) return nullptr;
@@ -540,7 +565,8 @@ exactz_server *exactz_server_create(const exactz_server_config *cfg)
          cudaMallocHost(&S->h_retire, 4ull * S->slots) == cudaSuccess &&
          cudaStreamCreateWithFlags(&S->cs, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&S->xs, cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&S->in_ev, cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&S->in_ev, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&S->refl_ev, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         // every slot starts out finished; the loop state and the bitmaps start clear
         std::vector<FieldState> idle(S->slots);

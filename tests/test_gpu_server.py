@@ -1,7 +1,8 @@
 """The request server (continuous batching): every result is bit-identical to
 the oracle's and to the same request run alone, whatever else is resident;
 admission respects the slot count and the arena budget; oversized requests are
-refused; an invalid request fails alone without disturbing the others."""
+refused; an invalid request fails alone without disturbing the others; a
+server for increasing edits matches the oracle's increasing mode."""
 import threading
 
 import numpy as np
@@ -91,6 +92,25 @@ def test_server_equals_frontier_entry_point():
         got = [_wait(s, t) for t in tickets]
     for (dims, f, fh, xi), m in zip(fields, got):
         r = ez.correct(f.cuda(), fh.cuda(), xi, dims=dims, N_steps=3, mode="frontier", max_iters=4)
+        r = {**r, "g": r["g"].cpu(), "edits": {k: v.cpu() for k, v in r["edits"].items()}}
+        _same(r, m)
+
+
+def test_increasing_edits_equal_oracle():
+    # a server created for increasing edits reflects each room's inputs at
+    # admission and its g at retirement; results equal the oracle's native
+    # increasing mode and the workspace's, whatever else is resident
+    import paper_2604_01397_b300 as ez
+
+    fields = _fields(MIX[:6])
+    with ez.Server(budget_bytes=1 << 30, max_fields=4, direction="increasing") as s:
+        tickets = [s.submit(f, fh, xi, dims=dims) for dims, f, fh, xi in fields]
+        got = [_wait(s, t) for t in tickets]
+        assert s.stats()["error"] == 0
+    for (dims, f, fh, xi), m in zip(fields, got):
+        ref = oracle_run(f.numpy(), fh.numpy(), xi, dims, increasing=True)
+        assert_same(_as_oracle_dict(m), ref, f.numel())
+        r = ez.correct(f.cuda(), fh.cuda(), xi, dims=dims, mode="frontier", direction="increasing")
         r = {**r, "g": r["g"].cpu(), "edits": {k: v.cpu() for k, v in r["edits"].items()}}
         _same(r, m)
 
