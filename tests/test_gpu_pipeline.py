@@ -124,3 +124,17 @@ def test_no_edit_lists_and_invalid_input():
         ws.correct_sequence([_pinned(fields[0][0][:-1].copy())], [_pinned(fields[0][1])], [fields[0][2]], gs[:1],
                             dims=DIMS)
     ws.close()
+
+
+def test_fields_larger_than_the_workspace_are_refused():
+    import paper_2604_01397_b300 as ez
+
+    fields = _fields([71, 72])
+    n = fields[0][0].size
+    gs, es = _bufs(n, 2)
+    ws = ez.Workspace([(8, 8, 8)])  # planned for 512 vertices
+    with pytest.raises(ez.ExactzError) as e:
+        ws.correct_sequence([_pinned(f) for f, _, _ in fields], [_pinned(h) for _, h, _ in fields],
+                            [xi for *_, xi in fields], gs, es, dims=DIMS)
+    assert e.value.rc == -7  # EXACTZ_ESIZE, before any kernel of the first field
+    ws.close()
