@@ -318,8 +318,9 @@ int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, uin
  * A GRAPH mode request runs the same passes as FRONTIER driven from the host
  * (identical results); opts->profile is ignored.  EXACTZ_EVENTS_ORIGINAL
  * needs set-up storage sized by the field's extremum graph and is refused
- * (EXACTZ_EINVAL), as are increasing edits.  Returns EXACTZ_ESIZE for larger
- * fields, otherwise as exactz_correct. */
+ * (EXACTZ_EINVAL); increasing edits are offered (their reflected fields live in
+ * the same scratch).  Returns EXACTZ_ESIZE for larger fields, otherwise as
+ * exactz_correct. */
 int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, float xi,
                            const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
                            uint64_t edits_cap, exactz_result *res, void *cuda_stream);

@@ -405,7 +405,7 @@ def cp_order(f: torch.Tensor, dims=None, stream=None) -> torch.Tensor:
 def correct_noalloc(f: torch.Tensor, fhat: torch.Tensor, xi: float, g_out: torch.Tensor,
                     edit_buf: Optional[torch.Tensor] = None, dims=None, N_steps: int = 5,
                     mode: str = "frontier", max_iters: int = 1_000_000, stream=None,
-                    raise_on_error: bool = True) -> dict:
+                    raise_on_error: bool = True, direction: str = "decreasing") -> dict:
     """exactz_correct_noalloc: the correction for fields of at most 2^18 vertices
     using only the library's fixed device scratch, for callers that must not
     allocate device memory during the call (e.g. while a stream is being
@@ -418,7 +418,7 @@ def correct_noalloc(f: torch.Tensor, fhat: torch.Tensor, xi: float, g_out: torch
     d = dims_of(f, dims)
     cap = 0 if edit_buf is None else edit_buf.shape[0]
     res = N.Result()
-    o = make_opts(N_steps, mode, max_iters, edit_buf is not None)
+    o = make_opts(N_steps, mode, max_iters, edit_buf is not None, direction=direction)
     rc = N.lib().exactz_correct_noalloc(
         ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(fhat.data_ptr()), N.Dims(*d),
         ctypes.c_float(float(np.float32(xi))), ctypes.byref(o), ctypes.c_void_p(g_out.data_ptr()),

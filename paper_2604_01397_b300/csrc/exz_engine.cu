@@ -1368,8 +1368,10 @@ bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, i
               c.take(ws->pin_pair_arena, 2 * C) && c.take(ws->fids, L.nfields) && c.take(ws->cp_key[0], C) &&
               c.take(ws->cp_key[1], C) &&
               c.take(ws->cp_ent[0], C) && c.take(ws->cp_ent[1], C) && c.take(ws->blk, nblk) &&
-              c.take(ws->blk_off, nblk) && c.take(ws->hist, 256ull * ws->sort_blocks);
+              c.take(ws->blk_off, nblk) && c.take(ws->hist, 256ull * ws->sort_blocks) &&
+              c.take(ws->refl, 2 * V);  // increasing edits: the reflected -f, -f_hat
     if (!ok) return false;
+    ws->ev_cap[8] = 2 * V;  // run() finds the reflection storage in place (never grows it)
     ws->cap_nf = L.nfields;
     ws->cap_v = V;
     ws->cap_w = W;
@@ -1388,8 +1390,9 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     int rc = check_device();
     if (rc) return rc;
     if (!f || !fhat || !g_out || !res) return EXACTZ_EINVAL;
-    // the event lists and the reflected fields need allocated storage
-    if (opts && (opts->events != EXACTZ_EVENTS_REFORMULATED || opts->direction != EXACTZ_EDITS_DECREASING))
+    // the event lists need storage sized after the sort (the reflected fields
+    // of increasing edits fit in the fixed scratch)
+    if (opts && (opts->events != EXACTZ_EVENTS_REFORMULATED || opts->direction > EXACTZ_EDITS_INCREASING))
         return EXACTZ_EINVAL;
     Layout L;
     if ((rc = make_layout(1, &d, L)) != EXACTZ_OK) return rc;

@@ -72,6 +72,27 @@ def test_two_calls_in_a_row_match_the_allocating_entry_point():
         _same(ez.correct_noalloc(f, fh, xi, torch.empty_like(f), buf), ref)
 
 
+def test_increasing_edits_match_the_allocating_entry_point():
+    # the reflected -f, -f_hat live in the fixed scratch: still nothing allocated
+    import paper_2604_01397_b300 as ez
+
+    dims = (48, 40, 33)
+    f, fh, xi = synth.make_case("bumps", dims, 8, 1e-2, "uniform", sigma=(2.0, 5.0))
+    f, fh = _dev(f.numpy(), dims), _dev(fh.numpy(), dims)
+    n = f.numel()
+    ref = ez.correct(f, fh, xi, mode="graph", edits_cap=n, direction="increasing")
+    g = torch.empty_like(f)
+    buf = torch.empty((n, 16), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    got = ez.correct_noalloc(f, fh, xi, g, buf, direction="increasing")
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    _same(got, ref)
+    # and a decreasing call right after it still matches
+    _same(ez.correct_noalloc(f, fh, xi, torch.empty_like(f), buf), ez.correct(f, fh, xi, edits_cap=n))
+
+
 def test_fields_beyond_the_limit_are_rejected():
     import paper_2604_01397_b300 as ez
 
