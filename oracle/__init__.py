@@ -131,13 +131,16 @@ def cp_order(f, dims=None) -> np.ndarray:
 
 
 def correct(f, fhat, xi: float, dims=None, N: int = 5, max_iters: int = 1 << 30,
-            worklist: bool = False, events: bool = False, increasing: bool = False) -> dict:
+            worklist: bool = False, events: bool = False, increasing: bool = False,
+            edit_list: bool = True) -> dict:
     """Run the correction to its fixpoint.  Returns g, k, iterations, residual,
     status, n_edits, n_lossless and the edit list (ascending index).
     events=True: the saddle-ordering and original event constraints replace the
     reformulated ones (every rule is evaluated in full each pass).
     increasing=True: monotone increasing edits (every rule raises the vertex
-    that must be higher; g <- fl(g + Delta) up to the lossless bound fl(f + xi))."""
+    that must be higher; g <- fl(g + Delta) up to the lossless bound fl(f + xi)).
+    edit_list=False: leave out the edit_* arrays (the caller derives the edits
+    from k and g; saves host memory on very large fields)."""
     f = _f32(f)
     fhat = _f32(fhat)
     nx, ny, nz = _dims_of(f, dims)
@@ -159,11 +162,13 @@ def correct(f, fhat, xi: float, dims=None, N: int = 5, max_iters: int = 1 << 30,
                                   int(bool(worklist)), _p(g), _p(k), _p(info))
     if rc != 0:
         raise ValueError(f"oracle_correct failed: {rc}")
-    idx = np.nonzero(k)[0]
-    return dict(g=g, k=k, iterations=int(info[0]), residual=int(info[1]),
-                status=int(info[2]), n_edits=int(info[3]), n_lossless=int(info[4]),
-                edit_idx=idx.astype(np.int64), edit_k=k[idx].copy(),
-                edit_lossless=(k[idx] == N + 1), edit_value=g[idx].copy())
+    out = dict(g=g, k=k, iterations=int(info[0]), residual=int(info[1]),
+               status=int(info[2]), n_edits=int(info[3]), n_lossless=int(info[4]))
+    if edit_list:
+        idx = np.nonzero(k)[0]
+        out.update(edit_idx=idx.astype(np.int64), edit_k=k[idx].copy(),
+                   edit_lossless=(k[idx] == N + 1), edit_value=g[idx].copy())
+    return out
 
 
 def correct_rc(f, fhat, xi: float, dims=None, N: int = 5) -> int:

@@ -13,6 +13,7 @@ from .fields import (  # noqa: F401
     fhat_uniform,
     clamp_into_bound,
     make_case,
+    make_cases_cpu,
     batched_specs,
     serving_requests,
     WORKLOADS,

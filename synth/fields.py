@@ -24,8 +24,12 @@ volumes, which are not available here):
 Random draws: scalar parameters (centres, sigmas, amplitudes, dims, arrival
 times) come from ``numpy.random.default_rng(seed)``; per-vertex noise comes
 from a ``torch.Generator`` seeded with the same seed on the generating
-device, so a field made on a GPU and one made on the CPU from the same seed
-differ.  Every comparison therefore feeds the *same bytes* to both sides.
+device (the multi-octave noise on the CPU: numpy's generator and FFT, whose
+results do not depend on the host's thread count), so a field made on a GPU
+and one made on the CPU from the same seed differ.  Every comparison
+therefore feeds the *same bytes* to both sides; CPU-made fields are the same
+on every host with this software (their SHA-256 is checked where stored
+digests are compared).
 """
 from __future__ import annotations
 
@@ -94,27 +98,60 @@ def gaussian_bumps(dims: Dims, n_bumps: int, sigma_range: Sequence[float],
 
 def multi_octave(dims: Dims, seed: int, sigmas=(2.0, 8.0, 32.0),
                  weights=(1.0, 0.5, 0.25), device="cpu") -> torch.Tensor:
-    """Weighted sum of periodic-Gaussian-filtered white-noise octaves (float32)."""
+    """Weighted sum of periodic-Gaussian-filtered white-noise octaves (float32).
+
+    On the CPU the noise comes from ``numpy.random.default_rng(seed)`` and the
+    filtering from numpy's FFT (single-threaded, no run-time CPU dispatch), so
+    the same seed gives the same bytes on every host with this software; on a
+    GPU the noise and the FFTs are torch's on that device (other bytes)."""
     nx, ny, nz = (int(d) for d in dims)
+    if torch.device(device).type == "cpu":
+        return _multi_octave_numpy((nx, ny, nz), seed, sigmas, weights)
     gen = _gen(device, seed)
     kz = torch.fft.fftfreq(nz, dtype=torch.float64, device=device)
     ky = torch.fft.fftfreq(ny, dtype=torch.float64, device=device)
     kx = torch.fft.rfftfreq(nx, dtype=torch.float64, device=device)
-    k2 = (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
     total = torch.zeros((nz, ny, nx), dtype=torch.float64, device=device)
     for s, w in zip(sigmas, weights):
         noise = torch.randn((nz, ny, nx), dtype=torch.float64, device=device, generator=gen)
         spec = torch.fft.rfftn(noise)
         del noise
-        spec *= torch.exp(-2.0 * math.pi ** 2 * float(s) ** 2 * k2)
+        c = -2.0 * math.pi ** 2 * float(s) ** 2
+        spec *= torch.exp(c * kz * kz)[:, None, None]
+        spec *= torch.exp(c * ky * ky)[None, :, None]
+        spec *= torch.exp(c * kx * kx)[None, None, :]
         sm = torch.fft.irfftn(spec, s=(nz, ny, nx))
         del spec
         sd = float(sm.std())
-        if sd > 0:
-            sm /= sd
-        total += float(w) * sm
+        sm *= float(w) / sd if sd > 0 else float(w)
+        total += sm
         del sm
     return total.to(torch.float32)
+
+
+def _multi_octave_numpy(dims: Dims, seed: int, sigmas, weights) -> torch.Tensor:
+    """The CPU form of ``multi_octave`` (numpy RNG and FFT)."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    kz = np.fft.fftfreq(nz)
+    ky = np.fft.fftfreq(ny)
+    kx = np.fft.rfftfreq(nx)
+    total = np.zeros((nz, ny, nx), dtype=np.float64)
+    for s, w in zip(sigmas, weights):
+        noise = rng.standard_normal((nz, ny, nx))
+        spec = np.fft.rfftn(noise, axes=(0, 1, 2))
+        del noise
+        c = -2.0 * math.pi ** 2 * float(s) ** 2
+        spec *= np.exp(c * kz * kz)[:, None, None]
+        spec *= np.exp(c * ky * ky)[None, :, None]
+        spec *= np.exp(c * kx * kx)[None, None, :]
+        sm = np.fft.irfftn(spec, s=(nz, ny, nx), axes=(0, 1, 2))
+        del spec
+        sd = float(sm.std())
+        sm *= float(w) / sd if sd > 0 else float(w)
+        total += sm
+        del sm
+    return torch.from_numpy(total.astype(np.float32))
 
 
 def xi_from_relative(f: torch.Tensor, rel: float) -> float:
@@ -167,6 +204,28 @@ def make_case(kind: str, dims: Dims, seed: int, rel: float, fhat: str,
     else:
         raise ValueError(f"unknown f_hat recipe {fhat!r}")
     return f, fh, xi
+
+
+def _make_case_worker(spec: dict):
+    torch.set_num_threads(1)
+    f, fh, xi = make_case(spec["kind"], spec["dims"], spec["seed"], spec["rel"], spec["fhat"],
+                          n_bumps=spec.get("n_bumps"), sigma=spec.get("sigma", (2.0, 8.0)), device="cpu")
+    return f.numpy(), fh.numpy(), xi
+
+
+def make_cases_cpu(specs: Sequence[dict], workers: int = 0):
+    """(f, f_hat, xi) for many specs, made on the CPU with one torch thread per
+    field in a pool of ``workers`` spawned processes (0: one per host core).
+    The bytes equal those of ``make_case(..., device="cpu")`` one by one."""
+    import concurrent.futures
+    import multiprocessing
+    import os
+
+    workers = workers or os.cpu_count() or 1
+    ctx = multiprocessing.get_context("spawn")  # safe after CUDA has been initialised
+    with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+        out = list(ex.map(_make_case_worker, specs, chunksize=1))
+    return [(torch.from_numpy(f), torch.from_numpy(fh), xi) for f, fh, xi in out]
 
 
 def workload_case(name: str, device="cpu", rel: float | None = None):
