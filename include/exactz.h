@@ -214,6 +214,7 @@ typedef struct {
     float loop_kernel_ms[3];
     uint32_t reserved;
     uint64_t loop_passes;
+    uint64_t sum_visits;      /* vertices checked by frontier passes (the dirty vertices of their tiles) */
 } exactz_stats;
 
 int exactz_ws_stats(const exactz_workspace *ws, exactz_stats *out);
@@ -301,26 +302,31 @@ int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, uin
 /* exactz_correct for fields of at most EXACTZ_NOALLOC_MAX_VERTICES vertices
  * (for example 64^3) that allocates no memory: no cudaMalloc, cudaFree,
  * pinned host memory, graph or event objects.  It is meant for callers that
- * cannot allocate device memory in the middle of their work -- code running
- * while a stream is captured into a CUDA graph, applications that reserve the
- * whole device for their own pool, or loops that cannot take the implicit
- * device synchronisation of cudaMalloc/cudaFree.  The caller still passes the
- * inputs and outputs (device pointers, as for exactz_correct).
+ * cannot allocate device memory in the middle of their work: applications
+ * that reserve the whole device memory up front for their own pool
+ * (simulations, in-situ analysis), where a cudaMalloc would fail or take
+ * memory promised elsewhere, and loops that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The caller still passes the inputs
+ * and outputs (device pointers, as for exactz_correct).
+ *
+ * The passes are driven from the host: every pass reads a few bytes of loop
+ * state back and synchronises cuda_stream, and the call returns only after
+ * its work on the stream has finished.
  *
  * Scratch: one EXACTZ_NOALLOC_SCRATCH_BYTES array of static device storage
  * inside this library, held by every GPU that loads the library until the
- * process exits.  The first call on a device looks up that array's device
- * address (a set-up step), so make the first call on each device before any
- * stream capture.  All calls share the array and it keeps the previous call's
- * contents; each call clears what must start at zero.  Calls whose GPU work
- * overlapped would race on the array: within one process they are serialised
- * by a lock, and each call returns only after its stream work has finished.
- * A GRAPH mode request runs the same passes as FRONTIER driven from the host
- * (identical results); opts->profile is ignored.  EXACTZ_EVENTS_ORIGINAL
- * needs set-up storage sized by the field's extremum graph and is refused
- * (EXACTZ_EINVAL); increasing edits are offered (their reflected fields live in
- * the same scratch).  Returns EXACTZ_ESIZE for larger fields, otherwise as
- * exactz_correct. */
+ * process exits (the largest accepted field uses about 19 MiB of it: about
+ * 72 bytes per vertex).  The first call on a device looks up that array's
+ * device address (a set-up step).  All calls share the array and it keeps the
+ * previous call's contents; each call clears what must start at zero.  Calls
+ * whose GPU work overlapped would race on the array: within one process they
+ * are serialised by a lock, which each call releases only after its stream
+ * has drained (on error returns too).
+ * A GRAPH mode request runs the same passes as FRONTIER (identical results);
+ * opts->profile is ignored.  EXACTZ_EVENTS_ORIGINAL needs set-up storage sized
+ * by the field's extremum graph and is refused (EXACTZ_EINVAL); increasing
+ * edits are offered (their reflected fields live in the same scratch).
+ * Returns EXACTZ_ESIZE for larger fields, otherwise as exactz_correct. */
 int exactz_correct_noalloc(const float *f, const float *fhat, exactz_dims d, float xi,
                            const exactz_opts *opts, float *g_out, exactz_edit *edits_out,
                            uint64_t edits_cap, exactz_result *res, void *cuda_stream);
@@ -360,6 +366,7 @@ typedef struct {
     double busy_s;              /* host time spent in passes */
     int32_t error;              /* 0, or the CUDA failure that stopped the server (EXACTZ_ENODEV) */
     int32_t reserved;
+    uint64_t cancelled;         /* requests withdrawn by exactz_server_cancel */
 } exactz_server_info;
 
 /* Returns NULL without a device, on a bad configuration or when the arena
@@ -385,12 +392,28 @@ int exactz_server_poll(exactz_server *s, uint64_t ticket, exactz_result *res, do
 int exactz_server_wait(exactz_server *s, uint64_t ticket, double timeout_s, exactz_result *res,
                        double *latency_s);
 int exactz_server_stats(exactz_server *s, exactz_server_info *out);
+/* Withdraws a request that is still queued (not yet admitted): returns 1, and
+ * the server never reads its inputs or writes its outputs again (the caller
+ * may free them); the ticket is then unknown to poll / wait.  Returns 0 when
+ * the request was already admitted or finished (its result comes as usual)
+ * and EXACTZ_EINVAL for an unknown ticket. */
+int exactz_server_cancel(exactz_server *s, uint64_t ticket);
 /* Finishes every submitted request, then frees the server.  Results not yet
  * taken are discarded (their host buffers hold them). */
 void exactz_server_destroy(exactz_server *s);
 
 /* Library build / device information (host string, static storage). */
 const char *exactz_version(void);
+
+/* ---- testing aid: allocation-failure injection (the paper has no counterpart) ---- */
+
+/* After `skip` more successful device allocations inside this library, the
+ * next `count` fail as if cudaMalloc had run out of memory (no cudaMalloc is
+ * called for them); count = 0 disarms it.  Process-wide; for tests that check
+ * that every call reports EXACTZ_ENOMEM (workspace and server creation return
+ * NULL), frees what it had allocated, and that the library works afterwards.
+ * Always returns EXACTZ_OK. */
+int exactz_debug_fail_allocations(uint64_t skip, uint64_t count);
 
 #ifdef __cplusplus
 }

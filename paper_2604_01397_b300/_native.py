@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("total_critical", ctypes.c_uint64), ("sum_requests", ctypes.c_uint64),
                 ("sum_tiles", ctypes.c_uint64), ("sum_pairs", ctypes.c_uint64),
                 ("stage_ms", ctypes.c_float * 8), ("loop_kernel_ms", ctypes.c_float * 3),
-                ("reserved", ctypes.c_uint32), ("loop_passes", ctypes.c_uint64)]
+                ("reserved", ctypes.c_uint32), ("loop_passes", ctypes.c_uint64),
+                ("sum_visits", ctypes.c_uint64)]
 
 
 class Tuning(ctypes.Structure):
@@ -72,7 +73,7 @@ class ServerInfo(ctypes.Structure):
                 ("resident", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("max_resident", ctypes.c_uint64),
                 ("admitted_vertices", ctypes.c_uint64), ("capacity_vertices", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64), ("busy_s", ctypes.c_double), ("error", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("cancelled", ctypes.c_uint64)]
 
 
 STAGES = ["setup", "compact", "sort", "first_pass", "loop", "finish", "edit_list", "total"]
@@ -84,7 +85,8 @@ EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exa
            "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc",
            "exactz_ws_get_tuning", "exactz_ws_set_tuning", "exactz_ws_autotune", "exactz_server_create",
            "exactz_server_submit", "exactz_server_poll", "exactz_server_wait", "exactz_server_stats",
-           "exactz_server_destroy", "exactz_encode_edits", "exactz_decode_edits"]
+           "exactz_server_destroy", "exactz_server_cancel", "exactz_encode_edits", "exactz_decode_edits",
+           "exactz_debug_fail_allocations"]
 
 _lib = None
 
@@ -157,6 +159,10 @@ def lib():
     L.exactz_server_wait.restype = ctypes.c_int
     L.exactz_server_stats.argtypes = [P, ctypes.POINTER(ServerInfo)]
     L.exactz_server_stats.restype = ctypes.c_int
+    L.exactz_server_cancel.argtypes = [P, ctypes.c_uint64]
+    L.exactz_server_cancel.restype = ctypes.c_int
+    L.exactz_debug_fail_allocations.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    L.exactz_debug_fail_allocations.restype = ctypes.c_int
     L.exactz_server_destroy.argtypes = [P]
     L.exactz_server_destroy.restype = None
     L.exactz_version.argtypes = []

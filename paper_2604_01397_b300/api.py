@@ -118,7 +118,7 @@ class Workspace:
                     sum_tiles=int(st.sum_tiles), sum_pairs=int(st.sum_pairs),
                     stage_ms={k: float(v) for k, v in zip(N.STAGES, st.stage_ms)},
                     loop_kernel_ms={k: float(v) for k, v in zip(("check", "pairs", "apply"), st.loop_kernel_ms)},
-                    loop_passes=int(st.loop_passes))
+                    loop_passes=int(st.loop_passes), sum_visits=int(st.sum_visits))
 
     def tuning(self) -> dict:
         t = N.Tuning()
@@ -407,11 +407,13 @@ def correct_noalloc(f: torch.Tensor, fhat: torch.Tensor, xi: float, g_out: torch
                     mode: str = "frontier", max_iters: int = 1_000_000, stream=None,
                     raise_on_error: bool = True, direction: str = "decreasing") -> dict:
     """exactz_correct_noalloc: the correction for fields of at most 2^18 vertices
-    using only the library's fixed device scratch, for callers that must not
-    allocate device memory during the call (e.g. while a stream is being
-    captured into a CUDA graph, or when an application owns all device memory).
-    The caller provides the output g_out and, optionally, a (cap, 16) uint8
-    edit-record buffer; this function allocates nothing on the device."""
+    using only the library's fixed device scratch, for callers that cannot
+    allocate device memory during the call (an application that has reserved
+    all device memory for its own pool, or a loop that cannot take the device
+    synchronisation of cudaMalloc / cudaFree).  The passes are driven from the
+    host: every pass synchronises the stream.  The caller provides the output
+    g_out and, optionally, a (cap, 16) uint8 edit-record buffer; this function
+    allocates nothing on the device."""
     _check(f, "f")
     _check(fhat, "fhat")
     _check(g_out, "g_out")
@@ -514,6 +516,16 @@ class Server:
         if rc < 0:
             raise ExactzError(rc, "exactz_server_wait")
         return self._finish(ticket, res, lat, decode) if rc == 1 else None
+
+    def cancel(self, ticket: int) -> bool:
+        """Withdraw a request that is still queued (True); False when it was
+        already admitted or finished (its result comes as usual)."""
+        rc = N.lib().exactz_server_cancel(self._h, int(ticket))
+        if rc < 0:
+            raise ExactzError(rc, "exactz_server_cancel")
+        if rc == 1:
+            self._live.pop(int(ticket), None)
+        return rc == 1
 
     def stats(self) -> dict:
         st = N.ServerInfo()

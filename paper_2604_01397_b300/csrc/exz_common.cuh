@@ -155,6 +155,7 @@ struct LoopState {
     unsigned long long sum_requests;  // requests applied or skipped, over all passes
     unsigned long long sum_tiles;     // tiles checked by frontier passes
     unsigned long long sum_pairs;     // CP pairs checked by frontier passes
+    unsigned long long sum_visits;    // vertices checked by frontier passes
     unsigned long long ev_cursor[3];  // event-list set-up: minima and maxima list ends, saddle-list end
     uint32_t any_active;
     uint32_t pass;

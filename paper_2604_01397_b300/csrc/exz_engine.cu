@@ -13,12 +13,14 @@
 //   finish     pinned-vertex residual check, status, edit-list compaction.
 // All three forms compute identical results (the frontier only skips checks
 // whose requests would target pinned vertices; see the oracle's notes).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -125,6 +127,18 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
     return EXACTZ_OK;
 }
 
+// Key of a layout (the fields' dims in order).  A workspace remembers the key
+// of its last run: padding words and vertices are cleared only when it changes.
+uint64_t layout_key(uint32_t nf, const exactz_dims *d)
+{
+    uint64_t h = 1469598103934665603ull ^ nf;
+    for (uint32_t i = 0; i < nf; i++) {
+        const uint64_t v[3] = {d[i].nx, d[i].ny, d[i].nz};
+        for (uint64_t x : v) h = (h ^ x) * 1099511628211ull;
+    }
+    return h;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- workspace
@@ -195,6 +209,11 @@ struct exactz_workspace {
     uint8_t *ev_tdone = nullptr;                 // per tile: every path end found
     float *refl = nullptr;                       // increasing edits: the reflected -f and -f_hat
     uint64_t ev_cap[9] = {};  // E, start, cnt, list, radj, room, room_off, tdone, refl (elements)
+    // set by the allocation-free entry point: every buffer is carved from its
+    // fixed scratch, and a request to grow one fails with EXACTZ_ENOMEM
+    // instead of allocating; alloc_refused counts such requests
+    bool no_alloc = false;
+    uint64_t alloc_refused = 0;
 
     std::mutex mu;
 };
@@ -204,9 +223,13 @@ namespace {
 template <class T>
 int dalloc(exactz_workspace *ws, T *&p, uint64_t count)
 {
+    if (ws->no_alloc) {
+        ws->alloc_refused++;
+        return EXACTZ_ENOMEM;
+    }
     if (count == 0) count = 1;
     void *q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    if (dev_malloc(&q, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return EXACTZ_ENOMEM;
     }
@@ -436,22 +459,26 @@ int ensure_graph(exactz_workspace *ws, const Dev &D)
 
 int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
 {
+    if (ws->no_alloc && (V > ws->st_cap_v || E > ws->st_cap_edits)) {
+        ws->alloc_refused++;
+        return EXACTZ_ENOMEM;
+    }
     if (V > ws->st_cap_v) {
         if (ws->st_f) cudaFree(ws->st_f);
         if (ws->st_fhat) cudaFree(ws->st_fhat);
         if (ws->st_g) cudaFree(ws->st_g);
         ws->st_f = ws->st_fhat = ws->st_g = nullptr;
         ws->st_cap_v = 0;
-        CK(cudaMalloc(&ws->st_f, V * 4));
-        CK(cudaMalloc(&ws->st_fhat, V * 4));
-        CK(cudaMalloc(&ws->st_g, V * 4));
+        CK(dev_malloc(&ws->st_f, V * 4));
+        CK(dev_malloc(&ws->st_fhat, V * 4));
+        CK(dev_malloc(&ws->st_g, V * 4));
         ws->st_cap_v = V;
     }
     if (E > ws->st_cap_edits) {
         if (ws->st_edits) cudaFree(ws->st_edits);
         ws->st_edits = nullptr;
         ws->st_cap_edits = 0;
-        CK(cudaMalloc(&ws->st_edits, E * sizeof(EditRec)));
+        CK(dev_malloc(&ws->st_edits, E * sizeof(EditRec)));
         ws->st_cap_edits = E;
     }
     return EXACTZ_OK;
@@ -461,6 +488,10 @@ int grow_staging(exactz_workspace *ws, uint64_t V, uint64_t E)
 // plus the copy streams and their events (created once).
 int grow_sequence(exactz_workspace *ws, uint64_t V, uint64_t E)
 {
+    if (ws->no_alloc) {
+        ws->alloc_refused++;
+        return EXACTZ_ENOMEM;
+    }
     if (!ws->sq_in) {
         CK(cudaStreamCreateWithFlags(&ws->sq_in, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&ws->sq_out, cudaStreamNonBlocking));
@@ -479,9 +510,9 @@ int grow_sequence(exactz_workspace *ws, uint64_t V, uint64_t E)
         }
         ws->sq_cap_v = 0;
         for (int b = 0; b < 2; b++) {
-            CK(cudaMalloc(&ws->sq_f[b], V * 4));
-            CK(cudaMalloc(&ws->sq_fhat[b], V * 4));
-            CK(cudaMalloc(&ws->sq_g[b], V * 4));
+            CK(dev_malloc(&ws->sq_f[b], V * 4));
+            CK(dev_malloc(&ws->sq_fhat[b], V * 4));
+            CK(dev_malloc(&ws->sq_g[b], V * 4));
         }
         ws->sq_cap_v = V;
     }
@@ -491,7 +522,7 @@ int grow_sequence(exactz_workspace *ws, uint64_t V, uint64_t E)
             ws->sq_edits[b] = nullptr;
         }
         ws->sq_cap_edits = 0;
-        for (int b = 0; b < 2; b++) CK(cudaMalloc(&ws->sq_edits[b], E * sizeof(EditRec)));
+        for (int b = 0; b < 2; b++) CK(dev_malloc(&ws->sq_edits[b], E * sizeof(EditRec)));
         ws->sq_cap_edits = E;
     }
     return EXACTZ_OK;
@@ -503,11 +534,15 @@ int ev_grow(exactz_workspace *ws, T *&p, int i, uint64_t need)
 {
     if (need == 0) need = 1;
     if (need <= ws->ev_cap[i]) return EXACTZ_OK;
+    if (ws->no_alloc) {
+        ws->alloc_refused++;
+        return EXACTZ_ENOMEM;
+    }
     if (p) cudaFree(p);
     p = nullptr;
     ws->bytes -= ws->ev_cap[i] * sizeof(T);
     ws->ev_cap[i] = 0;
-    CK(cudaMalloc(&p, need * sizeof(T)));
+    CK(dev_malloc(&p, need * sizeof(T)));
     ws->ev_cap[i] = need;
     ws->bytes += need * sizeof(T);
     return EXACTZ_OK;
@@ -650,11 +685,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         }
         CK(cudaMemcpyAsync(ws->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, s));
     }
-    uint64_t hsh = 1469598103934665603ull ^ nf;
-    for (uint32_t i = 0; i < nf; i++) {
-        const uint64_t v[3] = {d[i].nx, d[i].ny, d[i].nz};
-        for (uint64_t x : v) hsh = (hsh ^ x) * 1099511628211ull;
-    }
+    const uint64_t hsh = layout_key(nf, d);
     if (hsh != ws->layout_hash) {
         // a new layout: padding may hold another layout's vertices (edit counts, row bits)
         CK(cudaMemsetAsync(ws->desc, 0, L.total_v * 4, s));
@@ -763,6 +794,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     ws->stats.sum_requests = ws->h_ls->sum_requests;
     ws->stats.sum_tiles = ws->h_ls->sum_tiles;
     ws->stats.sum_pairs = ws->h_ls->sum_pairs;
+    ws->stats.sum_visits = ws->h_ls->sum_visits;
     if (opt.mode == EXACTZ_MODE_GRAPH) launches += 4 * (ws->h_ls->pass > 0 ? ws->h_ls->pass - 1 : 0);
     ws->stats.kernel_launches = launches;
     ws->stats.loop_passes = loop_passes;
@@ -812,6 +844,36 @@ int check_device()
 }
 
 }  // namespace
+
+// Allocation-failure injection (a testing aid): after `skip` more successful
+// allocations, the next `count` fail as out of memory.
+static std::mutex g_fail_mu;
+static uint64_t g_fail_skip = 0, g_fail_left = 0;
+
+cudaError_t exz::dev_malloc_bytes(void **p, size_t bytes)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_fail_mu);
+        if (g_fail_left > 0) {
+            if (g_fail_skip > 0) {
+                g_fail_skip--;
+            } else {
+                g_fail_left--;
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+extern "C" int exactz_debug_fail_allocations(uint64_t skip, uint64_t count)
+{
+    std::lock_guard<std::mutex> lk(g_fail_mu);
+    g_fail_skip = skip;
+    g_fail_left = count;
+    return EXACTZ_OK;
+}
 
 const uint32_t *exz::host_multi_table()
 {
@@ -1035,7 +1097,7 @@ int exactz_ws_autotune(exactz_workspace *ws, uint32_t nfields, const float *cons
     for (uint32_t i = 0; i < nfields && !rc; i++) {
         if (!d) { rc = EXACTZ_EINVAL; break; }
         const uint64_t n = (uint64_t)d[i].nx * d[i].ny * d[i].nz;
-        if (cudaMalloc(&gtmp[i], n * 4) != cudaSuccess) rc = EXACTZ_ENOMEM;
+        if (dev_malloc(&gtmp[i], n * 4) != cudaSuccess) rc = EXACTZ_ENOMEM;
     }
     exactz_opts o;
     exactz_default_opts(&o);
@@ -1164,7 +1226,7 @@ int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     float *scratch = nullptr;
     rc = EXACTZ_OK;
-    if (cudaMalloc(&scratch, L.fd[0].n * 4) != cudaSuccess) rc = EXACTZ_ENOMEM;
+    if (dev_malloc(&scratch, L.fd[0].n * 4) != cudaSuccess) rc = EXACTZ_ENOMEM;
     if (!rc) {
         FieldDesc &F = L.fd[0];
         F.f = f;
@@ -1220,10 +1282,10 @@ struct StreamScratch {
     }
     int alloc(uint64_t nb, cudaStream_t s)
     {
-        CK(cudaMalloc(&blk, 4 * (nb ? nb : 1)));
-        CK(cudaMalloc(&off, 8 * (nb ? nb : 1)));
-        CK(cudaMalloc(&total, 8));
-        CK(cudaMalloc(&bad, sizeof(int)));
+        CK(dev_malloc(&blk, 4 * (nb ? nb : 1)));
+        CK(dev_malloc(&off, 8 * (nb ? nb : 1)));
+        CK(dev_malloc(&total, 8));
+        CK(dev_malloc(&bad, sizeof(int)));
         CK(cudaMemsetAsync(total, 0, 8, s));
         CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
         return EXACTZ_OK;
@@ -1300,29 +1362,81 @@ int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, uin
 // ---------------------------------------------------------------- allocation-free entry point
 // exactz_correct_noalloc: the same correction for small fields, with every
 // device buffer carved out of one fixed array that lives in this library's
-// device image.  It exists for callers that must not allocate device memory
-// during the call: code that runs while a stream is being captured into a
-// CUDA graph (cudaMalloc is not capturable and may synchronise the device),
-// simulations and in-situ pipelines that reserve the whole device memory up
-// front for their own pool, and real-time loops that cannot afford the
-// implicit device synchronisation of cudaMalloc / cudaFree.
+// device image.  It is for callers that cannot allocate device memory in the
+// middle of their work: simulations and in-situ pipelines that reserve the
+// whole device memory up front for their own pool (a cudaMalloc would fail or
+// take memory they have promised elsewhere), and loops that cannot take the
+// implicit device synchronisation of cudaMalloc / cudaFree.  The loop is
+// driven from the host: every pass reads a few bytes of loop state back and
+// synchronises the caller's stream, and the call returns only after its work
+// on the stream has finished.
 //
 // The array is file-scope static device storage: every GPU that loads this
 // library holds EXACTZ_NOALLOC_SCRATCH_BYTES of it until the process exits.
 // In host code the symbol is only a host-side stand-in, so its device address
 // is obtained once per device with cudaGetSymbolAddress (with that device
-// current) on the first call there; that first call should therefore come
-// before any stream capture.  All calls share the array and it keeps the last
-// call's contents, so each call clears what must start at zero.  Two calls
-// whose GPU work overlapped would race on the shared array: calls from one
-// process are serialised by a lock and each returns only after its work on
-// the stream has finished.
+// current) on the first call there.  All calls share the array and it keeps
+// the last call's contents, so each call clears what must start at zero.  Two
+// calls whose GPU work overlapped would race on the shared array: calls from
+// one process are serialised by a lock, and the lock is released only after
+// the call's stream has drained, on error paths too.
 namespace {
 
 constexpr uint64_t kNoallocBytes = EXACTZ_NOALLOC_SCRATCH_BYTES;
+constexpr uint64_t kNoallocMaxV = EXACTZ_NOALLOC_MAX_VERTICES;
+constexpr uint32_t kNoallocSortBlocks = 512;  // at most 2 radix-sort blocks per SM for up to 256 SMs
 constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// The pieces carved from the scratch array, in order, and their byte offsets
+// (each piece starts on 256 bytes) for a layout of V arena vertices, W row
+// words, T tiles, C critical-point slots, nf fields, nblk scan blocks and sb
+// radix-sort blocks.  The roles are the ones ws_alloc gives the same buffers.
+enum NoallocPiece {
+    P_MULTI, P_FIELDS, P_FST, P_LS, P_DESC, P_CPRANK, P_CPWORDS, P_REQW, P_DIRTY, P_GS, P_PAIRBITS,
+    P_APPLY, P_TILEFLAG, P_PINTILE, P_PINBITS, P_PINPAIR, P_FIDS, P_KEY0, P_KEY1, P_ENT0, P_ENT1,
+    P_BLK, P_BLKOFF, P_HIST, P_REFL, P_COUNT
+};
+struct CarvePlan {
+    uint64_t off[P_COUNT];
+    uint64_t used;
+};
+
+constexpr CarvePlan carve_plan(uint64_t V, uint64_t W, uint64_t T, uint64_t C, uint64_t nf, uint64_t nblk,
+                               uint64_t sb)
+{
+    const uint64_t bytes[P_COUNT] = {
+        512 * 4,                       // link-component table
+        nf * sizeof(FieldDesc), nf * sizeof(FieldState), sizeof(LoopState),
+        4 * V, 4 * V,                  // descriptors, CP ranks
+        4 * W, 4 * W, 4 * W,           // CP, request and dirty row words
+        4 * C, 4 * (C / 32 + 1),       // sorted CP values, pair bits
+        T, T, 4 * T, 4 * (T / 32 + 1), // apply / check flags, pinned tiles and their bits
+        8 * C, 4 * nf,                 // pinned pairs, field ids
+        4 * C, 4 * C, 8 * C, 8 * C,    // radix-sort keys and entries (ping-pong)
+        4 * nblk, 8 * nblk, 4 * 256 * sb,  // block counts, offsets, digit histograms
+        8 * V};                        // increasing edits: the reflected -f and -f_hat
+    CarvePlan p{};
+    uint64_t used = 0;
+    for (int i = 0; i < P_COUNT; i++) {
+        const uint64_t off = (used + 255) / 256 * 256;
+        p.off[i] = off;
+        used = off + (bytes[i] ? bytes[i] : 1);
+    }
+    p.used = used;
+    return p;
+}
+
+// The largest field the call accepts fits: a field of n <= kNoallocMaxV
+// vertices has V = round_up(n, VBLOCK) <= kNoallocMaxV arena vertices, at most
+// n row words (a row of nx vertices has ceil(nx / 32) <= nx words), at most n
+// tiles and n critical-point slots (about 72 bytes per vertex in all).
+static_assert(kNoallocMaxV % VBLOCK == 0 && kNoallocMaxV % WBLOCK == 0, "padding of the largest field");
+static_assert(carve_plan(kNoallocMaxV, kNoallocMaxV, kNoallocMaxV, kNoallocMaxV, 1,
+                         kNoallocMaxV / WBLOCK + 1, kNoallocSortBlocks)
+                      .used <= kNoallocBytes,
+              "the largest accepted field must fit the fixed scratch");
 
 struct NoallocDevice {
     bool ready = false;
@@ -1335,51 +1449,62 @@ FieldState g_noalloc_hfst[kNoallocMaxDevices];      // pageable host read-back b
 LoopState g_noalloc_hls[kNoallocMaxDevices];
 std::mutex g_noalloc_mu;
 
-// Bump allocator over the scratch array (256-byte aligned pieces).
-struct Carver {
-    unsigned char *base;
-    uint64_t used, cap;
-    template <class T>
-    bool take(T *&p, uint64_t count)
-    {
-        if (count == 0) count = 1;
-        const uint64_t off = round_up(used, 256);
-        const uint64_t bytes = count * sizeof(T);
-        if (off + bytes > cap) return false;
-        p = reinterpret_cast<T *>(base + off);
-        used = off + bytes;
-        return true;
-    }
-};
-
-// Point every workspace buffer for layout L into the scratch array, in the
-// same roles ws_alloc gives them.  The link table sits first, at a fixed place.
+// Point every workspace buffer for layout L into the scratch array.
 bool noalloc_carve(exactz_workspace *ws, unsigned char *base, const Layout &L, int nsm)
 {
-    Carver c{base, 0, kNoallocBytes};
     const uint64_t V = L.total_v, W = L.total_w, T = L.total_tiles, C = L.total_real;
     const uint64_t nblk = std::max(V / VBLOCK, W / WBLOCK) + 1;
-    ws->sort_blocks = (uint32_t)nsm * 2;
-    bool ok = c.take(ws->d_multi, 512) && c.take(ws->d_fields, L.nfields) && c.take(ws->d_fst, L.nfields) &&
-              c.take(ws->d_ls, 1) && c.take(ws->desc, V) && c.take(ws->cp_rank, V) &&
-              c.take(ws->cpwords, W) && c.take(ws->reqw, W) && c.take(ws->dirty, W) && c.take(ws->gs, C) &&
-              c.take(ws->pairbits, C / 32 + 1) && c.take(ws->apply_flag, T) && c.take(ws->tile_flag, T) &&
-              c.take(ws->pin_tile_arena, T) && c.take(ws->pin_tile_bits, T / 32 + 1) &&
-              c.take(ws->pin_pair_arena, 2 * C) && c.take(ws->fids, L.nfields) && c.take(ws->cp_key[0], C) &&
-              c.take(ws->cp_key[1], C) &&
-              c.take(ws->cp_ent[0], C) && c.take(ws->cp_ent[1], C) && c.take(ws->blk, nblk) &&
-              c.take(ws->blk_off, nblk) && c.take(ws->hist, 256ull * ws->sort_blocks) &&
-              c.take(ws->refl, 2 * V);  // increasing edits: the reflected -f, -f_hat
-    if (!ok) return false;
-    ws->ev_cap[8] = 2 * V;  // run() finds the reflection storage in place (never grows it)
+    ws->sort_blocks = std::min<uint32_t>((uint32_t)nsm * 2, kNoallocSortBlocks);
+    const CarvePlan p = carve_plan(V, W, T, C, L.nfields, nblk, ws->sort_blocks);
+    if (p.used > kNoallocBytes) return false;
+    auto at = [&](auto *&ptr, int piece) {
+        ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(base + p.off[piece]);
+    };
+    at(ws->d_multi, P_MULTI);
+    at(ws->d_fields, P_FIELDS);
+    at(ws->d_fst, P_FST);
+    at(ws->d_ls, P_LS);
+    at(ws->desc, P_DESC);
+    at(ws->cp_rank, P_CPRANK);
+    at(ws->cpwords, P_CPWORDS);
+    at(ws->reqw, P_REQW);
+    at(ws->dirty, P_DIRTY);
+    at(ws->gs, P_GS);
+    at(ws->pairbits, P_PAIRBITS);
+    at(ws->apply_flag, P_APPLY);
+    at(ws->tile_flag, P_TILEFLAG);
+    at(ws->pin_tile_arena, P_PINTILE);
+    at(ws->pin_tile_bits, P_PINBITS);
+    at(ws->pin_pair_arena, P_PINPAIR);
+    at(ws->fids, P_FIDS);
+    at(ws->cp_key[0], P_KEY0);
+    at(ws->cp_key[1], P_KEY1);
+    at(ws->cp_ent[0], P_ENT0);
+    at(ws->cp_ent[1], P_ENT1);
+    at(ws->blk, P_BLK);
+    at(ws->blk_off, P_BLKOFF);
+    at(ws->hist, P_HIST);
+    at(ws->refl, P_REFL);
+    ws->ev_cap[8] = 2 * V;  // run() finds the reflection storage in place
     ws->cap_nf = L.nfields;
     ws->cap_v = V;
     ws->cap_w = W;
     ws->cap_real = C;
     ws->cap_tiles = L.total_tiles;
-    ws->bytes = c.used;
+    ws->bytes = p.used;
+    ws->no_alloc = true;  // any request to grow a buffer fails instead of allocating
     return true;
 }
+
+// Drains the call's stream when the call returns (on every path), before the
+// lock on the shared scratch is released.
+struct StreamDrain {
+    cudaStream_t s;
+    ~StreamDrain()
+    {
+        if (cudaStreamSynchronize(s) != cudaSuccess) cudaGetLastError();
+    }
+};
 
 }  // namespace
 
@@ -1401,6 +1526,7 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return EXACTZ_ENODEV;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    const StreamDrain drain{s};  // destroyed first: the stream drains before the lock is released
     NoallocDevice &D = g_noalloc_dev[dev];
     exactz_workspace *ws = &g_noalloc_ws[dev];
     int nsm = 148;
@@ -1432,7 +1558,7 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
         cudaGetLastError();
         return EXACTZ_ENODEV;
     }
-    ws->layout_hash = 0;
+    ws->layout_hash = layout_key(1, &d);  // cleared above: run() need not clear them again
     // no graph objects or events here: the loop is driven from the host
     exactz_opts opt;
     exactz_default_opts(&opt);

@@ -44,6 +44,11 @@ constexpr int SCTA = 128, STWARPS = SCTA / 32;  // 12 blocks per SM: 40 register
 static_assert(SCTA % 32 == 0 && SCTA >= 32 && SCTA >= ROWS, "stencil blocks: whole warps, one thread per tile row");
 static_assert(STWARPS == TZ && TY <= 32, "frontier check: warp w visits the dirty vertices of z-slab w");
 static_assert(WBLOCK % CTA == 0 && VBLOCK % (4 * CTA) == 0, "compaction and edit-list blocks");
+// Block sizes of the one-block scans and of the small grid-stride kernels.
+// Every launch below passes the named block size of its kernel's
+// __launch_bounds__ (a CPU test parses this file and checks each launch).
+constexpr int SCAN_NT = 1024;
+constexpr int SMALL_NT = 256;
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
@@ -125,7 +130,6 @@ struct Stn {
     uint32_t up, dn, mask, valid;
 };
 
-template <bool INTERIOR>
 __device__ __forceinline__ Stn stencil15(const float *s, int c)
 {
     float v[15];
@@ -144,14 +148,36 @@ __device__ __forceinline__ Stn stencil15(const float *s, int c)
     for (int r = 0; r < 7; r++) mask |= (v[r] <= cv) ? (1u << r) : 0u;
 #pragma unroll
     for (int r = 8; r < 15; r++) mask |= (v[r] < cv) ? (1u << (r - 1)) : 0u;
-    uint32_t valid = 0x3FFFu;
-    if (!INTERIOR) {
-        valid = 0;
-#pragma unroll
-        for (int r = 0; r < 15; r++)
-            if (r != 7) valid |= (v[r] == v[r]) ? (1u << slot_of(r)) : 0u;
+    return Stn{up, dn, mask, 0x3FFFu};
+}
+
+// Mask bits (slots) of the neighbours whose offset along `axis` (0 = x,
+// 1 = y, 2 = z) is `sign`.
+__host__ __device__ constexpr uint32_t slots_along(int axis, int sign)
+{
+    uint32_t m = 0;
+    for (int r = 0; r < 15; r++) {
+        if (r == 7) continue;
+        const int o = axis == 0 ? rdx(r) : (axis == 1 ? rdy(r) : rdz(r));
+        if (o == sign) m |= 1u << slot_of(r);
     }
-    return Stn{up, dn, mask, valid};
+    return m;
+}
+
+// Neighbours of vertex (x, y, z) that lie in an nx x ny x nz field, as mask
+// slots.  (Out-of-field halo cells also hold NaN, which no compare selects,
+// so the stencil needs no other change at the boundary.)
+__device__ __forceinline__ uint32_t valid_slots(uint32_t x, uint32_t y, uint32_t z, uint32_t nx, uint32_t ny,
+                                                uint32_t nz)
+{
+    uint32_t out = 0;
+    if (x == 0) out |= slots_along(0, -1);
+    if (x + 1 >= nx) out |= slots_along(0, 1);
+    if (y == 0) out |= slots_along(1, -1);
+    if (y + 1 >= ny) out |= slots_along(1, 1);
+    if (z == 0) out |= slots_along(2, -1);
+    if (z + 1 >= nz) out |= slots_along(2, 1);
+    return 0x3FFFu & ~out;
 }
 
 // Rules R1 (steepest neighbours) and R2 (saddle links) at one vertex, as the
@@ -287,7 +313,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     __shared__ uint32_t smulti[512];
     __shared__ uint32_t s_err, s_ncp;
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
-    __shared__ uint8_t s_vis[MODE == SM_CHECK_LIST ? STWARPS : 1][TY * TX];  // a warp's dirty vertices (ly << 5 | lx)
+    __shared__ uint16_t s_vis[MODE == SM_CHECK_LIST ? TILE_V : 1];  // the tile's dirty vertices (row << 5 | lx)
     __shared__ uint32_t s_tile[2];        // the tile staged in each buffer
     __shared__ TileGeo s_geo[NB];         // its position
 
@@ -300,6 +326,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
         mbar_init_fence();
     }
     uint32_t tma_pending = 0, tma_phase = 0;  // per buffer: a TMA load in flight; the parity it completes
+    uint32_t nvisits = 0;                     // CHECK_LIST: dirty vertices this warp visited
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float qnan = __int_as_float(0x7fc00000);
 
@@ -399,43 +426,53 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
         const uint64_t vbase = F.vbase;
         const float *S = sa[b];
         const uint32_t *RW = s_rw[b];
-        // CHECK_LIST: warp w visits the dirty vertices of the four rows of
-        // z-slab w, listed in shared memory (each lane writes its own bits)
+        // CHECK_LIST: the tile's dirty vertices are listed in shared memory in
+        // row order (warp w lists the four rows of z-slab w at the offset the
+        // row counts before them give, each lane writing its own bits); after a
+        // block barrier warp w checks the batches w, w + STWARPS, ... of 32.
         int nvisit = 0;
         if (MODE == SM_CHECK_LIST) {
             if (threadIdx.x < ROWS && RW[threadIdx.x]) {  // the dirty bits are taken: clear them
                 const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
                 D.dirty[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = 0;
             }
-            uint8_t *vis = s_vis[MODE == SM_CHECK_LIST ? warp : 0];
-            int cnt = 0;
+            const uint32_t rc = lane < ROWS ? __popc(RW[lane]) : 0u;
+            uint32_t incl = rc;
+#pragma unroll
+            for (int o = 1; o < ROWS; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            nvisit = (int)__shfl_sync(0xffffffffu, incl, ROWS - 1);
 #pragma unroll
             for (int r = 0; r < TY; r++) {
-                const uint32_t w = RW[warp * TY + r];
-                if ((w >> lane) & 1u) vis[cnt + __popc(w & lanemask_lt())] = (uint8_t)((r << 5) | lane);
-                cnt += __popc(w);
+                const int row = warp * TY + r;
+                const uint32_t w = RW[row];
+                const uint32_t before = __shfl_sync(0xffffffffu, incl - rc, row);
+                if ((w >> lane) & 1u) s_vis[before + __popc(w & lanemask_lt())] = (uint16_t)((row << 5) | lane);
             }
-            __syncwarp();
-            nvisit = cnt;
+            if (warp == 0) nvisits += (uint32_t)nvisit;
+            __syncthreads();
         }
-        // index of this warp's first vertex (x0, y0, z0 + warp) in the field
-        const uint64_t wfirst = ((uint64_t)(z0 + warp) * ny + (uint64_t)y0) * nx + (uint64_t)x0;
+        // index of the tile's first vertex (x0, y0, z0) in the field
+        const uint64_t nxy = (uint64_t)nx * ny;
+        const uint64_t tfirst = ((uint64_t)z0 * ny + (uint64_t)y0) * nx + (uint64_t)x0;
         const bool interior = x0 >= 1 && x0 + TX < (int)nx && y0 >= 1 && y0 + TY < (int)ny && z0 >= 1 &&
                               z0 + TZ < (int)nz;
-        // vertices of this tile to visit: all rows (one warp per row) or the warp's dirty vertices
-        // (all modes: warp w takes the rows of z-slab w)
+        // vertices of this tile to visit: the batches of the dirty list
+        // (CHECK_LIST) or all rows, warp w taking the rows of z-slab w
         const int vend = MODE == SM_CHECK_LIST ? nvisit : (warp + 1) * TY * TX;
-        for (int base = (MODE == SM_CHECK_LIST ? 0 : warp * TY * TX); base < vend;
-             base += (MODE == SM_CHECK_LIST ? 32 : TX)) {
+        for (int base = (MODE == SM_CHECK_LIST ? warp * 32 : warp * TY * TX); base < vend;
+             base += (MODE == SM_CHECK_LIST ? STWARPS * 32 : TX)) {
             int lx, ly, lz;
             bool sel = true;
             if (MODE == SM_CHECK_LIST) {
                 const int k = base + lane;
                 sel = k < nvisit;
-                const uint32_t code = sel ? s_vis[MODE == SM_CHECK_LIST ? warp : 0][k] : 0u;
+                const uint32_t code = sel ? s_vis[k] : 0u;
                 lx = (int)(code & 31u);
-                ly = (int)(code >> 5);
-                lz = warp;
+                ly = (int)((code >> 5) % TY);
+                lz = (int)((code >> 5) / TY);
             } else {
                 const int rr = base / TX;
                 lx = lane;
@@ -447,10 +484,13 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
             const int c = ((lz + 1) * HY + (ly + 1)) * HXP + (lx + XOFF);
             bool cp = false, listed = false;
             uint32_t req = 0;
-            const uint64_t i = wfirst + (uint64_t)ly * nx + (uint64_t)lx;  // lz == warp
+            const uint64_t i = tfirst + (uint64_t)lz * nxy + (uint64_t)ly * nx + (uint64_t)lx;
+            // the vertex's neighbours in the field (all 14 away from the boundary)
+            const uint32_t valid = interior ? 0x3FFFu : valid_slots(x, y, z, nx, ny, nz);
             if (in) {
                 if (MODE == SM_SETUP || MODE == SM_CLASSIFY) {
-                    Stn sf = interior ? stencil15<true>(S, c) : stencil15<false>(S, c);
+                    Stn sf = stencil15(S, c);
+                    sf.valid = valid;
                     const uint32_t L = sf.mask, U = sf.valid & ~sf.mask;
                     const bool mn = L == 0, mxx = !mn && U == 0;
                     const bool join = !mn && !mxx && multi_bit(smulti, L);
@@ -473,12 +513,14 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
                         D.desc[vbase + i] = d;  // edit count k = 0 in the top byte
                         F.g[i] = hv;
                         if (D.events && (mn || mxx)) D.cp_rank[vbase + i] = 0;  // no linked saddle yet
-                        Stn sg = interior ? stencil15<true>(SB, c) : stencil15<false>(SB, c);
+                        Stn sg = stencil15(SB, c);
+                        sg.valid = valid;
                         req = request_mask(smulti, d, sg);
                     }
                 } else {
                     const uint32_t d = F.tma ? s_desc[b][(lz * TY + ly) * TX + lx] : __ldg(&D.desc[vbase + i]);
-                    Stn sg = interior ? stencil15<true>(S, c) : stencil15<false>(S, c);
+                    Stn sg = stencil15(S, c);
+                    sg.valid = valid;
                     req = request_mask(smulti, d, sg);
                 }
             }
@@ -625,6 +667,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
         process(cur, b);
     }
     if (MODE == SM_CHECK_LIST && threadIdx.x == 0 && src.ntiles) atomicAdd(&D.ls->sum_tiles, src.ntiles);
+    if (MODE == SM_CHECK_LIST && lane == 0 && nvisits) atomicAdd(&D.ls->sum_visits, (unsigned long long)nvisits);
 }
 
 // ------------------------------------------------------------ block scan helpers
@@ -660,51 +703,74 @@ __device__ __forceinline__ uint32_t block_excl_scan_n(uint32_t v, uint32_t &excl
     return total;
 }
 
-// Exclusive scan of n uint32 values into uint64 offsets; one block of 1024.
-__global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n,
-                                                   unsigned long long *total)
+// Exclusive scan of n uint32 values into uint64 offsets, *total = the sum
+// (if not null).  One block of SCAN_NT threads walks the input in tiles of
+// 4 * SCAN_NT values (each thread one uint4 where the input allows it), so that
+// every load and store is coalesced; a running carry joins the tiles.
+__global__ void __launch_bounds__(SCAN_NT) k_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n,
+                                                      unsigned long long *total)
 {
+    static_assert(SCAN_NT == 32 * 32, "two-level warp scan: 32 warps of 32 lanes");
     __shared__ unsigned long long sw[32];
-    const uint64_t per = (n + 1023) / 1024;
-    const uint64_t b = threadIdx.x * per, e = min(n, b + per);
-    unsigned long long s = 0;
-    for (uint64_t j = b; j < e; j++) s += in[j];
+    __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sw[warp] = x;
+    if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = sw[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+    const bool vec = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
+    for (uint64_t base = 0; base < n; base += 4 * SCAN_NT) {
+        const uint64_t j = base + 4ull * threadIdx.x;
+        uint32_t v[4];
+        if (vec && j + 3 < n) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(in + j);
+            v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = (j + u < n) ? in[j + u] : 0u;
         }
-        sw[lane] = w;
+        const unsigned long long tsum = (unsigned long long)v[0] + v[1] + v[2] + v[3];
+        unsigned long long x = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sw[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = sw[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            sw[lane] = w;
+        }
+        __syncthreads();
+        unsigned long long run = s_carry + (warp ? sw[warp - 1] : 0ull) + x - tsum;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (j + u < n) out[j + u] = run;
+            run += v[u];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += sw[31];
+        __syncthreads();
     }
-    __syncthreads();
-    unsigned long long run = (warp ? sw[warp - 1] : 0) + x - s;
-    for (uint64_t j = b; j < e; j++) {
-        out[j] = run;
-        run += in[j];
-    }
-    if (threadIdx.x == 1023 && total) *total = sw[31];
+    if (threadIdx.x == 0 && total) *total = s_carry;
 }
 
 // In-place exclusive scan of n uint32 values (sum < 2^32); one block of 1024
 // threads walks the array in tiles of 4096 (each thread one uint4), so every
 // load and store is coalesced.
-__global__ void __launch_bounds__(1024) k_scan_inplace_u32(uint32_t *a, uint64_t n)
+__global__ void __launch_bounds__(SCAN_NT) k_scan_inplace_u32(uint32_t *a, uint64_t n)
 {
+    static_assert(SCAN_NT == 32 * 32, "two-level warp scan: 32 warps of 32 lanes");
     __shared__ uint32_t sw[32];
     __shared__ uint32_t s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (uint64_t base = 0; base < n; base += 4096) {
+    for (uint64_t base = 0; base < n; base += 4 * SCAN_NT) {
         const uint64_t j = base + 4ull * threadIdx.x;
         uint32_t v[4];
         if (j + 3 < n) {
@@ -818,7 +884,7 @@ __global__ void __launch_bounds__(CTA) k_cp_write(Dev D, SetupRange R)
     }
 }
 
-__global__ void k_cp_ncp(Dev D, SetupRange R)
+__global__ void __launch_bounds__(SMALL_NT) k_cp_ncp(Dev D, SetupRange R)
 {
     const unsigned long long end = R.cp0 + *R.cp_count;
     for (uint32_t f = R.fid0 + threadIdx.x + blockIdx.x * blockDim.x; f < R.fid1; f += blockDim.x * gridDim.x) {
@@ -1186,6 +1252,69 @@ __device__ __forceinline__ uint32_t star_tiles(uint32_t x, uint32_t y, uint32_t 
 
 enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
 
+// The bounded monotone edit (Sec. 3.3) of requested vertex t of field F with
+// its loaded descriptor d, f value fv, g value g0 and CP rank rk: unless it is
+// pinned at the lossless bound, g takes one more step fl(g - Delta), or the
+// bound fl(f - xi) once the steps are used up or the step would pass it (at the
+// iteration cap the request is counted instead).  Keeps the CP's value in
+// sorted order and marks, under the original event constraints, the saddles of
+// a changed extremum.  Returns whether the vertex changed; pinned: it reached
+// the bound; has_lo / has_hi: its CP pairs (q - 1, q) / (q, q + 1) exist and
+// are to be checked (FRONTIER, or pinned).
+template <int AM>
+__device__ __forceinline__ bool edit_vertex(const Dev &D, const FieldDesc &F, FieldState *S, uint64_t t, uint32_t d,
+                                            float fv, float g0, uint32_t rk, bool capped, uint32_t &ncap,
+                                            bool &pinned, bool &has_lo, bool &has_hi, unsigned long long &q)
+{
+    const uint32_t N = F.N;
+    uint32_t kk = d >> D_K_SHIFT;
+    if (kk > N) return false;  // a pinned target stays as it is
+    if (capped) {
+        ncap++;
+        return false;
+    }
+    const float fl = __fsub_rn(fv, F.xi);
+    float gv;
+    if (kk < N) {
+        const float tt = __fsub_rn(g0, F.delta);
+        if (tt < fl) {
+            gv = fl;
+            kk = N + 1;
+        } else {
+            gv = tt;
+            kk = kk + 1;
+        }
+    } else {
+        gv = fl;
+        kk = N + 1;
+    }
+    F.g[t] = gv;
+    D.desc[F.vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
+    pinned = kk == N + 1;
+    if (D.events && (AM == AM_FRONTIER || pinned) && !(d & D_CP) && rk != 0 &&
+        ((d & 15u) == 7u || ((d >> 4) & 15u) == 7u)) {
+        // an extremum linked to saddles: their rule C3 is checked next pass,
+        // and by the residual check if it is pinned
+        const unsigned long long pw = (D.cp_cap + 31) / 32;
+        const uint32_t deg = D.ev_radj[rk];
+        for (uint32_t j = 0; j < deg; j++) {
+            const uint32_t qq = D.ev_radj[rk + 1 + j];
+            if (AM == AM_FRONTIER) atomicOr(&D.pairbits[pw + (qq >> 5)], 1u << (qq & 31));
+            if (pinned) atomicOr(&D.pairbits[2 * pw + (qq >> 5)], 1u << (qq & 31));
+        }
+    }
+    if (d & D_CP) {  // value in sorted order; pairs inside the field
+        const unsigned long long r = rk;
+        q = S->cp_base + r;
+        D.gs[q] = gv;
+        if (AM == AM_FRONTIER || pinned) {
+            has_lo = r >= 1;
+            has_hi = r + 1 < S->ncp;
+        }
+    }
+    return true;
+}
+
 // One tile holding requested vertices per warp iteration (warps work
 // independently): a warp probes 32 of its tiles' flags at once, takes (and
 // clears) the flagged ones and works through them.  The tile's 16 request words are read (and
@@ -1231,7 +1360,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         const uint32_t fid = field_of_tile(D, tile);
         const FieldDesc &F = D.fields[fid];
         FieldState *S = &D.fst[fid];
-        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny, N = F.N;
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx, tny = F.tny;
         const uint32_t lt = (uint32_t)(tile - F.tbase);
         const uint32_t rest = fdiv(lt, F.div_tnx), tx = lt - rest * tnx;
         const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * tny;
@@ -1264,6 +1393,24 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         __syncwarp();
         const bool err = S->err != 0, capped = S->iterations >= F.max_iters;
         uint32_t ncap = 0, pin_nb = 0;
+        // After the edit of one vertex (lane-local results): queue its CP pairs
+        // (FRONTIER), list the pairs and tiles around it if it was pinned.  All
+        // lanes call it.
+        auto after_edit = [&](const bool pinned, const bool has_lo, const bool has_hi, const unsigned long long q,
+                              const uint32_t x, const uint32_t y, const uint32_t z) {
+            if (AM == AM_FRONTIER) {  // the pairs (q, q+1) and (q-1, q) are checked next pass
+                if (has_hi) atomicOr(&D.pairbits[q >> 5], 1u << (q & 31));
+                if (has_lo) atomicOr(&D.pairbits[(q - 1) >> 5], 1u << ((q - 1) & 31));
+            }
+            const uint32_t npp = pinned ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
+            if (__any_sync(0xffffffffu, npp != 0)) {
+                const unsigned long long p = warp_reserve(npp, &S->pin_pair_count);
+                if (pinned && has_hi) F.pin_pairs[p] = (uint32_t)q;
+                if (pinned && has_lo) F.pin_pairs[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
+            }
+            if (pinned) pin_nb |= star_tiles(x, y, z, nx, ny, nz);
+        };
+        // the requested vertices, numbered by the row prefix sums, 32 at a time
         for (int base = 0; base < nvisit; base += 32) {
             const int k = base + lane;
             const bool sel = k < nvisit && !err;
@@ -1289,65 +1436,10 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                 const uint32_t d = D.desc[vbase + t];
                 const float fv = F.f[t], g0 = F.g[t];
                 const uint32_t rk = D.cp_rank[vbase + t];
-                uint32_t kk = d >> D_K_SHIFT;
-                if (kk <= N) {  // a pinned target stays as it is
-                    if (capped) {
-                        ncap++;
-                    } else {
-                        const float fl = __fsub_rn(fv, F.xi);
-                        float gv;
-                        if (kk < N) {
-                            const float tt = __fsub_rn(g0, F.delta);
-                            if (tt < fl) {
-                                gv = fl;
-                                kk = N + 1;
-                            } else {
-                                gv = tt;
-                                kk = kk + 1;
-                            }
-                        } else {
-                            gv = fl;
-                            kk = N + 1;
-                        }
-                        F.g[t] = gv;
-                        D.desc[vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
-                        pinned = kk == N + 1;
-                        atomicOr(&s_cw[row], 1u << lx);
-                        if (D.events && (AM == AM_FRONTIER || pinned) && !(d & D_CP) && rk != 0 &&
-                            ((d & 15u) == 7u || ((d >> 4) & 15u) == 7u)) {
-                            // an extremum linked to saddles: their rule C3 is checked
-                            // next pass, and by the residual check if it is pinned
-                            const unsigned long long pw = (D.cp_cap + 31) / 32;
-                            const uint32_t deg = D.ev_radj[rk];
-                            for (uint32_t j = 0; j < deg; j++) {
-                                const uint32_t qq = D.ev_radj[rk + 1 + j];
-                                if (AM == AM_FRONTIER) atomicOr(&D.pairbits[pw + (qq >> 5)], 1u << (qq & 31));
-                                if (pinned) atomicOr(&D.pairbits[2 * pw + (qq >> 5)], 1u << (qq & 31));
-                            }
-                        }
-                        if (d & D_CP) {  // value in sorted order; pairs inside the field
-                            const unsigned long long r = rk;
-                            q = S->cp_base + r;
-                            D.gs[q] = gv;
-                            if (AM == AM_FRONTIER || pinned) {
-                                has_lo = r >= 1;
-                                has_hi = r + 1 < S->ncp;
-                            }
-                        }
-                    }
-                }
+                if (edit_vertex<AM>(D, F, S, t, d, fv, g0, rk, capped, ncap, pinned, has_lo, has_hi, q))
+                    atomicOr(&s_cw[row], 1u << lx);
             }
-            if (AM == AM_FRONTIER) {  // the pairs (q, q+1) and (q-1, q) are checked next pass
-                if (has_hi) atomicOr(&D.pairbits[q >> 5], 1u << (q & 31));
-                if (has_lo) atomicOr(&D.pairbits[(q - 1) >> 5], 1u << ((q - 1) & 31));
-            }
-            const uint32_t npp = pinned ? (uint32_t)has_hi + (uint32_t)has_lo : 0u;
-            if (__any_sync(0xffffffffu, npp != 0)) {
-                const unsigned long long p = warp_reserve(npp, &S->pin_pair_count);
-                if (pinned && has_hi) F.pin_pairs[p] = (uint32_t)q;
-                if (pinned && has_lo) F.pin_pairs[p + (has_hi ? 1 : 0)] = (uint32_t)(q - 1);
-            }
-            if (pinned) pin_nb |= star_tiles(x, y, z, nx, ny, nz);
+            after_edit(pinned, has_lo, has_hi, q, x, y, z);
         }
         // the residual check revisits the closed stars of pinned vertices: their
         // tiles are queued once per tile, one lane per neighbour tile
@@ -1846,10 +1938,11 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
     __shared__ uint32_t s_any;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
+    const bool fault = D.ls->fault != 0;  // a bounded wait ran out: stop every field (the call reports it)
     for (uint32_t f = threadIdx.x; f < D.nfields; f += CTA) {
         FieldState *S = &D.fst[f];
         if (S->done) continue;
-        if (S->err || S->capped) {
+        if (S->err || S->capped || fault) {
             S->done = 1;
             continue;
         }
@@ -1871,7 +1964,7 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
 }
 
 // Sets the loop flag (and graph conditional) from the per-field state.
-__global__ void k_loop_flag(Dev D, cudaGraphConditionalHandle h, int use_graph)
+__global__ void __launch_bounds__(SMALL_NT) k_loop_flag(Dev D, cudaGraphConditionalHandle h, int use_graph)
 {
     __shared__ uint32_t s_any;
     if (threadIdx.x == 0) s_any = 0;
@@ -1886,7 +1979,7 @@ __global__ void k_loop_flag(Dev D, cudaGraphConditionalHandle h, int use_graph)
 }
 
 // ------------------------------------------------------------ status
-__global__ void k_status(Dev D, FieldSet FS)
+__global__ void __launch_bounds__(SMALL_NT) k_status(Dev D, FieldSet FS)
 {
     for (uint32_t j = threadIdx.x + blockIdx.x * blockDim.x; j < FS.n; j += blockDim.x * gridDim.x) {
         FieldState *S = &D.fst[FS.fids[j]];
@@ -2128,7 +2221,7 @@ static unsigned grid_for(uint64_t items, int per_block, int cap_mult)
     return (unsigned)g;
 }
 
-__global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n)
+__global__ void __launch_bounds__(SMALL_NT) k_fill_u32(uint32_t *p, uint32_t v, uint64_t n)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         p[i] = v;
@@ -2136,7 +2229,7 @@ __global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n)
 
 void launch_fill_u32(uint32_t *p, uint32_t v, uint64_t n, cudaStream_t s)
 {
-    if (n) k_fill_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(p, v, n);
+    if (n) k_fill_u32<<<grid_for(n, SMALL_NT, 4), SMALL_NT, 0, s>>>(p, v, n);
 }
 
 int device_sms() { return sms(); }
@@ -2170,9 +2263,9 @@ void launch_cp_compact(const Dev &D, const SetupRange &R, cudaStream_t s)
 {
     const unsigned nb = (unsigned)R.nwblk;
     k_cp_count<<<nb, CTA, 0, s>>>(D, R.wblk0);
-    k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, R.nwblk, R.cp_count);
+    k_scan_u32<<<1, SCAN_NT, 0, s>>>(D.blk, D.blk_off, R.nwblk, R.cp_count);
     k_cp_write<<<nb, CTA, 0, s>>>(D, R);
-    k_cp_ncp<<<(R.fid1 - R.fid0 + 255) / 256, 256, 0, s>>>(D, R);
+    k_cp_ncp<<<(R.fid1 - R.fid0 + SMALL_NT - 1) / SMALL_NT, SMALL_NT, 0, s>>>(D, R);
 }
 
 // LSD passes of one sort: four 8-bit digits of the value key, then the digits
@@ -2197,7 +2290,7 @@ void launch_cp_sort(const Dev &D, const SetupRange &R, cudaStream_t s)
     for (int p = 0; p < P; p++) {
         const int dst = src ^ 1;
         k_sort_hist<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src] + R.cp0, D.cp_ent[src] + R.cp0, R.cp_count);
-        k_scan_inplace_u32<<<1, 1024, 0, s>>>(D.hist, (uint64_t)RADIX * B);
+        k_scan_inplace_u32<<<1, SCAN_NT, 0, s>>>(D.hist, (uint64_t)RADIX * B);
         k_sort_scatter<<<B, RADIX, 0, s>>>(D, p, D.cp_key[src] + R.cp0, D.cp_ent[src] + R.cp0,
                                            D.cp_key[dst] + R.cp0, D.cp_ent[dst] + R.cp0, p == P - 1, R.cp_count,
                                            R.cp0);
@@ -2236,7 +2329,7 @@ void launch_ev_lists(const Dev &D, const uint32_t *E, int write, uint32_t *room,
 void launch_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n, unsigned long long *total,
                      cudaStream_t s)
 {
-    k_scan_u32<<<1, 1024, 0, s>>>(in, out, n, total);
+    k_scan_u32<<<1, SCAN_NT, 0, s>>>(in, out, n, total);
 }
 void launch_ev_reverse(const Dev &D, uint32_t *radj, cudaStream_t s)
 {
@@ -2255,19 +2348,19 @@ void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cuda
 }
 void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s)
 {
-    k_loop_flag<<<1, 256, 0, s>>>(D, h, use_graph);
+    k_loop_flag<<<1, SMALL_NT, 0, s>>>(D, h, use_graph);
 }
 void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s)
 {
     k_apply_tiles<AM_COUNT><<<grid_for(D.total_tiles, WARPS, 16), CTA, 0, s>>>(D);
-    k_status<<<(FS.n + 255) / 256, 256, 0, s>>>(D, FS);
+    k_status<<<(FS.n + SMALL_NT - 1) / SMALL_NT, SMALL_NT, 0, s>>>(D, FS);
 }
 void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s)
 {
     const unsigned nb = (unsigned)FS.nvblk;
     k_edit_count<<<nb, CTA, 0, s>>>(D, FS);
     if (write) {
-        k_scan_u32<<<1, 1024, 0, s>>>(D.blk, D.blk_off, FS.nvblk, nullptr);
+        k_scan_u32<<<1, SCAN_NT, 0, s>>>(D.blk, D.blk_off, FS.nvblk, nullptr);
         k_edit_write<<<nb, CTA, 0, s>>>(D, FS);
     }
 }

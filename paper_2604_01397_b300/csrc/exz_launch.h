@@ -7,6 +7,15 @@
 namespace exz {
 
 void launch_fill_u32(uint32_t *p, uint32_t v, uint64_t n, cudaStream_t s);
+// cudaMalloc through the library's allocation-failure injection (a testing aid,
+// exactz_debug_fail_allocations): an injected failure returns
+// cudaErrorMemoryAllocation without calling cudaMalloc.
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
 int device_sms();
 // 2^14-bit link-component table (host copy, built on first use; see exz_engine.cu)
 const uint32_t *host_multi_table();

@@ -150,7 +150,7 @@ struct exactz_server {
     bool stop = false;
     int error = 0;
     uint64_t next_ticket = 1;
-    uint64_t submitted = 0, completed = 0, passes = 0, max_resident = 0, admitted_vertices = 0;
+    uint64_t submitted = 0, completed = 0, cancelled = 0, passes = 0, max_resident = 0, admitted_vertices = 0;
     std::atomic<uint64_t> launches{0};  // written by the serving thread
     double busy_s = 0;
     std::mutex mu;
@@ -183,7 +183,7 @@ bool salloc(exactz_server *S, T *&p, uint64_t count)
 {
     void *q = nullptr;
     const uint64_t bytes = std::max<uint64_t>(count, 1) * sizeof(T);
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    if (dev_malloc(&q, bytes) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -672,6 +672,22 @@ int exactz_server_wait(exactz_server *S, uint64_t ticket, double timeout_s, exac
     return S->error ? S->error : 0;
 }
 
+int exactz_server_cancel(exactz_server *S, uint64_t ticket)
+{
+    if (!S) return EXACTZ_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return EXACTZ_EINVAL;
+    Req *r = it->second;
+    if (r->state != Q_QUEUED) return 0;  // admitted or finished: its result comes as usual
+    auto q = std::find(S->queue.begin(), S->queue.end(), r);
+    if (q != S->queue.end()) S->queue.erase(q);
+    S->reqs.erase(it);
+    S->cancelled++;
+    delete r;
+    return 1;
+}
+
 int exactz_server_stats(exactz_server *S, exactz_server_info *out)
 {
     if (!S || !out) return EXACTZ_EINVAL;
@@ -689,6 +705,7 @@ int exactz_server_stats(exactz_server *S, exactz_server_info *out)
     out->kernel_launches = S->launches.load();
     out->busy_s = S->busy_s;
     out->error = S->error;
+    out->cancelled = S->cancelled;
     return EXACTZ_OK;
 }
 
