@@ -84,3 +84,38 @@ def test_malformed_input_is_refused():
     kc[3] = 7  # above N + 1
     with pytest.raises(ez.ExactzError, match="EINVAL"):
         ez.decode_edits_stream(fh.cuda().reshape(-1), kc, torch.zeros(1, device="cuda"), xi, 5)
+
+
+def _hand_streams():
+    from conftest import read_golden, read_golden_cases
+
+    return read_golden, read_golden_cases("stream_1d.txt")
+
+
+@pytest.mark.parametrize("name", ["cascade_1d.txt", "lossless_1d.txt", "stuck_1d.txt"])
+def test_encoder_writes_the_hand_written_stream(name):
+    import paper_2604_01397_b300 as ez
+
+    read_golden, cases = _hand_streams()
+    c = read_golden(name)
+    dims = tuple(int(x) for x in c["dims"])
+    f = np.array([float(x) for x in c["f"]], np.float32)
+    fh = np.array([float(x) for x in c["fhat"]], np.float32)
+    N = int(c["N"][0])
+    r = ez.correct(to_dev(f, dims), to_dev(fh, dims), float(c["xi"][0]), N_steps=N)
+    st = ez.encode_edits(r["edits"], f.size, N)
+    assert bytes(st["kcodes"].cpu().numpy()) == bytes(int(h, 16) for h in cases[name]["kcodes"])
+    want = np.array([int(h, 16) for h in cases[name]["lossless"]], np.uint32)
+    assert np.array_equal(st["lossless"].cpu().numpy().view(np.uint32), want)
+
+
+def test_decoder_reads_a_hand_written_stream():
+    import paper_2604_01397_b300 as ez
+
+    _, cases = _hand_streams()
+    c = cases["decode_by_hand"]
+    fh = torch.tensor([float(x) for x in c["fhat"]], dtype=torch.float32, device="cuda")
+    k = torch.tensor([int(h, 16) for h in c["kcodes"]], dtype=torch.uint8, device="cuda")
+    lv = torch.from_numpy(np.array([int(h, 16) for h in c["lossless"]], np.uint32).view(np.float32)).cuda()
+    g = ez.decode_edits_stream(fh, k, lv, float(c["xi"][0]), int(c["N"][0]))
+    assert np.array_equal(g.cpu().numpy(), np.array([float(x) for x in c["g"]], np.float32))

@@ -63,3 +63,32 @@ def test_malformed_streams_are_refused():
         oracle.decode_stream(fh, np.full(8, 7, np.uint8), np.zeros(8, np.float32), 0.1, 5)
     with pytest.raises(ValueError):
         oracle.decode_stream(fh, np.full(8, 6, np.uint8), np.zeros(3, np.float32), 0.1, 5)
+
+
+def _stream_cases():
+    from conftest import read_golden_cases
+
+    return read_golden_cases("stream_1d.txt")
+
+
+def _lossless_of(case):
+    return np.array([int(h, 16) for h in case["lossless"]], np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("name", ["cascade_1d.txt", "lossless_1d.txt", "stuck_1d.txt"])
+def test_stream_equals_the_hand_written_one(name):
+    # the layout is pinned by streams written out by hand, not only by round trips
+    case = _stream_cases()[name]
+    dims, xi, N, f, fh = _golden(name)
+    r = oracle.correct(f, fh, xi, dims=dims, N=N)
+    k, lossless = oracle.edit_stream(r, N)
+    assert bytes(k) == bytes(int(h, 16) for h in case["kcodes"])
+    assert np.array_equal(lossless.view(np.uint32), _lossless_of(case).view(np.uint32))
+
+
+def test_decode_of_a_hand_written_stream():
+    case = _stream_cases()["decode_by_hand"]
+    k = np.array([int(h, 16) for h in case["kcodes"]], np.uint8)
+    fh = np.array([float(x) for x in case["fhat"]], np.float32)
+    g = oracle.decode_stream(fh, k, _lossless_of(case), float(case["xi"][0]), int(case["N"][0]))
+    assert np.array_equal(g, np.array([float(x) for x in case["g"]], np.float32))
