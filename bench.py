@@ -1,23 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the B300 EXaCTz correction: corrected GB/s to fixpoint.
 
-Default workload (N = 1): one 512^3 float32 field of 4096 Gaussian bumps
-(sigma ~ U[2, 16]) + N(0, 0.01) noise, seed 1, xi = 1e-4 * range,
-f_hat = f + U(-xi, xi), corrected to its fixpoint with the CUDA-graph loop.
-A step is one whole correction (set-up stencil, CP compaction and sort, all
-passes, residual check, edit list) with inputs resident in HBM; the value is
-4 * n bytes of float32 input per step time (each input field is 512 MiB, so
-every step streams more than the 126 MB L2).
+Default workload (N = 1): the batched form.  256 independent float32 fields,
+each axis uniform in [32, 256] (806 M vertices, 3.0 GiB of input), each a sum
+of ceil(volume / 4096) Gaussian bumps (sigma ~ U[2, 8]) + N(0, 0.01) noise with
+its own seed 1000 + j, xi = 1e-3 / 1e-4 of its range (alternating), f_hat =
+f + U(-xi, xi); all fields corrected to their fixpoints in one run
+(exactz_ws_correct: one launch per kernel per pass over every field, the
+iterate-to-fixpoint loop as a CUDA-graph while-node).  A step is one whole
+correction of all 256 fields with inputs resident in HBM; the value is
+4 * (total vertices) bytes of float32 input per step time.
 
-Also reported on the same JSON line: the same metric end to end through the C
-ABI with host buffers (copies inside the timed region), the roofline of the
-dominant kernel from CUDA events recorded around it on its own stream during
-the timed steps, the plain and host-driven frontier loops, the oracle on a
-bounded crop of the same workload on the host cores, and the SM clocks
-sampled during the timed region.
+Beside it on the same JSON line:
+  batched_vs_plain  the same fields one call at a time in the plain loop (the
+                    one-field-per-launch form) and in the per-field graph
+                    loop, the ratios and the >= 2x target
+  roofline          the dominant kernel (the frontier vertex check) from CUDA
+                    events recorded around its launches on its own stream
+  e2e               the same correction through the C ABI with host buffers
+                    (copies in and out inside the timed region)
+  cpu_baseline      the oracle (worklist mode, OpenMP on all host cores; and
+                    the plain mode on one core) on a bounded sample of the
+                    same fields
+  p50_ms / p99_ms   the request server under a Poisson stream (lambda = 100/s,
+                    10 s): latency from arrival to results in host memory
+  extras            1024^3 multi-octave noise (xi = 1e-4): graph vs plain loop
+                    with its own roofline; serving details; per-field status
+                    and residual violations; SM clocks
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload bumps512|bumps64|octave1024|batched|serving] [--size S]
+                  [--workload batched|bumps512|bumps64|octave1024|serving|nsweep] [--size S]
 
 With N > 1 (torchrun) every rank corrects its own replica of the workload
 (no data-path collective; a barrier and a max-reduction of the step time only).
@@ -33,6 +45,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -44,6 +57,8 @@ METRIC = "corrected GB/s on 1 B300 to fixpoint, batched vs plain; % HBM peak; p9
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
 TILE_V = 32 * 4 * 4  # vertices of a tile
+CHECK_TILE_BYTES = TILE_V * 8 + 16 * 4  # g and descriptor of a checked tile's vertices + its dirty row words
+APPLY_REQUEST_BYTES = 24  # descriptor, f, g, CP rank read; g and descriptor written, per requested vertex
 
 
 def parse():
@@ -52,7 +67,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="bumps512")
+    p.add_argument("--workload", default="batched")
     p.add_argument("--size", type=int, default=0, help="override the cube side (profiling runs)")
     p.add_argument("--rel", type=float, default=0.0, help="override xi / range of the workload")
     p.add_argument("--mode", default="graph", choices=["graph", "frontier", "plain"])
@@ -67,6 +82,7 @@ def parse():
     p.add_argument("--rates", default="50,200,800", help="serving workload: Poisson arrival rates (1/s)")
     p.add_argument("--duration", type=float, default=10.0, help="serving workload: arrival window per rate (s)")
     p.add_argument("--budget-gb", type=float, default=120.0, help="serving workload: HBM budget (GB)")
+    p.add_argument("--serve-rate", type=float, default=100.0, help="batched workload: rate of its serving extra")
     return p.parse_args()
 
 
@@ -237,11 +253,6 @@ def oracle_sample(f, fh, xi, side: int, events: str = "reformulated"):
     return time.perf_counter() - t0, r
 
 
-def omp_threads() -> int:
-    v = os.environ.get("OMP_NUM_THREADS")
-    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
-
-
 def choose_side(f, fh, xi, budget_s: float, lo=32, hi=256, events: str = "reformulated"):
     """Pick a crop side whose oracle run takes about budget_s: calibrated on a
     small crop, then once more on the first estimate (the cost per vertex of a
@@ -255,41 +266,122 @@ def choose_side(f, fh, xi, budget_s: float, lo=32, hi=256, events: str = "reform
     return max(lo, min(cap, int(side * (budget_s / max(t, 1e-9)) ** (1 / 3))))
 
 
+def omp_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+# The oracle timed in a child process of its own (a fresh interpreter with no
+# CUDA context and no torch thread pool competing for the cores): it corrects
+# the fields written to `dir` in order until `budget_s` has passed (the sample),
+# then repeats that sample `repeats` more times and prints one JSON line.
+ORACLE_CHILD = r"""
+import json, os, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+d, budget, repeats, worklist = sys.argv[2], float(sys.argv[3]), int(sys.argv[4]), sys.argv[5] == "1"
+meta = json.load(open(os.path.join(d, "meta.json")))
+def one(j):
+    m = meta[j]
+    f = np.load(os.path.join(d, f"f{j}.npy")); h = np.load(os.path.join(d, f"h{j}.npy"))
+    t = time.perf_counter()
+    r = oracle.correct(f, h, m["xi"], dims=m["dims"], worklist=worklist, edit_list=False)
+    return time.perf_counter() - t, r
+t0 = time.perf_counter(); sample, its = [], []
+for j in range(len(meta)):
+    dt, r = one(j); sample.append(j); its.append(r["iterations"])
+    if time.perf_counter() - t0 >= budget: break
+first = time.perf_counter() - t0
+steps = []
+for _ in range(repeats):
+    t = time.perf_counter()
+    for j in sample: one(j)
+    steps.append(time.perf_counter() - t)
+nv = sum(int(np.prod(meta[j]["dims"])) for j in sample)
+print(json.dumps({"fields": len(sample), "vertices": nv, "first_s": first, "steps_s": steps, "iterations": its}))
+"""
+
+
+def write_oracle_inputs(d: str, fields):
+    """fields: (f, f_hat, xi, dims) with f, f_hat numpy float32 arrays."""
+    meta = []
+    for j, (f, fh, xi, dims) in enumerate(fields):
+        np.save(os.path.join(d, f"f{j}.npy"), np.ascontiguousarray(f, np.float32).reshape(-1))
+        np.save(os.path.join(d, f"h{j}.npy"), np.ascontiguousarray(fh, np.float32).reshape(-1))
+        meta.append({"xi": float(xi), "dims": [int(v) for v in dims]})
+    json.dump(meta, open(os.path.join(d, "meta.json"), "w"))
+
+
+def oracle_child(d: str, budget_s: float, repeats: int, worklist: bool, threads: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    out = subprocess.run([sys.executable, "-c", ORACLE_CHILD, ROOT, d, str(budget_s), str(repeats),
+                          "1" if worklist else "0"], env=env, check=True, capture_output=True, text=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    r["threads"] = threads
+    return r
+
+
 # ---------------------------------------------------------------- reference arm
+def batched_describe(count: int) -> str:
+    return (f"{count} fields, axes U{{32..256}}, Gaussian bumps (volume/4096, sigma~U[2,8]) + N(0,0.01), "
+            "seeds 1000+j, xi 1e-3/1e-4 alternating, f_hat = f + U(-xi,xi)")
+
+
 def run_reference(a):
+    """The oracle, as it stands, on the host cores: the reference arm."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import torch
-
-    c = workload_spec(a.workload, a.size, a.rel)
-    f, fh, xi = make_fields(c, "cpu")
-    f, fh = f.numpy(), fh.numpy()
     budget = max(2.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
-    side = choose_side(f, fh, xi, budget, events=a.events)
-    for _ in range(a.warmup):
-        oracle_sample(f, fh, xi, side, a.events)
-    times = []
-    for _ in range(a.steps):
-        t, r = oracle_sample(f, fh, xi, side, a.events)
-        times.append(t)
-    ms = 1e3 * statistics.mean(times)
-    val = 4.0 * side ** 3 / (ms / 1e3) / 1e9
     cores = omp_threads()
-    sample = (f"{side}^3 corner crop of the {c['name']} workload ({side ** 3} vertices), plain oracle "
-              f"(full sweep each pass, {a.events} event constraints), to fixpoint: {r['iterations']} passes, "
-              f"{r['n_edits']} edits")
+    if a.workload == "batched":
+        import synth
+
+        specs = synth.batched_specs(count=a.fields)
+        # the first fields of the batch, made on the CPU: more than the budget needs
+        take, nv = [], 0
+        for sp in specs:
+            take.append(sp)
+            nv += int(np.prod(sp["dims"]))
+            if nv >= budget * 3e6:
+                break
+        cases = synth.make_cases_cpu(take)
+        with tempfile.TemporaryDirectory() as d:
+            write_oracle_inputs(d, [(f.numpy(), fh.numpy(), xi, sp["dims"]) for (f, fh, xi), sp in zip(cases, take)])
+            del cases
+            r = oracle_child(d, budget, max(0, a.warmup - 1) + a.steps, True, cores)
+        ms = 1e3 * statistics.mean(r["steps_s"][-a.steps:])
+        val = 4.0 * r["vertices"] / (ms / 1e3) / 1e9
+        sample = (f"the first {r['fields']} fields of the batch ({r['vertices']} vertices, made on the CPU), "
+                  f"oracle worklist mode (OpenMP, {cores} threads), each to its fixpoint")
+        config = {"workload": batched_describe(a.fields), "events": "reformulated", "sample": sample}
+    else:
+        c = workload_spec(a.workload, a.size, a.rel)
+        f, fh, xi = make_fields(c, "cpu")
+        f, fh = f.numpy(), fh.numpy()
+        side = choose_side(f, fh, xi, budget, events=a.events)
+        for _ in range(a.warmup):
+            oracle_sample(f, fh, xi, side, a.events)
+        times = []
+        for _ in range(a.steps):
+            t, r = oracle_sample(f, fh, xi, side, a.events)
+            times.append(t)
+        ms = 1e3 * statistics.mean(times)
+        val = 4.0 * side ** 3 / (ms / 1e3) / 1e9
+        sample = (f"{side}^3 corner crop of the {c['name']} workload ({side ** 3} vertices), plain oracle "
+                  f"(full sweep each pass, {a.events} event constraints), to fixpoint: {r['iterations']} passes, "
+                  f"{r['n_edits']} edits")
+        config = {"workload": describe(c), "events": a.events, "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": describe(c), "events": a.events, "sample": sample},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
-
 # ---------------------------------------------------------------- our arm
-def run_ours(a):
+def run_single(a):
     import torch
 
     import paper_2604_01397_b300 as ez
@@ -599,44 +691,122 @@ def run_nsweep(a):
     ws.close()
 
 
-# ---------------------------------------------------------------- many fields
+# ---------------------------------------------------------------- many fields (the default workload)
+def frontier_roofline(ws, fs, fhs, xis, gs, ebufs, reps: int, peak: float, peak_kind: str, workload: str,
+                      **kw) -> dict:
+    """Roofline of the dominant kernel, the frontier vertex check
+    (k_stencil<CHECK_LIST>): `reps` more corrections in the host-driven
+    frontier form, which runs the same passes as the graph loop, with CUDA
+    events on the launching stream around every launch of the loop kernels.
+    Algorithmic bytes per checked tile: the g values and descriptors of its
+    512 vertices (4 + 4 bytes each) and its 16 dirty row words."""
+    chk_ms = tiles = passes = 0.0
+    ker = {"check": 0.0, "pairs": 0.0, "apply": 0.0}
+    for _ in range(reps):
+        ws.correct(fs, fhs, xis, mode="frontier", profile=True, g_out=gs, edit_bufs=ebufs, **kw)
+        st = ws.stats()
+        chk_ms += st["loop_kernel_ms"]["check"]
+        tiles += st["sum_tiles"]
+        passes += st["loop_passes"]
+        for k in ker:
+            ker[k] += st["loop_kernel_ms"][k]
+    launch_ms = chk_ms / max(1.0, passes)
+    alg = tiles / max(1.0, passes) * CHECK_TILE_BYTES
+    achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": "k_stencil<CHECK_LIST> (frontier vertex check)", "achieved": achieved,
+            "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic("k_stencil<CHECK_LIST>", workload), "algorithmic_bytes": alg,
+            "limiter": ncu_limiter("k_stencil<CHECK_LIST>"), "launch_ms": launch_ms, "launches": int(passes),
+            "measured": f"{reps} frontier-mode corrections, CUDA events around each launch",
+            "loop_kernel_ms_per_correction": {k: v / reps for k, v in ker.items()}}
+
+
+def octave_extra(a, ez, dev, peak, peak_kind) -> dict:
+    """1024^3 multi-octave noise at xi = 1e-4 of the range: the largest single
+    field, graph loop against the plain loop, with its own roofline."""
+    import torch
+
+    c = workload_spec("octave1024", 0, 1e-4)
+    t0 = time.perf_counter()
+    f, fh, xi = make_fields(c, dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n = f.numel()
+    ws = ez.Workspace([c["dims"]])
+    g = torch.empty_like(f)
+    ebuf = torch.empty((n // 4, 16), dtype=torch.uint8, device=dev)
+    tuning = ws.autotune([f], [fh], [xi], repeats=1) if not a.no_autotune else ws.tuning()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": describe(c), "tuning": tuning, "generation_s": gen_s}
+    for mode, reps in (("graph", 3), ("plain", 1)):
+        ws.correct([f], [fh], [xi], mode=mode, g_out=[g], edit_bufs=[ebuf])
+        e0.record(stream)
+        for _ in range(reps):
+            r = ws.correct([f], [fh], [xi], mode=mode, g_out=[g], edit_bufs=[ebuf])[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[mode] = {"ms": ms, "gbs": 4.0 * n / (ms / 1e3) / 1e9, "iterations": r["iterations"],
+                     "status": r["status_name"], "n_edits": r["n_edits"], "residual_violations": r["residual"]}
+    out["graph_vs_plain"] = out["plain"]["ms"] / out["graph"]["ms"]
+    out["roofline"] = frontier_roofline(ws, [f], [fh], [xi], [g], [ebuf], 1, peak, peak_kind, c["name"])
+    ws.close()
+    del f, fh, g, ebuf
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_batched(a):
-    """256 uneven fields corrected in one run (one launch per stage per pass over
-    all fields, CUDA-graph loop) against the same fields one call at a time."""
+    """All fields of the batch corrected in one run (one launch per kernel per
+    pass over every field, CUDA-graph loop), against the same fields one call
+    at a time (plain loop and graph loop)."""
     import torch
 
     import paper_2604_01397_b300 as ez
     import synth
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
     specs = synth.batched_specs(count=a.fields)
-    dev = torch.device("cuda", torch.cuda.current_device())
+    # made on the host cores (one process per core, the same bytes on every
+    # host: the inputs of the stored oracle digests), then copied to the device
     t0 = time.perf_counter()
     fs, fhs, xis = [], [], []
-    for sp in specs:
-        f, fh, xi = synth.make_case(sp["kind"], sp["dims"], sp["seed"], sp["rel"], sp["fhat"],
-                                    n_bumps=sp["n_bumps"], sigma=sp["sigma"], device=dev)
-        fs.append(f)
-        fhs.append(fh)
+    for f, fh, xi in synth.make_cases_cpu(specs, workers=max(1, (os.cpu_count() or 1) // world)):
+        fs.append(f.to(dev))
+        fhs.append(fh.to(dev))
         xis.append(xi)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     dims = [sp["dims"] for sp in specs]
-    n_total = sum(f.numel() for f in fs)
+    ns = [f.numel() for f in fs]
+    n_total = sum(ns)
     ws = ez.Workspace(dims)
     gs = [torch.empty_like(f) for f in fs]
-    caps = [min(f.numel(), 1 << 22) for f in fs]
+    caps = [min(n, 1 << 22) for n in ns]
     ebufs = [torch.empty((c, 16), dtype=torch.uint8, device=dev) for c in caps]
     stream = torch.cuda.current_stream()
 
-    def batched(mode="graph"):
-        return ws.correct(fs, fhs, xis, mode=mode, g_out=gs, edit_bufs=ebufs)
+    def batched(mode="graph", profile=False):
+        return ws.correct(fs, fhs, xis, mode=mode, g_out=gs, edit_bufs=ebufs, profile=profile)
 
     tuning = ws.autotune(fs, fhs, xis, repeats=1) if not a.no_autotune else ws.tuning()
-
     for _ in range(max(3, a.warmup)):
         rs = batched()
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(dev.index, enabled=not a.no_clocks)
+    clocks = Clocks(dev.index if dev.index is not None else 0, enabled=not a.no_clocks)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
     e0.record(stream)
@@ -647,47 +817,146 @@ def run_batched(a):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / a.steps
+    if dist:
+        ms = max_over_ranks(ms, dist, dev)
+    value = replica_throughput(world, n_total, ms)
     st = ws.stats()
+    if rank != 0:
+        ws.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    statuses = {}
+    for r in rs:
+        statuses[r["status_name"]] = statuses.get(r["status_name"], 0) + 1
+    iters = [r["iterations"] for r in rs]
+    extras = {"passes": st["passes"], "max_iterations": max(iters), "mean_iterations": statistics.mean(iters),
+              "status_counts": statuses, "residual_violations": sum(r["residual"] for r in rs),
+              "n_edits": sum(r["n_edits"] for r in rs), "n_lossless": sum(r["n_lossless"] for r in rs),
+              "mvertices_per_s": n_total / (ms / 1e3) / 1e6, "generation_s": gen_s,
+              "workspace_gib": ws.nbytes / 2 ** 30}
+    roof = frontier_roofline(ws, fs, fhs, xis, gs, ebufs, max(1, min(a.steps, 3)), peak, peak_kind,
+                             f"batched{a.fields}")
+    batched(profile=True)
+    extras["stage_ms"] = ws.stats()["stage_ms"]
 
     # the same fields one call at a time, each with its own workspace (made beforehand)
-    per = [ez.Workspace([d]) for d in dims]
-    g1 = [torch.empty_like(f) for f in fs]
-    loop_ms = {}
-    same = True
-    for mode in ("graph", "plain"):
-        for i in range(len(fs)):  # warm-up: graphs captured, caches primed
-            per[i].correct([fs[i]], [fhs[i]], [xis[i]], mode=mode, g_out=[g1[i]], edit_bufs=[ebufs[i]])
-        torch.cuda.synchronize()
-        e0.record(stream)
+    vs_plain = None
+    if world == 1 and not a.no_extras:
+        per = [ez.Workspace([d]) for d in dims]
+        g1 = [torch.empty_like(f) for f in fs]
+        loop_ms = {}
+        same = True
+        for mode in ("plain", "graph"):
+            for i in range(len(fs)):  # warm-up: graphs captured, caches primed
+                per[i].correct([fs[i]], [fhs[i]], [xis[i]], mode=mode, g_out=[g1[i]], edit_bufs=[ebufs[i]])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(len(fs)):
+                r1 = per[i].correct([fs[i]], [fhs[i]], [xis[i]], mode=mode, g_out=[g1[i]], edit_bufs=[ebufs[i]])[0]
+                same &= r1["iterations"] == rs[i]["iterations"] and r1["status"] == rs[i]["status"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            loop_ms[mode] = e0.elapsed_time(e1)
+            same &= all(torch.equal(g1[i].view(torch.int32), gs[i].view(torch.int32)) for i in range(len(fs)))
+        for w in per:
+            w.close()
+        del g1, per
+        vs_plain = {"batched_gbs": value, "per_field_plain_ms": loop_ms["plain"],
+                    "per_field_plain_gbs": 4.0 * n_total / (loop_ms["plain"] / 1e3) / 1e9,
+                    "ratio": loop_ms["plain"] / ms, "target_ratio": 2.0,
+                    "per_field_graph_ms": loop_ms["graph"],
+                    "per_field_graph_gbs": 4.0 * n_total / (loop_ms["graph"] / 1e3) / 1e9,
+                    "ratio_vs_per_field_graph": loop_ms["graph"] / ms, "same_results": bool(same),
+                    "plain": "exactz_ws_correct per field, plain loop (full sweep each pass, host reads the flag)"}
+
+    # end to end through the C ABI with host buffers: every step copies all
+    # fields' f and f_hat in and their g and edit records out
+    e2e = None
+    if not a.no_e2e:
+        offs = np.cumsum([0] + ns)
+        hf = torch.empty(n_total, dtype=torch.float32, pin_memory=True)
+        hh = torch.empty(n_total, dtype=torch.float32, pin_memory=True)
+        hg = torch.empty(n_total, dtype=torch.float32, pin_memory=True)
         for i in range(len(fs)):
-            r1 = per[i].correct([fs[i]], [fhs[i]], [xis[i]], mode=mode, g_out=[g1[i]], edit_bufs=[ebufs[i]])[0]
-            same &= r1["iterations"] == rs[i]["iterations"] and r1["status"] == rs[i]["status"]
-        e1.record(stream)
+            hf[offs[i]:offs[i + 1]].copy_(fs[i].reshape(-1))
+            hh[offs[i]:offs[i + 1]].copy_(fhs[i].reshape(-1))
+        ecaps = [r["n_edits"] + 1 for r in rs]
+        eoffs = np.cumsum([0] + ecaps)
+        he = torch.empty((int(eoffs[-1]), 16), dtype=torch.uint8, pin_memory=True)
+        hfs = [hf[offs[i]:offs[i + 1]] for i in range(len(fs))]
+        hhs = [hh[offs[i]:offs[i + 1]] for i in range(len(fs))]
+        hgs = [hg[offs[i]:offs[i + 1]] for i in range(len(fs))]
+        hes = [he[eoffs[i]:eoffs[i + 1]] for i in range(len(fs))]
+        kw = dict(dims=dims, g_out=hgs, edit_bufs=hes, host_buffers=True, mode="graph")
+        ws.correct(hfs, hhs, xis, **kw)
         torch.cuda.synchronize()
-        loop_ms[mode] = e0.elapsed_time(e1)
-        same &= all(torch.equal(g1[i].view(torch.int32), gs[i].view(torch.int32)) for i in range(len(fs)))
-    for w in per:
-        w.close()
-    value = 4.0 * n_total / (ms / 1e3) / 1e9
-    iters = [r["iterations"] for r in rs]
-    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
+        reps = max(1, min(a.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            rh = ws.correct(hfs, hhs, xis, **kw)
+        torch.cuda.synchronize()
+        ems = 1e3 * (time.perf_counter() - t0) / reps
+        same = all(torch.equal(hgs[i].view(torch.int32), gs[i].reshape(-1).cpu().view(torch.int32))
+                   and rh[i]["n_edits"] == rs[i]["n_edits"] for i in range(len(fs)))
+        e2e = {"value": 4.0 * n_total / (ems / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": 8 * n_total, "d2h_bytes_per_step": 4 * n_total + 16 * sum(r["n_edits"] for r in rh),
+               "api": "Workspace.correct(host_buffers=True) over all fields (exactz_ws_correct), "
+                      f"{reps} steps, wall clock", "same_result": bool(same)}
+        del hf, hh, hg, he, hfs, hhs, hgs, hes
+
+    # the oracle on a bounded sample of the same fields (the bytes timed above)
+    cpu = None
+    if not a.no_cpu and world == 1:
+        def sample(order, cap):
+            take, nv = [], 0
+            for i in order:
+                take.append((fs[i].cpu().numpy(), fhs[i].cpu().numpy(), xis[i], dims[i]))
+                nv += ns[i]
+                if nv >= cap:
+                    break
+            return take
+
+        with tempfile.TemporaryDirectory() as d:  # worklist + OpenMP: the batch's fields in order
+            write_oracle_inputs(d, sample(range(len(fs)), 40e6))
+            wl = oracle_child(d, 12.0, 0, True, omp_threads())
+        with tempfile.TemporaryDirectory() as d:  # plain, one core: the smallest fields first
+            write_oracle_inputs(d, sample(sorted(range(len(fs)), key=lambda i: ns[i]), 4e6))
+            pl = oracle_child(d, 6.0, 0, False, 1)
+        cpu = {"value": 4.0 * wl["vertices"] / wl["first_s"] / 1e9, "unit": "GB/s", "cores": wl["threads"],
+               "kind": "oracle",
+               "sample": f"the first {wl['fields']} fields of this batch ({wl['vertices']} vertices), oracle worklist "
+                         f"mode (OpenMP, {wl['threads']} threads), each to its fixpoint, {wl['first_s']:.1f} s",
+               "plain_1core": {"value": 4.0 * pl["vertices"] / pl["first_s"] / 1e9, "unit": "GB/s", "cores": 1,
+                               "sample": f"the {pl['fields']} smallest fields ({pl['vertices']} vertices), plain "
+                                         f"mode (full sweep each pass), {pl['first_s']:.1f} s"}}
+
+    ws.close()
+    del fs, fhs, gs, ebufs, rs
+    torch.cuda.empty_cache()
+    serving = None
+    if world == 1 and not a.no_extras:
+        extras["octave1024"] = octave_extra(a, ez, dev, peak, peak_kind)
+        per_rate, sgen, _, slaunch = serve_stream(ez, dev, [a.serve_rate], a.duration, a.budget_gb)
+        serving = per_rate[0]
+        serving["pool_generation_s"] = sgen
+        serving["gpu_launches"] = slaunch
+        extras["serving"] = serving
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
             "warmup": max(3, a.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{len(fs)} fields, axes U{{32..256}}, Gaussian bumps (volume/4096, sigma~U[2,8]) "
-                                   f"+ N(0,0.01), seeds 1000+j, xi 1e-3/1e-4 alternating, f_hat = f + U(-xi,xi)",
-                       "vertices": n_total, "mode": "graph, all fields in one run", "parallelism": "replicas x1",
-                       "tuning": tuning},
-            "gpu_launches": launches, "clocks": clk,
-            "extras": {"per_field_graph_ms": loop_ms["graph"], "per_field_plain_ms": loop_ms["plain"],
-                       "speedup_vs_per_field_graph": loop_ms["graph"] / ms,
-                       "speedup_vs_per_field_plain": loop_ms["plain"] / ms,
-                       "per_field_plain_gbs": 4.0 * n_total / (loop_ms["plain"] / 1e3) / 1e9,
-                       "same_results": bool(same), "passes": st["passes"], "max_iterations": max(iters),
-                       "mean_iterations": statistics.mean(iters), "generation_s": gen_s,
-                       "workspace_gib": ws.nbytes / 2 ** 30}}
+            "config": {"workload": batched_describe(a.fields), "vertices": n_total,
+                       "input_bytes": 4 * n_total, "mode": "graph, all fields in one run (exactz_ws_correct)",
+                       "l2": "inputs larger than L2 (3.0 GiB of input per step)",
+                       "parallelism": f"replicas x{world}", "tuning": tuning},
+            "batched_vs_plain": vs_plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "p50_ms": serving["p50_ms"] if serving else None, "p99_ms": serving["p99_ms"] if serving else None,
+            "gpu_launches": launches, "clocks": clk, "extras": extras}
     print(json.dumps(line), flush=True)
-    ws.close()
-
+    if dist:
+        dist.destroy_process_group()
 
 # ---------------------------------------------------------------- serving
 POOL = {64: 8, 128: 6, 256: 4, 512: 2}  # distinct pre-generated fields per cube side
@@ -716,18 +985,16 @@ def _fifo(arrivals, service):
     return lat, kept, free_at
 
 
-def run_serving(a):
-    """Poisson request streams served by the continuous-batching server, with
-    host buffers (copies in and out inside every latency), against the plain
-    per-request path on the same arrivals."""
+def serve_stream(ez, dev, rates, duration: float, budget_gb: float):
+    """Poisson request streams at each rate served by the continuous-batching
+    server, with host buffers (copies in and out inside every latency), against
+    the plain per-request path on the same arrivals.  Returns (one dict per
+    rate, pool generation seconds, per-request service seconds, launches)."""
     import torch
 
-    import paper_2604_01397_b300 as ez
     import synth
 
-    dev = torch.device("cuda", torch.cuda.current_device())
-    rates = [float(x) for x in a.rates.split(",") if x]
-    streams = {lam: synth.serving_requests(lam, a.duration) for lam in rates}
+    streams = {lam: synth.serving_requests(lam, duration) for lam in rates}
     # pool: the first POOL[side] requests of each side in the densest stream give the fields
     t0 = time.perf_counter()
     pool = {side: [] for side in POOL}
@@ -747,7 +1014,7 @@ def run_serving(a):
     rings = {side: [(torch.empty(side ** 3, dtype=torch.float32, pin_memory=True),
                      torch.empty((side ** 3 // 4, 16), dtype=torch.uint8, pin_memory=True))
                     for _ in range(2 if side >= 512 else 4)] for side in POOL}
-    budget = int(min(a.budget_gb * 1e9, torch.cuda.mem_get_info()[0] - 24e9))
+    budget = int(min(budget_gb * 1e9, torch.cuda.mem_get_info()[0] - 24e9))
 
     def entry(sp):
         side = sp["dims"][0]
@@ -771,7 +1038,6 @@ def run_serving(a):
 
     per_rate = []
     launches = 0
-    clocks = Clocks(dev.index, enabled=not a.no_clocks)
     for lam in rates:
         reqs = streams[lam]
         srv = ez.Server(budget_bytes=budget, max_fields=64, N_steps=5)
@@ -827,15 +1093,32 @@ def run_serving(a):
         pbytes = sum(4 * r["dims"][0] ** 3 for r, ok in zip(reqs, kept) if ok)
         pshed = kept.count(False)
         per_rate.append({
-            "rate_per_s": lam, "requests": len(reqs), "completed": len(lat), "shed": shed,
-            "offered_gbs": sum(4 * r["dims"][0] ** 3 for r in reqs) / a.duration / 1e9,
+            "rate_per_s": lam, "window_s": duration, "requests": len(reqs), "completed": len(lat), "shed": shed,
+            "offered_gbs": sum(4 * r["dims"][0] ** 3 for r in reqs) / duration / 1e9,
             "gbs": bytes_done / wall / 1e9, "p50_ms": _percentile(lat, 50) * 1e3, "p99_ms": _percentile(lat, 99) * 1e3,
             "passes": st["passes"] - base_passes, "max_resident": st["max_resident"],
             "h2d_bytes_per_request": h2d / max(1, len(lat)), "d2h_bytes_per_request": d2h / max(1, len(lat)),
             "same_counts_as_per_request": bool(same),
             "per_request_plain": {"gbs": pbytes / max(pend, 1e-9) / 1e9, "shed": pshed,
                                   "p50_ms": _percentile(plat, 50) * 1e3, "p99_ms": _percentile(plat, 99) * 1e3},
+            "budget_bytes": budget,
         })
+    service_s = {f"{k[0]}^3#{k[1]}": v for k, v in service.items()}
+    del pool, rings
+    torch.cuda.empty_cache()
+    return per_rate, gen_s, service_s, launches
+
+
+def run_serving(a):
+    """Poisson request streams served by the continuous-batching server."""
+    import torch
+
+    import paper_2604_01397_b300 as ez
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rates = [float(x) for x in a.rates.split(",") if x]
+    clocks = Clocks(dev.index, enabled=not a.no_clocks)
+    per_rate, gen_s, service, launches = serve_stream(ez, dev, rates, a.duration, a.budget_gb)
     clk = clocks.stop()
     best = max(per_rate, key=lambda r: r["gbs"])
     knee = max([r["rate_per_s"] for r in per_rate if r["shed"] == 0 and r["completed"] == r["requests"]
@@ -846,16 +1129,17 @@ def run_serving(a):
             "config": {"workload": "Poisson request streams, cubes 64/128/256/512 (p .4/.3/.2/.1), bumps or 3-octave "
                                    "noise 50/50, xi 1e-3/1e-4 of range, f_hat by 2xi-quantisation, request seed 1e6+r; "
                                    f"each request draws its field from a pool of {POOL} pre-generated fields",
-                       "rates_per_s": rates, "window_s": a.duration, "budget_bytes": budget, "max_fields": 64,
-                       "shed_above_outstanding": QMAX, "l2": "inputs larger than L2 (the 512^3 fields)",
+                       "rates_per_s": rates, "window_s": a.duration, "budget_bytes": best["budget_bytes"],
+                       "max_fields": 64, "shed_above_outstanding": QMAX, "l2": "inputs larger than L2 (the 512^3 fields)",
                        "latency": "arrival to g and edit list in pinned host memory",
                        "per_request_path": "exactz_ws_correct, host buffers, plain loop; service time measured per "
                                            "pool field, FIFO queue simulated on the same arrivals"},
             "e2e": {"value": best["gbs"], "unit": "GB/s", "h2d_bytes_per_step": best["h2d_bytes_per_request"],
                     "d2h_bytes_per_step": best["d2h_bytes_per_request"],
                     "step": "one request (the value is already host to host)"},
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
             "gpu_launches": launches, "clocks": clk, "knee_rate_per_s": knee, "per_rate": per_rate,
-            "extras": {"generation_s": gen_s, "service_s": {f"{k[0]}^3#{k[1]}": v for k, v in service.items()}}}
+            "extras": {"generation_s": gen_s, "service_s": service}}
     print(json.dumps(line), flush=True)
 
 
@@ -871,7 +1155,7 @@ def main():
     elif a.workload == "nsweep" or a.workload.startswith("nsweep:"):
         run_nsweep(a)
     else:
-        run_ours(a)
+        run_single(a)
 
 
 if __name__ == "__main__":
