@@ -161,6 +161,7 @@ struct exactz_workspace {
     uint32_t *pin_tile_arena = nullptr, *pin_tile_bits = nullptr;
     uint32_t *pin_pair_arena = nullptr;
     uint32_t *fids = nullptr;  // 0, 1, ..., cap_nf - 1: the set of all fields
+    uint32_t *tile_field = nullptr;  // field of each tile (workspaces for several fields)
     CUtensorMap *d_tmaps = nullptr;  // TMA maps of each field's f, f_hat, g, descriptors (TMAPS per field slot)
     uint32_t *cp_key[2] = {nullptr, nullptr};
     unsigned long long *cp_ent[2] = {nullptr, nullptr};
@@ -193,6 +194,7 @@ struct exactz_workspace {
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[6] = {0, 0, 0, 0, 0, 0};
     uint64_t layout_hash = 0;  // dims of the previous run (padding must hold k = 0, no CP bits)
+    uint64_t tile_field_key = 0;  // layout the tile-field table was filled for
     exactz_stats stats{};
     cudaEvent_t ev[9] = {};
     cudaEvent_t kev[4] = {};  // around the loop kernels of one host-driven pass (profiling)
@@ -325,6 +327,7 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->pin_tile_bits, T / 32 + 1);
     AL(ws->pin_pair_arena, 2 * C);
     AL(ws->fids, L.nfields);
+    if (L.nfields > 1) AL(ws->tile_field, L.total_tiles);
     AL(ws->d_tmaps, (uint64_t)TMAPS * L.nfields);
     AL(ws->cp_key[0], C);
     AL(ws->cp_key[1], C);
@@ -703,6 +706,18 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemsetAsync(ws->apply_flag, 0, L.total_tiles, s));
     Dev D = make_dev(ws, L);
     D.events = events ? 1u : 0u;
+    if (nf > 1 && ws->tile_field) {  // the field of each tile: one load instead of a search over the fields
+        if (ws->tile_field_key != hsh) {
+            std::vector<uint32_t> tf(L.total_tiles);
+            for (uint32_t i = 0; i < nf; i++) {
+                const uint64_t t0 = L.fd[i].tbase, nt = (uint64_t)L.fd[i].tnx * L.fd[i].tny * L.fd[i].tnz;
+                for (uint64_t t = 0; t < nt; t++) tf[t0 + t] = i;
+            }
+            CK(cudaMemcpy(ws->tile_field, tf.data(), 4ull * L.total_tiles, cudaMemcpyHostToDevice));
+            ws->tile_field_key = hsh;
+        }
+        D.tile_field = ws->tile_field;
+    }
     const int frontier = opt.mode != EXACTZ_MODE_PLAIN;
     const bool prof = opt.profile != 0;
     auto mark = [&](int i) {

@@ -86,22 +86,39 @@ __device__ __forceinline__ void warp_mark_nb_tiles(uint32_t nb, uint32_t tile, u
     }
 }
 
-// Request the closed-star ranks in m of vertex (x, y, z) of field F (every
+// The field constants a tile's request emission needs, held in registers (the
+// FieldDesc lives in global memory, which the emission's atomics and stores
+// might alias, so reading it inside the loop would reload it every time).
+struct EmitGeo {
+    uint32_t nx, ny, tnx, tny, N;
+    uint64_t vbase, wbase, tbase;
+};
+
+// Offset + 1 (0, 1 or 2) along one axis of every rank, two bits per rank.
+__host__ __device__ constexpr uint32_t rank_axis_bits(int axis)
+{
+    uint32_t m = 0;
+    for (int r = 0; r < 15; r++) m |= (uint32_t)((axis == 0 ? rdx(r) : (axis == 1 ? rdy(r) : rdz(r))) + 1) << (2 * r);
+    return m;
+}
+
+// Request the closed-star ranks in m of vertex (x, y, z) of field G (every
 // rank in m names a vertex of the field).  PINNED keeps only targets already
 // at the lossless bound (the residual count).
 template <bool PINNED>
-__device__ __forceinline__ void emit_targets(const Dev &D, const FieldDesc &F, uint32_t x, uint32_t y, uint32_t z,
+__device__ __forceinline__ void emit_targets(const Dev &D, const EmitGeo &G, uint32_t x, uint32_t y, uint32_t z,
                                              uint32_t m)
 {
+    constexpr uint32_t BX = rank_axis_bits(0), BY = rank_axis_bits(1), BZ = rank_axis_bits(2);
     while (m) {
         const int r = __ffs(m) - 1;
         m &= m - 1;
-        const uint32_t X = (uint32_t)((int)x + rdx(r)), Y = (uint32_t)((int)y + rdy(r)),
-                       Z = (uint32_t)((int)z + rdz(r));
-        const uint64_t row = (uint64_t)Z * F.ny + Y;
-        if (PINNED && (D.desc[F.vbase + row * F.nx + X] >> D_K_SHIFT) <= F.N) continue;
-        atomicOr(&D.reqw[F.wbase + row * F.tnx + (X >> 5)], 1u << (X & 31));
-        const uint32_t tile = (uint32_t)(F.tbase + (X >> 5) + (uint64_t)F.tnx * (Y / TY + (uint64_t)F.tny * (Z / TZ)));
+        const uint32_t X = x + ((BX >> (2 * r)) & 3u) - 1u, Y = y + ((BY >> (2 * r)) & 3u) - 1u,
+                       Z = z + ((BZ >> (2 * r)) & 3u) - 1u;
+        const uint64_t row = (uint64_t)Z * G.ny + Y;
+        if (PINNED && (D.desc[G.vbase + row * G.nx + X] >> D_K_SHIFT) <= G.N) continue;
+        atomicOr(&D.reqw[G.wbase + row * G.tnx + (X >> 5)], 1u << (X & 31));
+        const uint32_t tile = (uint32_t)(G.tbase + (X >> 5) + (uint64_t)G.tnx * (Y / TY + (uint64_t)G.tny * (Z / TZ)));
         if (!D.apply_flag[tile]) D.apply_flag[tile] = 1;
     }
 }
@@ -277,10 +294,10 @@ struct TileGeo {
     int x0, y0, z0;
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
+__device__ __forceinline__ TileGeo tile_geo_of(const Dev &D, uint32_t tile, uint32_t fid)
 {
     TileGeo G;
-    G.fid = field_of_tile(D, tile);
+    G.fid = fid;
     const FieldDesc &F = D.fields[G.fid];
     const uint32_t lt = (uint32_t)(tile - F.tbase);
     const uint32_t rest = fdiv(lt, F.div_tnx);
@@ -290,6 +307,27 @@ __device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
     G.y0 = (int)(ty * TY);
     G.z0 = (int)(tz * TZ);
     return G;
+}
+
+__device__ __forceinline__ TileGeo tile_geo(const Dev &D, uint32_t tile)
+{
+    return tile_geo_of(D, tile, field_of_tile(D, tile));
+}
+
+// A staged tile's position and the constants of its field, published in
+// shared memory by the warp that stages it, so that the checking threads read
+// them there instead of each loading the field table from global memory.
+struct TileInfo {
+    TileGeo G;
+    uint32_t nx, ny, nz, tnx, tny, N;
+    uint64_t vbase, wbase, tbase;
+    float xi;
+    float *g;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const TileGeo &G, const FieldDesc &F)
+{
+    return TileInfo{G, F.nx, F.ny, F.nz, F.tnx, F.tny, F.N, F.vbase, F.wbase, F.tbase, F.xi, F.g};
 }
 
 // One tile per block iteration: the tile's values plus a one-vertex halo are
@@ -315,7 +353,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     __shared__ uint32_t s_rw[NB][ROWS];   // dirty row words of the tile (CHECK_LIST)
     __shared__ uint16_t s_vis[MODE == SM_CHECK_LIST ? TILE_V : 1];  // the tile's dirty vertices (row << 5 | lx)
     __shared__ uint32_t s_tile[2];        // the tile staged in each buffer
-    __shared__ TileGeo s_geo[NB];         // its position
+    __shared__ TileInfo s_ti[NB];         // its position and field constants
 
     for (int j = threadIdx.x; j < 512; j += SCTA) smulti[j] = D.multi[j];
     if (threadIdx.x == 0) {
@@ -333,28 +371,50 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     // Stage tile into buffer b: the halo rows (one warp per row of HXP values,
     // x0-1 .. x0+TX) and, for CHECK_LIST, the tile's dirty row words.
     auto stage = [&](const uint32_t tile, const int b) {
-        const TileGeo G = tile_geo(D, tile);
-        if (threadIdx.x == 0) s_geo[b] = G;
-        const FieldDesc &F = D.fields[G.fid];
+        const uint32_t fid = field_of_tile(D, tile);
+        if (D.fields[fid].tma) {  // the whole halo (NaN outside the field) in one TMA load per array
+            tma_pending |= 1u << b;
+            if (warp == 0) {  // warp 0 alone: the geometry, the dirty words and the TMA loads
+                const TileGeo G = tile_geo_of(D, tile, fid);
+                const FieldDesc &F = D.fields[fid];
+                const uint32_t ny = F.ny, nz = F.nz;
+                if (MODE == SM_CHECK_LIST && lane < ROWS) {
+                    const uint32_t y = (uint32_t)G.y0 + lane % TY, z = (uint32_t)G.z0 + lane / TY;
+                    if (y < ny && z < nz)
+                        cp_async4(&s_rw[b][lane], D.dirty + F.wbase + ((uint64_t)z * ny + y) * F.tnx + G.tx);
+                    else s_rw[b][lane] = 0;
+                }
+                if (lane == 0) {
+                    s_ti[b] = tile_info(G, F);
+                    const CUtensorMap *maps = D.tmaps + (uint64_t)TMAPS * G.fid;
+                    fence_proxy_async();  // the buffer's earlier reads come first
+                    mbar_expect_tx(&s_mbar[b], (MODE == SM_SETUP ? 2u : 1u) * (uint32_t)(HALO_N * sizeof(float)) +
+                                                   (CHECK ? (uint32_t)(TILE_V * sizeof(uint32_t)) : 0u));
+                    tma_load_3d(sa[b], maps + ((MODE == SM_SETUP || MODE == SM_CLASSIFY) ? 0 : 2), G.x0 - XOFF,
+                                G.y0 - 1, G.z0 - 1, &s_mbar[b]);
+                    if (MODE == SM_SETUP) tma_load_3d(sb[b], maps + 1, G.x0 - XOFF, G.y0 - 1, G.z0 - 1, &s_mbar[b]);
+                    if (CHECK) tma_load_3d(s_desc[b], maps + 3, G.x0, G.y0, G.z0, &s_mbar[b]);
+                }
+            }
+            return;
+        }
+        // fields without tensor maps: every thread copies its share with cp.async
+        const TileGeo G = tile_geo_of(D, tile, fid);
+        const FieldDesc &F = D.fields[fid];
+        if (threadIdx.x == 0) s_ti[b] = tile_info(G, F);
         const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
         if (MODE == SM_CHECK_LIST && threadIdx.x < ROWS) {
             const uint32_t y = (uint32_t)G.y0 + threadIdx.x % TY, z = (uint32_t)G.z0 + threadIdx.x / TY;
             if (y < ny && z < nz) cp_async4(&s_rw[b][threadIdx.x], D.dirty + F.wbase + ((uint64_t)z * ny + y) * F.tnx + G.tx);
             else s_rw[b][threadIdx.x] = 0;
         }
-        if (F.tma) {  // the whole halo (NaN outside the field) in one TMA load per array
-            tma_pending |= 1u << b;
-            if (threadIdx.x == 0) {
-                const CUtensorMap *maps = D.tmaps + (uint64_t)TMAPS * G.fid;
-                fence_proxy_async();  // the buffer's earlier reads come first
-                mbar_expect_tx(&s_mbar[b], (MODE == SM_SETUP ? 2u : 1u) * (uint32_t)(HALO_N * sizeof(float)) +
-                                               (CHECK ? (uint32_t)(TILE_V * sizeof(uint32_t)) : 0u));
-                tma_load_3d(sa[b], maps + ((MODE == SM_SETUP || MODE == SM_CLASSIFY) ? 0 : 2), G.x0 - XOFF, G.y0 - 1,
-                            G.z0 - 1, &s_mbar[b]);
-                if (MODE == SM_SETUP) tma_load_3d(sb[b], maps + 1, G.x0 - XOFF, G.y0 - 1, G.z0 - 1, &s_mbar[b]);
-                if (CHECK) tma_load_3d(s_desc[b], maps + 3, G.x0, G.y0, G.z0, &s_mbar[b]);
+        if (CHECK) {  // the tile's descriptors, one row of TX per warp at a time
+            const uint32_t X = (uint32_t)G.x0 + lane;
+            for (int row = warp; row < ROWS; row += STWARPS) {
+                const uint32_t Y = (uint32_t)G.y0 + row % TY, Z = (uint32_t)G.z0 + row / TY;
+                if (X < nx && Y < ny && Z < nz)
+                    cp_async4(&s_desc[b][row * TX + lane], D.desc + F.vbase + ((uint64_t)Z * ny + Y) * nx + X);
             }
-            return;
         }
         const float *A = (MODE == SM_SETUP || MODE == SM_CLASSIFY) ? F.f : F.g;
         const float *B = F.fhat;
@@ -418,12 +478,11 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
 
     // Check (or classify) the staged tile in buffer b; ends with a barrier.
     auto process = [&](const uint32_t tile, const int b) {
-        const TileGeo G = s_geo[b];
-        const uint32_t fid = G.fid, tx = G.tx;
-        const int x0 = G.x0, y0 = G.y0, z0 = G.z0;
-        const FieldDesc &F = D.fields[fid];
-        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz, tnx = F.tnx;
-        const uint64_t vbase = F.vbase;
+        const TileInfo &T = s_ti[b];
+        const uint32_t fid = T.G.fid, tx = T.G.tx;
+        const int x0 = T.G.x0, y0 = T.G.y0, z0 = T.G.z0;
+        const uint32_t nx = T.nx, ny = T.ny, nz = T.nz, tnx = T.tnx;
+        const uint64_t vbase = T.vbase;
         const float *S = sa[b];
         const uint32_t *RW = s_rw[b];
         // CHECK_LIST: the tile's dirty vertices are listed in shared memory in
@@ -434,7 +493,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
         if (MODE == SM_CHECK_LIST) {
             if (threadIdx.x < ROWS && RW[threadIdx.x]) {  // the dirty bits are taken: clear them
                 const uint32_t y = (uint32_t)y0 + threadIdx.x % TY, z = (uint32_t)z0 + threadIdx.x / TY;
-                D.dirty[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = 0;
+                D.dirty[T.wbase + ((uint64_t)z * ny + y) * tnx + tx] = 0;
             }
             const uint32_t rc = lane < ROWS ? __popc(RW[lane]) : 0u;
             uint32_t incl = rc;
@@ -454,6 +513,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
             if (warp == 0) nvisits += (uint32_t)nvisit;
             __syncthreads();
         }
+        const EmitGeo EG{nx, ny, tnx, T.tny, T.N, vbase, T.wbase, T.tbase};
         // index of the tile's first vertex (x0, y0, z0) in the field
         const uint64_t nxy = (uint64_t)nx * ny;
         const uint64_t tfirst = ((uint64_t)z0 * ny + (uint64_t)y0) * nx + (uint64_t)x0;
@@ -508,27 +568,27 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
                         const float fv = S[c], hv = SB[c];
                         uint32_t e = 0;
                         if (!isfinite(fv) || !isfinite(hv)) e = ERR_NONFINITE;
-                        else if (hv < __fsub_rn(fv, F.xi) || hv > __fadd_rn(fv, F.xi)) e = ERR_BOUND;
+                        else if (hv < __fsub_rn(fv, T.xi) || hv > __fadd_rn(fv, T.xi)) e = ERR_BOUND;
                         if (e) atomicOr(&s_err, e);
                         D.desc[vbase + i] = d;  // edit count k = 0 in the top byte
-                        F.g[i] = hv;
+                        T.g[i] = hv;
                         if (D.events && (mn || mxx)) D.cp_rank[vbase + i] = 0;  // no linked saddle yet
                         Stn sg = stencil15(SB, c);
                         sg.valid = valid;
                         req = request_mask(smulti, d, sg);
                     }
                 } else {
-                    const uint32_t d = F.tma ? s_desc[b][(lz * TY + ly) * TX + lx] : __ldg(&D.desc[vbase + i]);
+                    const uint32_t d = s_desc[b][(lz * TY + ly) * TX + lx];
                     Stn sg = stencil15(S, c);
                     sg.valid = valid;
                     req = request_mask(smulti, d, sg);
                 }
             }
-            if (MODE != SM_CLASSIFY && req) emit_targets<MODE == SM_PINNED>(D, F, x, y, z, req);
+            if (MODE != SM_CLASSIFY && req) emit_targets<MODE == SM_PINNED>(D, EG, x, y, z, req);
             if (MODE == SM_SETUP) {
                 const uint32_t w = __ballot_sync(0xffffffffu, listed);
                 if (lane == 0 && y < ny && z < nz)
-                    D.cpwords[F.wbase + ((uint64_t)z * ny + y) * tnx + tx] = w;
+                    D.cpwords[T.wbase + ((uint64_t)z * ny + y) * tnx + tx] = w;
                 if (D.events) {
                     const uint32_t c = __popc(__ballot_sync(0xffffffffu, cp));
                     if (lane == 0 && c) atomicAdd(&s_ncp, c);
