@@ -56,9 +56,22 @@ sys.path.insert(0, ROOT)
 METRIC = "corrected GB/s on 1 B300 to fixpoint, batched vs plain; % HBM peak; p99 ms"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-TILE_V = 32 * 4 * 4  # vertices of a tile
-CHECK_TILE_BYTES = TILE_V * 8 + 16 * 4  # g and descriptor of a checked tile's vertices + its dirty row words
 APPLY_REQUEST_BYTES = 24  # descriptor, f, g, CP rank read; g and descriptor written, per requested vertex
+
+
+def tile_shape(ez):
+    """The library's tile (x, y, z sizes), from its version string ("tile AxBxC")."""
+    m = re.search(r"tile (\d+)x(\d+)x(\d+)", ez.version())
+    if not m:
+        raise SystemExit("the library does not state its tile shape")
+    return tuple(int(v) for v in m.groups())
+
+
+def check_tile_bytes(ez):
+    """Algorithmic bytes of one checked tile: the g values and descriptors of
+    its vertices (4 + 4 bytes each) and its dirty row words (one per row)."""
+    tx, ty, tz = tile_shape(ez)
+    return tx * ty * tz * 8 + ty * tz * 4
 
 
 def parse():
@@ -210,8 +223,9 @@ def kernel_source_hash() -> str:
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source (null otherwise)."""
+    """DRAM bytes (read + written) per checked tile of `kernel` from the committed
+    ncu summary (profiles/ncu_traffic.md), if it was taken on the current kernel
+    source and a workload of the same kind (null otherwise)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     if not os.path.exists(path):
         return None
@@ -445,34 +459,11 @@ def run_single(a):
     st = ws.stats()
     stages = {k: v / a.steps for k, v in stage_tot.items()}
 
-    # Roofline of the dominant kernel, the frontier vertex check
-    # (k_stencil<CHECK_LIST>, about 45% of a correction's kernel time): K more
-    # corrections in the host-driven frontier form, which runs the same passes
-    # as the graph loop, with CUDA events on the launching stream around every
-    # launch of the loop kernels.
+    # Roofline of the dominant kernel, the frontier vertex check, from K more
+    # corrections in the host-driven frontier form (the graph loop's passes)
     peak, peak_kind = peaks()
-    chk_ms = chk_tiles = chk_launches = 0.0
-    ker_ms = {"check": 0.0, "pairs": 0.0, "apply": 0.0}
-    for _ in range(a.steps):
-        step("frontier", True)
-        sf = ws.stats()
-        chk_ms += sf["loop_kernel_ms"]["check"]
-        chk_tiles += sf["sum_tiles"]
-        chk_launches += sf["loop_passes"]
-        for k in ker_ms:
-            ker_ms[k] += sf["loop_kernel_ms"][k]
-    launch_ms = chk_ms / max(1.0, chk_launches)
-    # algorithmic bytes per checked tile: the g values and descriptors of its
-    # 512 vertices (4 + 4 bytes each) and its 16 dirty row words
-    alg_bytes = chk_tiles / max(1.0, chk_launches) * (TILE_V * 8 + 16 * 4)
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
-    roof = {"bound": "hbm", "kernel": "k_stencil<CHECK_LIST> (frontier vertex check)", "achieved": achieved,
-            "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic("k_stencil<CHECK_LIST>", c["name"]), "algorithmic_bytes": alg_bytes,
-            "limiter": ncu_limiter("k_stencil<CHECK_LIST>"),
-            "launch_ms": launch_ms, "launches": int(chk_launches),
-            "measured": f"{a.steps} frontier-mode corrections, CUDA events around each launch",
-            "loop_kernel_ms_per_correction": {k: v / a.steps for k, v in ker_ms.items()}}
+    roof = frontier_roofline(ez, ws, [f], [fh], [xi], [g], [ebuf], a.steps, peak, peak_kind, c["kind"],
+                             events=a.events)
 
     storage = edit_storage(ez, r, n, 5) if not a.no_extras else None
     extras = {"edit_storage": storage,
@@ -492,7 +483,7 @@ def run_single(a):
     # edit.  (The residual check on pinned stars is left out.)
     ncp = float(r["n_critical"])
     terms = {"setup": 16.0 * n, "cp_list": n / 8 + 12.0 * ncp, "sort": (4 * 24 + 8) * ncp,
-             "check": float(st["sum_tiles"]) * (TILE_V * 8 + 16 * 4), "pairs": 8.0 * st["sum_pairs"],
+             "check": float(st["sum_tiles"]) * check_tile_bytes(ez), "pairs": 8.0 * st["sum_pairs"],
              "apply": 24.0 * st["sum_requests"], "edit_list": 4.0 * n + 24.0 * r["n_edits"]}
     tot = sum(terms.values())
     extras["step_hbm"] = {"bytes": tot, "gbs": tot / (ms / 1e3) / 1e9, "frac": tot / (ms / 1e3) / 1e9 / peak,
@@ -692,31 +683,46 @@ def run_nsweep(a):
 
 
 # ---------------------------------------------------------------- many fields (the default workload)
-def frontier_roofline(ws, fs, fhs, xis, gs, ebufs, reps: int, peak: float, peak_kind: str, workload: str,
+def frontier_roofline(ez, ws, fs, fhs, xis, gs, ebufs, reps: int, peak: float, peak_kind: str, workload: str,
                       **kw) -> dict:
     """Roofline of the dominant kernel, the frontier vertex check
     (k_stencil<CHECK_LIST>): `reps` more corrections in the host-driven
     frontier form, which runs the same passes as the graph loop, with CUDA
     events on the launching stream around every launch of the loop kernels.
     Algorithmic bytes per checked tile: the g values and descriptors of its
-    512 vertices (4 + 4 bytes each) and its 16 dirty row words."""
-    chk_ms = tiles = passes = 0.0
+    vertices (4 + 4 bytes each) and its dirty row words (check_tile_bytes).
+    Beside it, the same time against 8 bytes per visited (dirty) vertex plus
+    the dirty words, the bytes of the vertices actually checked."""
+    chk_ms = tiles = passes = visits = 0.0
     ker = {"check": 0.0, "pairs": 0.0, "apply": 0.0}
     for _ in range(reps):
         ws.correct(fs, fhs, xis, mode="frontier", profile=True, g_out=gs, edit_bufs=ebufs, **kw)
         st = ws.stats()
         chk_ms += st["loop_kernel_ms"]["check"]
         tiles += st["sum_tiles"]
+        visits += st["sum_visits"]
         passes += st["loop_passes"]
         for k in ker:
             ker[k] += st["loop_kernel_ms"][k]
     launch_ms = chk_ms / max(1.0, passes)
-    alg = tiles / max(1.0, passes) * CHECK_TILE_BYTES
+    tb = check_tile_bytes(ez)
+    alg = tiles / max(1.0, passes) * tb
     achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+    tx, ty, tz = tile_shape(ez)
+    vbytes = (visits * 8 + tiles * ty * tz * 4) / max(1.0, passes)
+    per_visit = {"algorithmic_bytes": vbytes, "achieved": vbytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0,
+                 "visits_per_launch": visits / max(1.0, passes)}
+    per_visit["frac"] = per_visit["achieved"] / peak
+    per_tile = ncu_traffic("k_stencil<CHECK_LIST>", workload)
+    traffic = per_tile * tiles / max(1.0, passes) if per_tile is not None else None
     return {"bound": "hbm", "kernel": "k_stencil<CHECK_LIST> (frontier vertex check)", "achieved": achieved,
             "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic("k_stencil<CHECK_LIST>", workload), "algorithmic_bytes": alg,
+            "traffic": traffic, "traffic_source": ("DRAM bytes per checked tile from profiles/ncu_traffic.md "
+                                                   f"({workload}) x tiles per launch") if per_tile else None,
+            "algorithmic_bytes": alg,
             "limiter": ncu_limiter("k_stencil<CHECK_LIST>"), "launch_ms": launch_ms, "launches": int(passes),
+            "tile": f"{tx}x{ty}x{tz}", "bytes_per_checked_tile": tb, "tiles_per_launch": tiles / max(1.0, passes),
+            "per_visited_vertex": per_visit,
             "measured": f"{reps} frontier-mode corrections, CUDA events around each launch",
             "loop_kernel_ms_per_correction": {k: v / reps for k, v in ker.items()}}
 
@@ -750,7 +756,7 @@ def octave_extra(a, ez, dev, peak, peak_kind) -> dict:
         out[mode] = {"ms": ms, "gbs": 4.0 * n / (ms / 1e3) / 1e9, "iterations": r["iterations"],
                      "status": r["status_name"], "n_edits": r["n_edits"], "residual_violations": r["residual"]}
     out["graph_vs_plain"] = out["plain"]["ms"] / out["graph"]["ms"]
-    out["roofline"] = frontier_roofline(ws, [f], [fh], [xi], [g], [ebuf], 1, peak, peak_kind, c["name"])
+    out["roofline"] = frontier_roofline(ez, ws, [f], [fh], [xi], [g], [ebuf], 1, peak, peak_kind, "octave")
     ws.close()
     del f, fh, g, ebuf
     torch.cuda.empty_cache()
@@ -836,8 +842,7 @@ def run_batched(a):
               "n_edits": sum(r["n_edits"] for r in rs), "n_lossless": sum(r["n_lossless"] for r in rs),
               "mvertices_per_s": n_total / (ms / 1e3) / 1e6, "generation_s": gen_s,
               "workspace_gib": ws.nbytes / 2 ** 30}
-    roof = frontier_roofline(ws, fs, fhs, xis, gs, ebufs, max(1, min(a.steps, 3)), peak, peak_kind,
-                             f"batched{a.fields}")
+    roof = frontier_roofline(ez, ws, fs, fhs, xis, gs, ebufs, max(1, min(a.steps, 3)), peak, peak_kind, "batched")
     batched(profile=True)
     extras["stage_ms"] = ws.stats()["stage_ms"]
 

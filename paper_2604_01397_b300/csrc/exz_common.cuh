@@ -17,7 +17,7 @@ namespace exz {
 
 // ---------------------------------------------------------------- geometry
 constexpr int TX = 32;   // tile width: one warp per tile row, one cp-bitmap word
-constexpr int TY = 4;
+constexpr int TY = 8;
 constexpr int TZ = 4;
 constexpr int TILE_V = TX * TY * TZ;
 // Halo tile in shared memory: HY x HZ rows of HXP floats.  Slot j of a row

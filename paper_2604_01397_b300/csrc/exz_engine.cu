@@ -1279,7 +1279,7 @@ int exactz_cp_order(const float *f, exactz_dims d, uint64_t *order_out, uint64_t
 
 const char *exactz_version(void)
 {
-    return "exactz-b300 0.1 (sm_103a; tile 32x4x4; stencil/sort/apply kernels; graph while-loop)";
+    return "exactz-b300 0.2 (sm_103a; tile 32x8x4; stencil/sort/apply kernels; graph while-loop)";
 }
 
 // Scratch of the edit-stream calls: block counts, their offsets, the total

@@ -1476,7 +1476,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
             const bool sel = k < nvisit && !err;
             int row = 0;  // the last row whose first request number is <= k
 #pragma unroll
-            for (int step = 8; step >= 1; step >>= 1) {
+            for (int step = ROWS / 2; step >= 1; step >>= 1) {
                 const uint32_t pe = __shfl_sync(0xffffffffu, excl, row + step);
                 if ((int)pe <= k) row += step;
             }
