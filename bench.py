@@ -803,10 +803,10 @@ def run_batched(a):
     ebufs = [torch.empty((c, 16), dtype=torch.uint8, device=dev) for c in caps]
     stream = torch.cuda.current_stream()
 
-    def batched(mode="graph", profile=False):
+    def batched(mode=a.mode, profile=False):
         return ws.correct(fs, fhs, xis, mode=mode, g_out=gs, edit_bufs=ebufs, profile=profile)
 
-    tuning = ws.autotune(fs, fhs, xis, repeats=1) if not a.no_autotune else ws.tuning()
+    tuning = ws.autotune(fs, fhs, xis, repeats=1, mode=a.mode) if not a.no_autotune else ws.tuning()
     for _ in range(max(3, a.warmup)):
         rs = batched()
     if dist:
@@ -953,7 +953,7 @@ def run_batched(a):
             "warmup": max(3, a.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": batched_describe(a.fields), "vertices": n_total,
-                       "input_bytes": 4 * n_total, "mode": "graph, all fields in one run (exactz_ws_correct)",
+                       "input_bytes": 4 * n_total, "mode": f"{a.mode}, all fields in one run (exactz_ws_correct)",
                        "l2": "inputs larger than L2 (3.0 GiB of input per step)",
                        "parallelism": f"replicas x{world}", "tuning": tuning},
             "batched_vs_plain": vs_plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -72,6 +72,11 @@ constexpr uint32_t D_CP = 1u << 23;
 constexpr uint32_t D_K_SHIFT = 24;
 constexpr uint32_t D_F_MASK = 0x00FFFFFFu;
 
+// Tile loads by TMA (FieldDesc::tma bits): the halos of f and f_hat (set-up),
+// the halo of g (checks; from gm where the field has one) and the tile's
+// descriptors (checks); the others are staged with cp.async.
+constexpr uint32_t TMA_SETUP = 1, TMA_G = 2, TMA_DESC = 4;
+
 // Field errors (FieldState::err bits)
 constexpr uint32_t ERR_NONFINITE = 1, ERR_BOUND = 2;
 // Status codes (match the C ABI)
@@ -109,14 +114,16 @@ struct FieldDesc {
     uint64_t n;
     uint32_t tnx, tny, tnz;        // tiles per axis (tnx = cp-bitmap words per row)
     uint32_t mirror;               // 1: the field is the point reflection of -f (increasing edits)
-    uint32_t tma;                  // 1: tiles are loaded with the tensor maps Dev::tmaps[TMAPS * field slot ..]
-    uint32_t pad1;
+    uint32_t tma;                  // TMA_* bits: which tile loads use the tensor maps Dev::tmaps[TMAPS * field slot ..]
+    uint32_t pitch;                // row pitch (vertices) of gm
     uint64_t tbase;                // first global tile id
     uint64_t vbase;                // arena offset (vertices): k, desc, cp_rank, request bits
     uint64_t wbase;                // cp-bitmap offset (words)
     const float *f;
     const float *fhat;
     float *g;
+    float *gm;                     // g with rows padded to 16 bytes (fields whose g has no tensor map), or null:
+                                   // while it is set, g lives there until k_unmirror copies it into g
     float xi, delta;
     uint64_t max_iters;
     struct EditRec *edits;  // output edit list (device), may be null

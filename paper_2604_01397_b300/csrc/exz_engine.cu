@@ -82,6 +82,11 @@ struct Layout {
     uint32_t total_tiles = 0;
     std::vector<FieldDesc> fd;
     std::vector<uint64_t> cpc;  // per field: sum of the vertex counts before it (CP capacity offset)
+    // fields whose rows are not a multiple of 16 bytes: the offset and row
+    // pitch of their padded copy of g (pitch 0: none)
+    std::vector<uint64_t> moff;
+    std::vector<uint32_t> mpitch;
+    uint64_t total_mirror = 0;
 };
 
 int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
@@ -90,6 +95,8 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
     L.nfields = nf;
     L.fd.assign(nf, FieldDesc{});
     L.cpc.assign(nf, 0);
+    L.moff.assign(nf, 0);
+    L.mpitch.assign(nf, 0);
     uint64_t v = 0, w = 0, t = 0, real = 0;
     for (uint32_t i = 0; i < nf; i++) {
         const uint64_t nx = d[i].nx, ny = d[i].ny, nz = d[i].nz;
@@ -118,6 +125,11 @@ int make_layout(uint32_t nf, const exactz_dims *d, Layout &L)
         w += ny * nz * F.tnx;
         L.cpc[i] = real;
         real += n;
+        if (nx % 4 != 0) {
+            L.mpitch[i] = (uint32_t)round_up(nx, 4);
+            L.moff[i] = L.total_mirror;
+            L.total_mirror = round_up(L.total_mirror + (uint64_t)L.mpitch[i] * ny * nz, 64);
+        }
     }
     if (t >= (1ull << 32) || real >= (1ull << 32)) return EXACTZ_EINVAL;
     L.total_v = round_up(v, VBLOCK);
@@ -210,6 +222,8 @@ struct exactz_workspace {
     unsigned long long *ev_room_off = nullptr;   // its exclusive prefix sums
     uint8_t *ev_tdone = nullptr;                 // per tile: every path end found
     float *refl = nullptr;                       // increasing edits: the reflected -f and -f_hat
+    float *g_mirror = nullptr;                   // padded copies of g (fields whose rows are not 16-byte multiples)
+    uint64_t cap_mirror = 0;
     uint64_t ev_cap[9] = {};  // E, start, cnt, list, radj, room, room_off, tdone, refl (elements)
     // set by the allocation-free entry point: every buffer is carved from its
     // fixed scratch, and a request to grow one fails with EXACTZ_ENOMEM
@@ -328,6 +342,10 @@ int ws_alloc(exactz_workspace *ws, const Layout &L)
     AL(ws->pin_pair_arena, 2 * C);
     AL(ws->fids, L.nfields);
     if (L.nfields > 1) AL(ws->tile_field, L.total_tiles);
+    if (L.total_mirror) {
+        AL(ws->g_mirror, L.total_mirror);
+        ws->cap_mirror = L.total_mirror;
+    }
     AL(ws->d_tmaps, (uint64_t)TMAPS * L.nfields);
     AL(ws->cp_key[0], C);
     AL(ws->cp_key[1], C);
@@ -682,9 +700,17 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         for (uint32_t i = 0; i < nf; i++) {
             FieldDesc &F = L.fd[i];
             CUtensorMap *m = &maps[(uint64_t)TMAPS * i];
-            F.tma = make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) && make_map(m + 2, F.g, F, true) &&
-                    make_map(m + 3, ws->desc + F.vbase, F, false);
-            if (getenv("EXACTZ_DEBUG")) fprintf(stderr, "exactz: field %u halo loads by %s\n", i, F.tma ? "TMA" : "cp.async");
+            F.tma = (make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) ? TMA_SETUP : 0u) |
+                    (make_map(m + 3, ws->desc + F.vbase, F, false) ? TMA_DESC : 0u);
+            if (make_map(m + 2, F.g, F, true)) {
+                F.tma |= TMA_G;
+            } else if (ws->g_mirror && L.mpitch[i] && L.total_mirror <= ws->cap_mirror) {  // the checks read a padded copy of g
+                F.gm = ws->g_mirror + L.moff[i];
+                F.pitch = L.mpitch[i];
+                if (make_map(m + 2, F.gm, F, true, F.pitch)) F.tma |= TMA_G;
+                else F.gm = nullptr;
+            }
+            if (getenv("EXACTZ_DEBUG")) fprintf(stderr, "exactz: field %u tile loads by TMA: %x\n", i, F.tma);
         }
         CK(cudaMemcpyAsync(ws->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, s));
     }
@@ -777,6 +803,9 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         }
     }
     mark(5);
+    bool padded = false;
+    for (uint32_t i = 0; i < nf; i++) padded = padded || L.fd[i].gm;
+    if (padded) launch_unmirror(D, s);  // g of the fields kept in padded copies, in place for what follows
     // residual violations on pinned vertices and status; beside them the edit
     // list (the edit counts are final; the residual check writes only request
     // bits, flags and counters the edit list does not read)
@@ -797,7 +826,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     if (inc)  // g back in the caller's coordinates and sign
         for (uint32_t i = 0; i < nf; i++) launch_reflect_out(L.fd[i].g, ws->desc + L.fd[i].vbase, L.fd[i].n, s);
     mark(7);
-    launches += 4 + (opt.want_edit_list ? 3 : 1) + (inc ? 3 * nf : 0);
+    launches += 4 + (padded ? 1 : 0) + (opt.want_edit_list ? 3 : 1) + (inc ? 3 * nf : 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ws->h_fst, ws->d_fst, sizeof(FieldState) * nf, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -901,8 +930,9 @@ const uint32_t *exz::host_multi_table()
 // (x0 - XOFF); the map needs rows of a multiple of 16 bytes (nx % 4 == 0) and a
 // 16-byte aligned base.  Returns false (the field keeps the cp.async halo
 // loads) where a map cannot be made.
-bool exz::make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo)
+bool exz::make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo, uint32_t pitch)
 {
+    if (!pitch) pitch = F.nx;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -915,14 +945,14 @@ bool exz::make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool 
             fprintf(stderr, "exactz: cuTensorMapEncodeTiled not found (%d, %d)\n", (int)e, (int)q);
         cudaGetLastError();
     });
-    if (!encode || !base || (F.nx % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) {
+    if (!encode || !base || (pitch % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) {
         if (getenv("EXACTZ_DEBUG"))
             fprintf(stderr, "exactz: no halo map (encoder %s, nx %u, base %p)\n", encode ? "found" : "missing", F.nx,
                     (const void *)base);
         return false;
     }
     const cuuint64_t dims[3] = {F.nx, F.ny, F.nz};
-    const cuuint64_t strides[2] = {4ull * F.nx, 4ull * F.nx * F.ny};
+    const cuuint64_t strides[2] = {4ull * pitch, 4ull * pitch * F.ny};
     const cuuint32_t box[3] = {halo ? (cuuint32_t)HXP : (cuuint32_t)TX, halo ? (cuuint32_t)HY : (cuuint32_t)TY,
                                halo ? (cuuint32_t)HZ : (cuuint32_t)TZ};
     const cuuint32_t elem[3] = {1, 1, 1};

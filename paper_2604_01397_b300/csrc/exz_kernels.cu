@@ -323,11 +323,13 @@ struct TileInfo {
     uint64_t vbase, wbase, tbase;
     float xi;
     float *g;
+    float *gm;  // the padded copy of g, or null
+    uint32_t pitch;
 };
 
 __device__ __forceinline__ TileInfo tile_info(const TileGeo &G, const FieldDesc &F)
 {
-    return TileInfo{G, F.nx, F.ny, F.nz, F.tnx, F.tny, F.N, F.vbase, F.wbase, F.tbase, F.xi, F.g};
+    return TileInfo{G, F.nx, F.ny, F.nz, F.tnx, F.tny, F.N, F.vbase, F.wbase, F.tbase, F.xi, F.g, F.gm, F.pitch};
 }
 
 // One tile per block iteration: the tile's values plus a one-vertex halo are
@@ -372,8 +374,21 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     // x0-1 .. x0+TX) and, for CHECK_LIST, the tile's dirty row words.
     auto stage = [&](const uint32_t tile, const int b) {
         const uint32_t fid = field_of_tile(D, tile);
-        if (D.fields[fid].tma) {  // the whole halo (NaN outside the field) in one TMA load per array
+        const uint32_t tmab = D.fields[fid].tma;
+        const bool tma_halo = (tmab & ((MODE == SM_SETUP || MODE == SM_CLASSIFY) ? TMA_SETUP : TMA_G)) != 0;
+        const bool tma_desc = CHECK && (tmab & TMA_DESC) != 0;
+        if (tma_halo) {  // the whole halo (NaN outside the field) in one TMA load per array
             tma_pending |= 1u << b;
+            if (CHECK && !tma_desc) {  // descriptors without a tensor map (rows not 16-byte multiples): cp.async
+                const TileGeo G = tile_geo_of(D, tile, fid);
+                const FieldDesc &F = D.fields[fid];
+                const uint32_t X = (uint32_t)G.x0 + lane;
+                for (int row = warp; row < ROWS; row += STWARPS) {
+                    const uint32_t Y = (uint32_t)G.y0 + row % TY, Z = (uint32_t)G.z0 + row / TY;
+                    if (X < F.nx && Y < F.ny && Z < F.nz)
+                        cp_async4(&s_desc[b][row * TX + lane], D.desc + F.vbase + ((uint64_t)Z * F.ny + Y) * F.nx + X);
+                }
+            }
             if (warp == 0) {  // warp 0 alone: the geometry, the dirty words and the TMA loads
                 const TileGeo G = tile_geo_of(D, tile, fid);
                 const FieldDesc &F = D.fields[fid];
@@ -389,11 +404,11 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
                     const CUtensorMap *maps = D.tmaps + (uint64_t)TMAPS * G.fid;
                     fence_proxy_async();  // the buffer's earlier reads come first
                     mbar_expect_tx(&s_mbar[b], (MODE == SM_SETUP ? 2u : 1u) * (uint32_t)(HALO_N * sizeof(float)) +
-                                                   (CHECK ? (uint32_t)(TILE_V * sizeof(uint32_t)) : 0u));
+                                                   (tma_desc ? (uint32_t)(TILE_V * sizeof(uint32_t)) : 0u));
                     tma_load_3d(sa[b], maps + ((MODE == SM_SETUP || MODE == SM_CLASSIFY) ? 0 : 2), G.x0 - XOFF,
                                 G.y0 - 1, G.z0 - 1, &s_mbar[b]);
                     if (MODE == SM_SETUP) tma_load_3d(sb[b], maps + 1, G.x0 - XOFF, G.y0 - 1, G.z0 - 1, &s_mbar[b]);
-                    if (CHECK) tma_load_3d(s_desc[b], maps + 3, G.x0, G.y0, G.z0, &s_mbar[b]);
+                    if (tma_desc) tma_load_3d(s_desc[b], maps + 3, G.x0, G.y0, G.z0, &s_mbar[b]);
                 }
             }
             return;
@@ -571,7 +586,8 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
                         else if (hv < __fsub_rn(fv, T.xi) || hv > __fadd_rn(fv, T.xi)) e = ERR_BOUND;
                         if (e) atomicOr(&s_err, e);
                         D.desc[vbase + i] = d;  // edit count k = 0 in the top byte
-                        T.g[i] = hv;
+                        if (T.gm) T.gm[((uint64_t)z * ny + y) * T.pitch + x] = hv;  // g is kept there
+                        else T.g[i] = hv;
                         if (D.events && (mn || mxx)) D.cp_rank[vbase + i] = 0;  // no linked saddle yet
                         Stn sg = stencil15(SB, c);
                         sg.valid = valid;
@@ -1078,7 +1094,7 @@ __global__ void __launch_bounds__(RADIX) k_sort_scatter(Dev D, int pass, const u
                 const uint32_t fid = (uint32_t)(en >> LOCAL_BITS);
                 const FieldDesc &F = D.fields[fid];
                 D.cp_rank[F.vbase + (en & LOCAL_MASK)] = (uint32_t)(cp0 + pos - D.fst[fid].cp_base);
-                D.gs[cp0 + pos] = F.g[en & LOCAL_MASK];  // g == f_hat before the first edit
+                D.gs[cp0 + pos] = F.fhat[en & LOCAL_MASK];  // g == f_hat before the first edit
             }
         }
         __syncthreads();
@@ -1103,7 +1119,10 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
     if (!c) return 0;
     const unsigned long long ent = D.o[q];
     const FieldDesc &F = D.fields[ent >> LOCAL_BITS];
-    const float *g = F.g;
+    // g of vertex e: in the padded copy (row stride pitch) when the field has one
+    const float *gp = F.gm ? F.gm : F.g;
+    const uint32_t gpad = F.gm ? F.pitch - F.nx : 0u;
+    auto g = [&](const uint32_t e) { return gp[(uint64_t)e + (uint64_t)(e / F.nx) * gpad]; };
     const uint32_t *lm = D.ev_list + D.ev_start[q];
     const uint32_t nm = c & 255u, nx = c >> 8;
     uint32_t target[2];
@@ -1112,10 +1131,10 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
         const uint32_t *l = lm;
         const uint32_t sel = l[0];
         uint32_t best = sel;
-        float bg = g[sel];
+        float bg = g(sel);
         for (uint32_t j = 1; j < nm; j++) {
             const uint32_t e = l[j];
-            const float ge = g[e];
+            const float ge = g(e);
             if (bg < ge || (bg == ge && best < e)) {
                 best = e;
                 bg = ge;
@@ -1127,10 +1146,10 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
         const uint32_t *l = lm + nm;
         const uint32_t sel = l[0];
         uint32_t best = sel;
-        float bg = g[sel];
+        float bg = g(sel);
         for (uint32_t j = 1; j < nx; j++) {
             const uint32_t e = l[j];
-            const float ge = g[e];
+            const float ge = g(e);
             if (ge < bg || (ge == bg && e < best)) {
                 best = e;
                 bg = ge;
@@ -1321,10 +1340,14 @@ enum { AM_PLAIN = 0, AM_FRONTIER = 1, AM_COUNT = 2 };
 // a changed extremum.  Returns whether the vertex changed; pinned: it reached
 // the bound; has_lo / has_hi: its CP pairs (q - 1, q) / (q, q + 1) exist and
 // are to be checked (FRONTIER, or pinned).
+// gm, tm: the field's padded copy of g, which holds g during the passes when
+// the field has one (null otherwise; held in a register by the caller: the
+// field table could be reloaded after every store), and the vertex's index in it.
 template <int AM>
-__device__ __forceinline__ bool edit_vertex(const Dev &D, const FieldDesc &F, FieldState *S, uint64_t t, uint32_t d,
-                                            float fv, float g0, uint32_t rk, bool capped, uint32_t &ncap,
-                                            bool &pinned, bool &has_lo, bool &has_hi, unsigned long long &q)
+__device__ __forceinline__ bool edit_vertex(const Dev &D, const FieldDesc &F, float *gm, FieldState *S, uint64_t t,
+                                            uint64_t tm, uint32_t d, float fv, float g0, uint32_t rk, bool capped,
+                                            uint32_t &ncap, bool &pinned, bool &has_lo, bool &has_hi,
+                                            unsigned long long &q)
 {
     const uint32_t N = F.N;
     uint32_t kk = d >> D_K_SHIFT;
@@ -1348,7 +1371,8 @@ __device__ __forceinline__ bool edit_vertex(const Dev &D, const FieldDesc &F, Fi
         gv = fl;
         kk = N + 1;
     }
-    F.g[t] = gv;
+    if (gm) gm[tm] = gv;  // g is kept in the padded copy during the passes
+    else F.g[t] = gv;
     D.desc[F.vbase + t] = (d & D_F_MASK) | (kk << D_K_SHIFT);
     pinned = kk == N + 1;
     if (D.events && (AM == AM_FRONTIER || pinned) && !(d & D_CP) && rk != 0 &&
@@ -1426,6 +1450,8 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         const uint32_t tz = fdiv(rest, F.div_tny), ty = rest - tz * tny;
         const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
         const uint64_t vbase = F.vbase, wbase = F.wbase;
+        float *const gm = F.gm;
+        const uint32_t pitch = F.pitch;
         uint32_t W = 0;  // lane r < ROWS: request word of tile row r (taken: read and cleared)
         if (lane < ROWS) {
             const uint32_t y = y0 + lane % TY, z = z0 + lane / TY;
@@ -1494,9 +1520,10 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
                 // all loads of the vertex at once (f, g and the CP rank are not
                 // needed for a pinned target or a regular vertex)
                 const uint32_t d = D.desc[vbase + t];
-                const float fv = F.f[t], g0 = F.g[t];
+                const uint64_t tm = ((uint64_t)z * ny + y) * pitch + x;  // index in the padded copy
+                const float fv = F.f[t], g0 = gm ? gm[tm] : F.g[t];
                 const uint32_t rk = D.cp_rank[vbase + t];
-                if (edit_vertex<AM>(D, F, S, t, d, fv, g0, rk, capped, ncap, pinned, has_lo, has_hi, q))
+                if (edit_vertex<AM>(D, F, gm, S, t, tm, d, fv, g0, rk, capped, ncap, pinned, has_lo, has_hi, q))
                     atomicOr(&s_cw[row], 1u << lx);
             }
             after_edit(pinned, has_lo, has_hi, q, x, y, z);
@@ -2169,6 +2196,35 @@ __global__ void __launch_bounds__(CTA) k_reflect_out(float *g, const uint32_t *d
     }
 }
 
+// g of the fields kept in a padded copy during the passes, back in the
+// field's own layout: one tile per warp, lane x of each of the tile's rows.
+__global__ void __launch_bounds__(CTA) k_unmirror(Dev D)
+{
+    const int lane = threadIdx.x & 31;
+    for (uint64_t tile = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); tile < D.total_tiles;
+         tile += (uint64_t)gridDim.x * WARPS) {
+        const uint32_t fid = field_of_tile(D, (uint32_t)tile);
+        const FieldDesc &F = D.fields[fid];
+        const float *gm = F.gm;
+        if (!gm) continue;
+        const TileGeo G = tile_geo_of(D, (uint32_t)tile, fid);
+        const uint32_t x = (uint32_t)G.x0 + lane, nx = F.nx, ny = F.ny, nz = F.nz, pitch = F.pitch;
+        if (x >= nx) continue;
+        float *g = F.g;
+        float v[ROWS];  // all of the tile's rows in flight before the first store
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            const uint32_t y = (uint32_t)G.y0 + r % TY, z = (uint32_t)G.z0 + r / TY;
+            v[r] = (y < ny && z < nz) ? gm[((uint64_t)z * ny + y) * pitch + x] : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            const uint32_t y = (uint32_t)G.y0 + r % TY, z = (uint32_t)G.z0 + r / TY;
+            if (y < ny && z < nz) g[((uint64_t)z * ny + y) * nx + x] = v[r];
+        }
+    }
+}
+
 // ------------------------------------------------------------ edit stream (Sec. 3.3; storage accounting)
 // The stored form of a result: one edit-count byte per vertex (0..N steps of
 // Delta, N+1 = the lossless bound) and the lossless values in index order.
@@ -2450,6 +2506,10 @@ void launch_stream_decode(const float *fhat, const uint8_t *kcodes, const float 
 void launch_reflect_in(const float *src, float *dst, uint64_t n, cudaStream_t s)
 {
     k_reflect_in<<<grid_for(n, CTA, 8), CTA, 0, s>>>(src, dst, n);
+}
+void launch_unmirror(const Dev &D, cudaStream_t s)
+{
+    k_unmirror<<<grid_for(D.total_tiles, WARPS, 8), CTA, 0, s>>>(D);
 }
 void launch_reflect_out(float *g, const uint32_t *desc, uint64_t n, cudaStream_t s)
 {

@@ -20,7 +20,8 @@ int device_sms();
 // 2^14-bit link-component table (host copy, built on first use; see exz_engine.cu)
 const uint32_t *host_multi_table();
 // TMA map of a field's halo box (halo) or descriptor tile; false where the field cannot be mapped
-bool make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo);
+// (pitch: row pitch of the array in elements, 0 for nx)
+bool make_map(CUtensorMap *map, const void *base, const FieldDesc &F, bool halo, uint32_t pitch = 0);
 
 void launch_setup(const Dev &D, const SetupRange &R, cudaStream_t s);
 void launch_check_all(const Dev &D, cudaStream_t s);
@@ -51,6 +52,8 @@ void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t 
 // increasing edits by reflection of the field
 void launch_reflect_in(const float *src, float *dst, uint64_t n, cudaStream_t s);
 void launch_reflect_out(float *g, const uint32_t *desc, uint64_t n, cudaStream_t s);
+// g of the fields kept in a padded copy (FieldDesc::gm) copied back into FieldDesc::g.
+void launch_unmirror(const Dev &D, cudaStream_t s);
 // edit stream (storage form of a result)
 unsigned stream_blocks(uint64_t items);
 void launch_stream_kcodes(const EditRec *edits, uint64_t ne, uint64_t n, uint32_t N, uint8_t *kcodes, int *bad,

@@ -346,8 +346,8 @@ int start_request(exactz_server *S, const Dev &D, Req *r)
     F.mirror = inc ? 1u : 0u;  // increasing edits: the room holds the reflection of -f, -f_hat
     // tile loads by TMA where the room's arrays can be mapped (else cp.async)
     CUtensorMap *m = S->h_tmaps + (uint64_t)TMAPS * slot;
-    F.tma = make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) && make_map(m + 2, F.g, F, true) &&
-            make_map(m + 3, S->desc + r->v0, F, false);
+    F.tma = (make_map(m, F.f, F, true) && make_map(m + 1, F.fhat, F, true) ? TMA_SETUP : 0u) |
+            (make_map(m + 2, F.g, F, true) ? TMA_G : 0u) | (make_map(m + 3, S->desc + r->v0, F, false) ? TMA_DESC : 0u);
     S->h_fd[slot] = F;
     if (!inc) {
         SK(cudaMemcpyAsync(S->f + r->v0, r->f, r->n * 4, cudaMemcpyHostToDevice, S->xs));
