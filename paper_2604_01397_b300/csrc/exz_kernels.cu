@@ -370,6 +370,20 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float qnan = __int_as_float(0x7fc00000);
 
+    // The tile's descriptors into buffer b with cp.async, one row of TX per
+    // warp at a time.  The field's constants are read once, into registers:
+    // each cp.async is an asm statement with a memory clobber, after which a
+    // read through the field table would be issued again.
+    auto stage_desc = [&](const int b, const TileGeo &G, const FieldDesc &F) {
+        const uint32_t nx = F.nx, ny = F.ny, nz = F.nz;
+        const uint32_t *const desc = D.desc + F.vbase;
+        const uint32_t X = (uint32_t)G.x0 + lane;
+        for (int row = warp; row < ROWS; row += STWARPS) {
+            const uint32_t Y = (uint32_t)G.y0 + row % TY, Z = (uint32_t)G.z0 + row / TY;
+            if (X < nx && Y < ny && Z < nz) cp_async4(&s_desc[b][row * TX + lane], desc + ((uint64_t)Z * ny + Y) * nx + X);
+        }
+    };
+
     // Stage tile into buffer b: the halo rows (one warp per row of HXP values,
     // x0-1 .. x0+TX) and, for CHECK_LIST, the tile's dirty row words.
     auto stage = [&](const uint32_t tile, const int b) {
@@ -379,16 +393,8 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
         const bool tma_desc = CHECK && (tmab & TMA_DESC) != 0;
         if (tma_halo) {  // the whole halo (NaN outside the field) in one TMA load per array
             tma_pending |= 1u << b;
-            if (CHECK && !tma_desc) {  // descriptors without a tensor map (rows not 16-byte multiples): cp.async
-                const TileGeo G = tile_geo_of(D, tile, fid);
-                const FieldDesc &F = D.fields[fid];
-                const uint32_t X = (uint32_t)G.x0 + lane;
-                for (int row = warp; row < ROWS; row += STWARPS) {
-                    const uint32_t Y = (uint32_t)G.y0 + row % TY, Z = (uint32_t)G.z0 + row / TY;
-                    if (X < F.nx && Y < F.ny && Z < F.nz)
-                        cp_async4(&s_desc[b][row * TX + lane], D.desc + F.vbase + ((uint64_t)Z * F.ny + Y) * F.nx + X);
-                }
-            }
+            if (CHECK && !tma_desc)  // descriptors without a tensor map (rows not 16-byte multiples): cp.async
+                stage_desc(b, tile_geo_of(D, tile, fid), D.fields[fid]);
             if (warp == 0) {  // warp 0 alone: the geometry, the dirty words and the TMA loads
                 const TileGeo G = tile_geo_of(D, tile, fid);
                 const FieldDesc &F = D.fields[fid];
@@ -423,14 +429,7 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
             if (y < ny && z < nz) cp_async4(&s_rw[b][threadIdx.x], D.dirty + F.wbase + ((uint64_t)z * ny + y) * F.tnx + G.tx);
             else s_rw[b][threadIdx.x] = 0;
         }
-        if (CHECK) {  // the tile's descriptors, one row of TX per warp at a time
-            const uint32_t X = (uint32_t)G.x0 + lane;
-            for (int row = warp; row < ROWS; row += STWARPS) {
-                const uint32_t Y = (uint32_t)G.y0 + row % TY, Z = (uint32_t)G.z0 + row / TY;
-                if (X < nx && Y < ny && Z < nz)
-                    cp_async4(&s_desc[b][row * TX + lane], D.desc + F.vbase + ((uint64_t)Z * ny + Y) * nx + X);
-            }
-        }
+        if (CHECK) stage_desc(b, G, F);
         const float *A = (MODE == SM_SETUP || MODE == SM_CLASSIFY) ? F.f : F.g;
         const float *B = F.fhat;
         const bool interior = G.x0 >= 1 && G.x0 + TX < (int)nx && G.y0 >= 1 && G.y0 + TY < (int)ny && G.z0 >= 1 &&
