@@ -876,6 +876,26 @@ def run_batched(a):
                     "ratio_vs_per_field_graph": loop_ms["graph"] / ms, "same_results": bool(same),
                     "plain": "exactz_ws_correct per field, plain loop (full sweep each pass, host reads the flag)"}
 
+    # the same batch with each pass as one cooperatively launched kernel
+    # (EXACTZ_MODE_FUSED) beside the four-kernel graph body timed above
+    if world == 1 and not a.no_extras and a.mode == "graph":
+        batched(mode="fused")  # warm-up: its graph captured
+        torch.cuda.synchronize()
+        reps = max(1, min(a.steps, 5))
+        e0.record(stream)
+        for _ in range(reps):
+            rf = batched(mode="fused")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / reps
+        same_f = all(x["iterations"] == y["iterations"] and x["status"] == y["status"] and
+                     x["n_edits"] == y["n_edits"] and x["residual"] == y["residual"] for x, y in zip(rf, rs))
+        extras["fused_pass_kernel"] = {
+            "ms": fms, "gbs": 4.0 * n_total / (fms / 1e3) / 1e9, "graph_ms": ms, "graph_over_fused": ms / fms,
+            "same_counts": bool(same_f), "launches": ws.stats()["kernel_launches"],
+            "form": "graph while-loop whose body is one cooperative kernel per pass (k_pass: check and CP pairs, "
+                    "grid barrier, apply, bookkeeping by the last block)"}
+
     # end to end through the C ABI with host buffers: every step copies all
     # fields' f and f_hat in and their g and edit records out
     e2e = None

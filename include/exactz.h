@@ -69,6 +69,8 @@ extern "C" {
 #define EXACTZ_MODE_PLAIN 0     /* Algorithm 1 literally: full sweep each pass, host-driven loop */
 #define EXACTZ_MODE_FRONTIER 1  /* re-check only tiles touched by last pass's edits, host-driven loop */
 #define EXACTZ_MODE_GRAPH 2     /* frontier passes in a CUDA graph; device-side while-loop exit */
+#define EXACTZ_MODE_FUSED 3     /* the graph loop with each pass as one cooperatively launched kernel
+                                 * (check and CP pairs, grid barrier, apply, bookkeeping); same results */
 
 /* Edit direction (opts.direction).  Every rule names the vertex that must be
  * lower (decreasing edits, Sec. 3.3: g <- fl(g - Delta) down to fl(f - xi)) or
@@ -322,7 +324,7 @@ int exactz_decode_edits(const float *fhat, uint64_t n, float xi, uint32_t N, uin
  * whose GPU work overlapped would race on the array: within one process they
  * are serialised by a lock, which each call releases only after its stream
  * has drained (on error returns too).
- * A GRAPH mode request runs the same passes as FRONTIER (identical results);
+ * A GRAPH or FUSED mode request runs the same passes as FRONTIER (identical results);
  * opts->profile is ignored.  EXACTZ_EVENTS_ORIGINAL needs set-up storage sized
  * by the field's extremum graph and is refused (EXACTZ_EINVAL); increasing
  * edits are offered (their reflected fields live in the same scratch).

@@ -23,7 +23,7 @@ ERROR_NAMES = {-1: "EINVAL", -2: "ENONFINITE", -3: "EBOUND", -4: "ENOMEM", -5: "
                -6: "ENODEV", -7: "ESIZE"}
 
 CONVERGED, STUCK, ITER_LIMIT = 1, 2, 3
-MODE_PLAIN, MODE_FRONTIER, MODE_GRAPH = 0, 1, 2
+MODE_PLAIN, MODE_FRONTIER, MODE_GRAPH, MODE_FUSED = 0, 1, 2, 3
 
 
 class Dims(ctypes.Structure):

@@ -15,7 +15,7 @@ import torch
 
 from . import _native as N
 
-MODES = {"plain": N.MODE_PLAIN, "frontier": N.MODE_FRONTIER, "graph": N.MODE_GRAPH}
+MODES = {"plain": N.MODE_PLAIN, "frontier": N.MODE_FRONTIER, "graph": N.MODE_GRAPH, "fused": N.MODE_FUSED}
 # event constraints: the global order of all critical points (Sec. 4.3), or the
 # saddle order and extremum-graph merge / split events (Sec. 4.2)
 EVENTS = {"reformulated": 0, "original": 1}

@@ -168,6 +168,8 @@ struct LoopState {
     uint32_t pass;
     uint32_t fault;  // a bounded wait ran out (the call reports EXACTZ_ENODEV)
     uint32_t ev_changed;  // event-list set-up: a path end moved in the last jump round
+    uint32_t bar_count, bar_gen;  // fused pass kernel: blocks arrived at the grid barrier; its generation
+    uint32_t pass_done, pad0;     // fused pass kernel: blocks done with the apply this pass
 };
 
 // Launch schedule of the per-pass kernels (chosen by the autotuner): blocks per

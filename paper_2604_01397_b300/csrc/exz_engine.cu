@@ -415,10 +415,11 @@ Dev make_dev(exactz_workspace *ws, const Layout &L)
     return D;
 }
 
-// Graph: [loop-flag kernel] -> while (flag) { check, pairs, apply, bookkeeping }.
-int ensure_graph(exactz_workspace *ws, const Dev &D)
+// Graph: [loop-flag kernel] -> while (flag) { check, pairs, apply, bookkeeping },
+// the body as four kernels or (fused) as one cooperative kernel.
+int ensure_graph(exactz_workspace *ws, const Dev &D, bool fused)
 {
-    uint64_t evk = D.events;
+    uint64_t evk = D.events ^ (fused ? 0x8000000000000000ull : 0ull);
     for (const void *p : {(const void *)D.ev_start, (const void *)D.ev_cnt, (const void *)D.ev_list,
                           (const void *)D.ev_radj})
         evk = (evk ^ (uint64_t)(uintptr_t)p) * 1099511628211ull;
@@ -437,6 +438,8 @@ int ensure_graph(exactz_workspace *ws, const Dev &D)
         ws->graph = nullptr;
     }
     cudaStream_t cs = ws->cap_stream;
+    unsigned pgrid = 0;
+    if (fused) CK(pass_grid(&pgrid));
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     ws->graph = g;
@@ -462,16 +465,20 @@ int ensure_graph(exactz_workspace *ws, const Dev &D)
     CK(cudaStreamEndCapture(cs, &g));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    // the vertex check and the CP-pair check read nothing the other writes
-    // (both only OR request bits and set apply flags): they run side by side
-    CK(cudaEventRecord(ws->cap_fork, cs));
-    CK(cudaStreamWaitEvent(ws->cap_stream2, ws->cap_fork, 0));
-    launch_pairs_list(D, ws->cap_stream2);
-    CK(cudaEventRecord(ws->cap_join, ws->cap_stream2));
-    launch_check_list(D, cs);
-    CK(cudaStreamWaitEvent(cs, ws->cap_join, 0));
-    launch_apply(D, 1, cs);
-    launch_book(D, h, 1, cs);
+    if (fused) {
+        CK(launch_pass(D, h, pgrid, cs));
+    } else {
+        // the vertex check and the CP-pair check read nothing the other writes
+        // (both only OR request bits and set apply flags): they run side by side
+        CK(cudaEventRecord(ws->cap_fork, cs));
+        CK(cudaStreamWaitEvent(ws->cap_stream2, ws->cap_fork, 0));
+        launch_pairs_list(D, ws->cap_stream2);
+        CK(cudaEventRecord(ws->cap_join, ws->cap_stream2));
+        launch_check_list(D, cs);
+        CK(cudaStreamWaitEvent(cs, ws->cap_join, 0));
+        launch_apply(D, 1, cs);
+        launch_book(D, h, 1, cs);
+    }
     CK(cudaStreamEndCapture(cs, &body));
     CK(cudaGraphInstantiate(&ws->gexec, g, 0));
     std::memcpy(ws->gkey, key, sizeof(key));
@@ -631,7 +638,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     exactz_opts opt;
     exactz_default_opts(&opt);
     if (o) opt = *o;
-    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH || opt.events > EXACTZ_EVENTS_ORIGINAL ||
+    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_FUSED || opt.events > EXACTZ_EVENTS_ORIGINAL ||
         opt.direction > EXACTZ_EDITS_INCREASING)
         return EXACTZ_EINVAL;
     const bool events = opt.events == EXACTZ_EVENTS_ORIGINAL;
@@ -771,10 +778,11 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     launches += 1 + 4 + 3 * P + 3;
     CK(cudaGetLastError());
 
-    if (opt.mode == EXACTZ_MODE_GRAPH) {
-        if ((rc = ensure_graph(ws, D)) != EXACTZ_OK) return rc;
+    const bool in_graph = opt.mode == EXACTZ_MODE_GRAPH || opt.mode == EXACTZ_MODE_FUSED;
+    if (in_graph) {
+        if ((rc = ensure_graph(ws, D, opt.mode == EXACTZ_MODE_FUSED)) != EXACTZ_OK) return rc;
         CK(cudaGraphLaunch(ws->gexec, s));
-        launches += 1;  // loop-flag kernel; the body's 4 kernels per pass are added below
+        launches += 1;  // loop-flag kernel; the body's kernels per pass are added below
     } else {
         for (;;) {
             CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -839,7 +847,8 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     ws->stats.sum_tiles = ws->h_ls->sum_tiles;
     ws->stats.sum_pairs = ws->h_ls->sum_pairs;
     ws->stats.sum_visits = ws->h_ls->sum_visits;
-    if (opt.mode == EXACTZ_MODE_GRAPH) launches += 4 * (ws->h_ls->pass > 0 ? ws->h_ls->pass - 1 : 0);
+    if (in_graph)
+        launches += (opt.mode == EXACTZ_MODE_FUSED ? 1 : 4) * (ws->h_ls->pass > 0 ? ws->h_ls->pass - 1 : 0);
     ws->stats.kernel_launches = launches;
     ws->stats.loop_passes = loop_passes;
     for (int k = 0; k < 3; k++) ws->stats.loop_kernel_ms[k] = (float)loop_ms[k];
@@ -1028,7 +1037,7 @@ int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const floa
     exactz_opts opt;
     exactz_default_opts(&opt);
     if (opts) opt = *opts;
-    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_GRAPH || opt.events > EXACTZ_EVENTS_ORIGINAL ||
+    if (opt.N < 1 || opt.N > 254 || opt.mode > EXACTZ_MODE_FUSED || opt.events > EXACTZ_EVENTS_ORIGINAL ||
         opt.direction > EXACTZ_EDITS_INCREASING)
         return EXACTZ_EINVAL;
     Layout L;
@@ -1608,7 +1617,7 @@ extern "C" int exactz_correct_noalloc(const float *f, const float *fhat, exactz_
     exactz_opts opt;
     exactz_default_opts(&opt);
     if (opts) opt = *opts;
-    if (opt.mode == EXACTZ_MODE_GRAPH) opt.mode = EXACTZ_MODE_FRONTIER;
+    if (opt.mode == EXACTZ_MODE_GRAPH || opt.mode == EXACTZ_MODE_FUSED) opt.mode = EXACTZ_MODE_FRONTIER;
     opt.profile = 0;
     const float *fp[1] = {f};
     const float *hp[1] = {fhat};

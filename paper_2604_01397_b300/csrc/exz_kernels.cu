@@ -340,9 +340,11 @@ __device__ __forceinline__ TileInfo tile_info(const TileGeo &G, const FieldDesc 
 // pinned-tile lists of fields fids[0..nf) (PINNED).
 // The next tile is staged with cp.async into a second buffer while the
 // current one is checked.
+// (The body of k_stencil and of the fused pass kernel's check phase; blocks of
+// SCTA threads.)
 template <int MODE>
-__global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHECK_LIST || MODE == SM_PINNED) ? 10 : 12)) k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
-                                                      uint32_t t1, const uint32_t *fids, uint32_t nf)
+__device__ __forceinline__ void stencil_tiles(const Dev &D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0,
+                                              uint32_t t1, const uint32_t *fids, uint32_t nf)
 {
     constexpr int NB = 2;
     __shared__ __align__(128) float sa[NB][HALO_N];
@@ -743,6 +745,13 @@ __global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHEC
     }
     if (MODE == SM_CHECK_LIST && threadIdx.x == 0 && src.ntiles) atomicAdd(&D.ls->sum_tiles, src.ntiles);
     if (MODE == SM_CHECK_LIST && lane == 0 && nvisits) atomicAdd(&D.ls->sum_visits, (unsigned long long)nvisits);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(SCTA, MODE == SM_SETUP ? 8 : ((MODE == SM_CHECK_LIST || MODE == SM_PINNED) ? 10 : 12))
+    k_stencil(Dev D, uint32_t *desc_out, uint8_t *type_out, uint32_t t0, uint32_t t1, const uint32_t *fids, uint32_t nf)
+{
+    stencil_tiles<MODE>(D, desc_out, type_out, t0, t1, fids, nf);
 }
 
 // ------------------------------------------------------------ block scan helpers
@@ -1177,9 +1186,11 @@ __device__ __forceinline__ int check_events(const Dev &D, unsigned long long q, 
 // ALL at every listed saddle, LIST at those whose event bit (set by the apply
 // kernel when a linked extremum changed) is set, PINNED at those whose pinned
 // event bit (set when a linked extremum was pinned) is set.
-template <int PM>
-__global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsigned long long *countp,
-                                               const uint32_t *fids, uint32_t nf)
+// (The body of k_pairs and of the fused pass kernel's CP-pair phase; blocks of
+// NT threads.)
+template <int PM, int NT>
+__device__ __forceinline__ void pairs_body(const Dev &D, uint64_t cp0, const unsigned long long *countp,
+                                           const uint32_t *fids, uint32_t nf)
 {
     const int lane = threadIdx.x & 31;
     // evaluate pair q; true (and the tile of the request) when its target is requested
@@ -1202,7 +1213,7 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
         tile = request_vertex(D, F, t);
         return true;
     };
-    const unsigned long long stride = (unsigned long long)gridDim.x * CTA;
+    const unsigned long long stride = (unsigned long long)gridDim.x * NT;
     const unsigned long long pw = (D.cp_cap + 31) / 32;  // pair-bit words; event bits, pinned event bits follow
     if (PM == PM_LIST || (PM == PM_PINNED && D.events)) {
         // each warp takes 32 consecutive words of pairbits at a time (one per
@@ -1211,7 +1222,7 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
         // linked to pinned extrema.
         const unsigned long long w0 = PM == PM_LIST ? 0ull : 2 * pw;
         const unsigned long long w1 = PM == PM_LIST ? (D.events ? 2 * pw : pw) : 3 * pw;
-        const unsigned long long gw = ((unsigned long long)blockIdx.x * CTA + threadIdx.x) >> 5;
+        const unsigned long long gw = ((unsigned long long)blockIdx.x * NT + threadIdx.x) >> 5;
         const unsigned long long nw = stride >> 5;
         uint32_t npairs = 0;
         for (unsigned long long c = gw; w0 + c * 32 < w1; c += nw) {
@@ -1270,7 +1281,7 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
             count = D.fst[fids[fi]].pin_pair_count;
             list = D.fields[fids[fi]].pin_pairs;
         }
-        for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
+        for (unsigned long long j = (unsigned long long)blockIdx.x * NT + threadIdx.x; j < count; j += stride) {
             uint32_t tile = 0;
             if (check(list ? (unsigned long long)list[j] : cp0 + j, tile) && !D.apply_flag[tile])
                 D.apply_flag[tile] = 1;
@@ -1278,13 +1289,20 @@ __global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsign
     }
     if (PM == PM_ALL && D.events) {  // rule C3 at every listed saddle
         const unsigned long long count = *countp;
-        for (unsigned long long j = (unsigned long long)blockIdx.x * CTA + threadIdx.x; j < count; j += stride) {
+        for (unsigned long long j = (unsigned long long)blockIdx.x * NT + threadIdx.x; j < count; j += stride) {
             uint32_t tl[2];
             const int nt = check_events<false>(D, cp0 + j, tl);
             for (int u = 0; u < nt; u++)
                 if (!D.apply_flag[tl[u]]) D.apply_flag[tl[u]] = 1;
         }
     }
+}
+
+template <int PM>
+__global__ void __launch_bounds__(CTA) k_pairs(Dev D, uint64_t cp0, const unsigned long long *countp,
+                                               const uint32_t *fids, uint32_t nf)
+{
+    pairs_body<PM, CTA>(D, cp0, countp, fids, nf);
 }
 
 // ------------------------------------------------------------ apply (Sec. 3.3)
@@ -1411,15 +1429,18 @@ __device__ __forceinline__ bool edit_vertex(const Dev &D, const FieldDesc &F, fl
 //     sets the next pass's dirty bits (the closed stars of the changed
 //     vertices) and queues their tiles.
 //   COUNT: add the requested (pinned) vertices to the field's residual.
-template <int AM>
-__global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
+// (The body of k_apply_tiles and of the fused pass kernel's apply phase; NW
+// warps per block.  The tile flags and request words are read through L2: in
+// the fused kernel other blocks wrote them earlier in the same launch.)
+template <int AM, int NW>
+__device__ __forceinline__ void apply_tiles(const Dev &D)
 {
-    __shared__ uint32_t s_cw_all[WARPS][ROWS];
+    __shared__ uint32_t s_cw_all[NW][ROWS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *s_cw = s_cw_all[warp];
     unsigned long long nreq = 0;
     uint32_t pb, pe, pst;
-    work_range(D, D.total_tiles, blockIdx.x * WARPS + warp, gridDim.x * WARPS, pb, pe, pst);
+    work_range(D, D.total_tiles, blockIdx.x * NW + warp, gridDim.x * NW, pb, pe, pst);
     // The warp's flagged tiles, one at a time: probe 32 flags at once and take
     // the flagged ones.
     uint64_t p = pb;
@@ -1428,7 +1449,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
     auto next_tile = [&]() -> uint32_t {
         while (!pend && p < pe) {
             const uint64_t ti = p + (uint64_t)lane * pst;
-            const bool flagged = ti < pe && D.apply_flag[ti] != 0;
+            const bool flagged = ti < pe && __ldcg(&D.apply_flag[ti]) != 0;
             if (flagged) D.apply_flag[ti] = 0;
             pend = __ballot_sync(0xffffffffu, flagged);
             pbase = p;
@@ -1456,7 +1477,7 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
             const uint32_t y = y0 + lane % TY, z = z0 + lane / TY;
             if (y < ny && z < nz) {
                 uint32_t *wp = D.reqw + wbase + ((uint64_t)z * ny + y) * tnx + tx;
-                W = *wp;
+                W = __ldcg(wp);
                 if (W) *wp = 0;
             }
             s_cw[lane] = 0;
@@ -1598,6 +1619,12 @@ __global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
         __syncwarp();
     }
     if (AM != AM_COUNT && lane == 0 && nreq) atomicAdd(&D.ls->sum_requests, nreq);
+}
+
+template <int AM>
+__global__ void __launch_bounds__(CTA, 4) k_apply_tiles(Dev D)
+{
+    apply_tiles<AM, WARPS>(D);
 }
 
 // ------------------------------------------------------------ event lists (set-up, Sec. 4.2)
@@ -2019,14 +2046,20 @@ __global__ void __launch_bounds__(CTA) k_ev_fill(Dev D, uint32_t *radj)
 }
 
 // ------------------------------------------------------------ bookkeeping
-__global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle h, int use_graph)
+// Per-field end of a pass by one block of NT threads: a field with requests
+// this pass counts an iteration, the others are done; sets the loop flag and
+// the graph conditional.  The field state is read through volatile accesses:
+// in the fused pass kernel other blocks wrote it earlier in the same launch.
+template <int NT>
+__device__ __forceinline__ void book_fields(const Dev &D, cudaGraphConditionalHandle h, int use_graph)
 {
     __shared__ uint32_t s_any;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
-    const bool fault = D.ls->fault != 0;  // a bounded wait ran out: stop every field (the call reports it)
-    for (uint32_t f = threadIdx.x; f < D.nfields; f += CTA) {
-        FieldState *S = &D.fst[f];
+    // a bounded wait ran out: stop every field (the call reports it)
+    const bool fault = *reinterpret_cast<volatile uint32_t *>(&D.ls->fault) != 0;
+    for (uint32_t f = threadIdx.x; f < D.nfields; f += NT) {
+        volatile FieldState *S = &D.fst[f];
         if (S->done) continue;
         if (S->err || S->capped || fault) {
             S->done = 1;
@@ -2049,6 +2082,11 @@ __global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle 
     }
 }
 
+__global__ void __launch_bounds__(CTA) k_book(Dev D, cudaGraphConditionalHandle h, int use_graph)
+{
+    book_fields<CTA>(D, h, use_graph);
+}
+
 // Sets the loop flag (and graph conditional) from the per-field state.
 __global__ void __launch_bounds__(SMALL_NT) k_loop_flag(Dev D, cudaGraphConditionalHandle h, int use_graph)
 {
@@ -2062,6 +2100,67 @@ __global__ void __launch_bounds__(SMALL_NT) k_loop_flag(Dev D, cudaGraphConditio
         D.ls->any_active = s_any;
         if (use_graph) cudaGraphSetConditional(h, s_any ? 1u : 0u);
     }
+}
+
+// ------------------------------------------------------------ fused pass
+// Barrier across all blocks of the fused pass kernel, which is launched
+// cooperatively (every block resident).  The wait is bounded: when it runs
+// out, the block sets the fault flag, stops the graph loop and gets false
+// (the caller returns; blocks still waiting run out the same way).
+__device__ __forceinline__ bool grid_barrier(const Dev &D, cudaGraphConditionalHandle h)
+{
+    __shared__ uint32_t s_ok;
+    __threadfence();  // this block's writes before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *gen = &D.ls->bar_gen;
+        const uint32_t g0 = *gen;
+        __threadfence();  // the generation is read before the arrival
+        uint32_t ok = 1;
+        if (atomicAdd(&D.ls->bar_count, 1u) == gridDim.x - 1) {
+            D.ls->bar_count = 0;  // everyone has arrived; nobody arrives again before the generation moves
+            __threadfence();
+            atomicAdd(&D.ls->bar_gen, 1u);
+        } else {
+            for (uint32_t i = 0; *gen == g0; i++) {
+                if (i == (1u << 24)) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!ok) {
+            atomicOr(&D.ls->fault, 1u);
+            cudaGraphSetConditional(h, 0u);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// One frontier pass in one launch, the body of the fused graph loop
+// (EXACTZ_MODE_FUSED): the vertex check (rules R1, R2) and the CP-pair check
+// (R3) of every block, a grid barrier, the bounded edit, and the bookkeeping
+// by the last block to finish its edits.  The same phases and results as the
+// graph loop's four kernels.
+__global__ void __launch_bounds__(SCTA, 6) k_pass(Dev D, cudaGraphConditionalHandle h)
+{
+    stencil_tiles<SM_CHECK_LIST>(D, nullptr, nullptr, 0, 0, nullptr, 0);
+    pairs_body<PM_LIST, SCTA>(D, 0, nullptr, nullptr, 0);
+    if (!grid_barrier(D, h)) return;
+    apply_tiles<AM_FRONTIER, SCTA / 32>(D);
+    __shared__ uint32_t s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&D.ls->pass_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();  // every block's edits and counters before the bookkeeping reads them
+    if (threadIdx.x == 0) D.ls->pass_done = 0;
+    book_fields<SCTA>(D, h, 1);
 }
 
 // ------------------------------------------------------------ status
@@ -2460,6 +2559,29 @@ void launch_apply(const Dev &D, int frontier, cudaStream_t s)
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s)
 {
     k_book<<<1, CTA, 0, s>>>(D, h, use_graph);
+}
+cudaError_t pass_grid(unsigned *grid)
+{
+    int nb = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pass, SCTA, 0);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorCooperativeLaunchTooLarge;
+    *grid = (unsigned)(nb * sms());  // every block resident
+    return cudaSuccess;
+}
+cudaError_t launch_pass(const Dev &D, cudaGraphConditionalHandle h, unsigned grid, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(SCTA);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pass, D, h);
 }
 void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s)
 {

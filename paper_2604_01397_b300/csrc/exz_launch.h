@@ -46,6 +46,10 @@ void launch_scan_u32(const uint32_t *in, unsigned long long *out, uint64_t n, un
                      cudaStream_t s);
 void launch_ev_reverse(const Dev &D, uint32_t *radj, cudaStream_t s);
 void launch_book(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);
+// One frontier pass (check, CP pairs, apply, bookkeeping) as one cooperative kernel launch of
+// pass_grid() blocks: as many as can be resident at once.
+cudaError_t pass_grid(unsigned *grid);
+cudaError_t launch_pass(const Dev &D, cudaGraphConditionalHandle h, unsigned grid, cudaStream_t s);
 void launch_loop_flag(const Dev &D, cudaGraphConditionalHandle h, int use_graph, cudaStream_t s);
 void launch_finish(const Dev &D, const FieldSet &FS, cudaStream_t s);
 void launch_edit_list(const Dev &D, const FieldSet &FS, int write, cudaStream_t s);

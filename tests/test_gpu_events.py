@@ -14,7 +14,7 @@ import synth
 from gpu_util import assert_same, gpu_run, oracle_run, to_dev
 
 pytestmark = pytest.mark.gpu
-MODES = ["plain", "frontier", "graph"]
+MODES = ["plain", "frontier", "graph", "fused"]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -167,13 +167,18 @@ def test_batched256_matches_oracle_digests():
     ws.autotune(fs, fhs, xis, repeats=1)
     gs = [torch.empty_like(f) for f in fs]
     ebufs = [torch.empty((ref["n_edits"] + 1, 16), dtype=torch.uint8, device=dev) for ref in refs]
-    rs = ws.correct(fs, fhs, xis, mode="graph", g_out=gs, edit_bufs=ebufs)
-    torch.cuda.synchronize()
-    for j, (ref, r, g) in enumerate(zip(refs, rs, gs)):
-        try:
-            _check_result(ref, r, g)
-        except AssertionError as e:
-            raise AssertionError(f"field {j} {specs[j]['dims']}: {e}") from None
+    # the bench's form (graph loop, autotuned schedule), then each pass as one
+    # cooperative kernel
+    for mode in ("graph", "fused"):
+        rs = ws.correct(fs, fhs, xis, mode=mode, g_out=gs, edit_bufs=ebufs)
+        torch.cuda.synchronize()
+        for j, (ref, r, g) in enumerate(zip(refs, rs, gs)):
+            try:
+                _check_result(ref, r, g)
+            except AssertionError as e:
+                raise AssertionError(f"{mode}: field {j} {specs[j]['dims']}: {e}") from None
+        for g in gs:
+            g.fill_(float("nan"))  # the next mode writes every value again
     ws.close()
 
 

@@ -12,7 +12,7 @@ from conftest import read_golden
 from gpu_util import assert_same, gpu_run, k_from_edits, oracle_run, to_dev
 
 pytestmark = pytest.mark.gpu
-MODES = ["plain", "frontier", "graph"]
+MODES = ["plain", "frontier", "graph", "fused"]
 
 
 @pytest.fixture(scope="module", autouse=True)
