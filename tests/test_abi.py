@@ -62,6 +62,27 @@ def test_default_opts():
     assert (o.events, o.direction) == (ez.EVENTS["reformulated"], ez.DIRECTIONS["decreasing"])
 
 
+def test_binding_constants_match_the_header():
+    """Every EXACTZ_* value the Python binding uses equals the header's
+    #define: return codes, loop modes, event constraints, edit directions."""
+    import paper_2604_01397_b300 as ez
+
+    txt = open(os.path.join(ROOT, "include", "exactz.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(EXACTZ_[A-Z_]+)\s+\(?(-?\d+)\)?", txt)}
+    N = ez._native
+    for name in ("OK", "EINVAL", "ENONFINITE", "EBOUND", "ENOMEM", "ECAP", "ENODEV", "ESIZE"):
+        assert getattr(N, "EXACTZ_" + name) == defs["EXACTZ_" + name], name
+    modes = {"plain": "EXACTZ_MODE_PLAIN", "frontier": "EXACTZ_MODE_FRONTIER", "graph": "EXACTZ_MODE_GRAPH",
+             "fused": "EXACTZ_MODE_FUSED"}
+    assert set(ez.api.MODES) == set(modes)
+    for k, d in modes.items():
+        assert ez.api.MODES[k] == defs[d], k
+    assert ez.EVENTS["reformulated"] == defs["EXACTZ_EVENTS_REFORMULATED"]
+    assert ez.EVENTS["original"] == defs["EXACTZ_EVENTS_ORIGINAL"]
+    assert ez.DIRECTIONS["decreasing"] == defs["EXACTZ_EDITS_DECREASING"]
+    assert ez.DIRECTIONS["increasing"] == defs["EXACTZ_EDITS_INCREASING"]
+
+
 def test_oracle_and_library_share_no_code():
     # the oracle is plain C compiled by gcc; the library is CUDA; neither
     # includes, imports or links the other
