@@ -195,6 +195,23 @@ int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const floa
                                exactz_edit *const *edits_out, const uint64_t *edits_cap,
                                exactz_result *res, void *cuda_stream);
 
+/* The same for a sequence of nsteps batches of nfields fields each (the
+ * paper has no counterpart): step s corrects fields s*nfields .. s*nfields +
+ * nfields - 1 together, as exactz_ws_correct would, field j having dims[j]
+ * in every step.  Step s+1's inputs are copied in and step s-1's outputs
+ * copied out while step s is corrected (two device slots of the whole batch,
+ * held by the workspace and grown on first use: 24 bytes per vertex plus the
+ * edit records).  f, fhat, xi, g_out, edits_out, edits_cap and res hold
+ * nsteps*nfields entries, step-major, with the meanings above; field j's
+ * edit records get a region of the largest edits_cap[s*nfields + j] over
+ * the steps.  Errors as above, per step (EXACTZ_EINVAL also for nfields = 0).
+ * exactz_ws_correct_sequence is the case nfields = 1. */
+int exactz_ws_correct_batch_sequence(exactz_workspace *ws, uint32_t nsteps, uint32_t nfields,
+                                     const exactz_dims *dims, const float *const *f,
+                                     const float *const *fhat, const float *xi, const exactz_opts *opts,
+                                     float *const *g_out, exactz_edit *const *edits_out,
+                                     const uint64_t *edits_cap, exactz_result *res, void *cuda_stream);
+
 /* Statistics of the last exactz_ws_correct on a workspace.  stage_ms holds
  * CUDA-event times on the call's stream when opts.profile was 1 (else 0):
  * [0] set-up stencil kernel, [1] critical-point compaction, [2] radix sort

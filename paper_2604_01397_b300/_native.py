@@ -81,7 +81,7 @@ STAGES = ["setup", "compact", "sort", "first_pass", "loop", "finish", "edit_list
 assert ctypes.sizeof(Edit) == 16 and ctypes.sizeof(Result) == 48
 
 EXPORTS = ["exactz_default_opts", "exactz_correct", "exactz_correct_batch", "exactz_workspace_create",
-           "exactz_workspace_destroy", "exactz_workspace_bytes", "exactz_ws_correct", "exactz_ws_correct_sequence", "exactz_classify",
+           "exactz_workspace_destroy", "exactz_workspace_bytes", "exactz_ws_correct", "exactz_ws_correct_sequence", "exactz_ws_correct_batch_sequence", "exactz_classify",
            "exactz_cp_order", "exactz_version", "exactz_ws_stats", "exactz_correct_noalloc",
            "exactz_ws_get_tuning", "exactz_ws_set_tuning", "exactz_ws_autotune", "exactz_server_create",
            "exactz_server_submit", "exactz_server_poll", "exactz_server_wait", "exactz_server_stats",
@@ -124,6 +124,10 @@ def lib():
                                              ctypes.POINTER(Opts), PP, PP, ctypes.POINTER(ctypes.c_uint64),
                                              ctypes.POINTER(Result), P]
     L.exactz_ws_correct_sequence.restype = ctypes.c_int
+    L.exactz_ws_correct_batch_sequence.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Dims), PP, PP,
+                                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Opts), PP, PP,
+                                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), P]
+    L.exactz_ws_correct_batch_sequence.restype = ctypes.c_int
     L.exactz_ws_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
     L.exactz_ws_get_tuning.restype = ctypes.c_int
     L.exactz_ws_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]

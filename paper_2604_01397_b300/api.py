@@ -256,6 +256,68 @@ class Workspace:
             out.append(r)
         return out
 
+    def correct_batch_sequence(self, fs, fhats, xis, g_outs, edit_bufs=None, dims=None, N_steps: int = 5,
+                               mode: str = "graph", max_iters: int = 1_000_000, stream=None,
+                               raise_on_error: bool = True, events: str = "reformulated",
+                               direction: str = "decreasing") -> List[List[dict]]:
+        """Correct a sequence of batches of host-resident fields
+        (exactz_ws_correct_batch_sequence): fs[s][j], fhats[s][j], xis[s][j],
+        g_outs[s][j] (and edit_bufs[s][j]) for step s and field j, field j of
+        every step having dims[j] (default: the shapes of fs[0]).  Step s+1 is
+        copied in and step s-1 copied out while step s is corrected.  Host
+        tensors as for correct_sequence.  Returns the result dicts per step."""
+        ns = len(fs)
+        nf = len(fs[0]) if ns else 0
+        for name, arr in (("fhats", fhats), ("xis", xis), ("g_outs", g_outs)) + (
+                (("edit_bufs", edit_bufs),) if edit_bufs is not None else ()):
+            if len(arr) != ns or any(len(x) != nf for x in arr):
+                raise ValueError(f"{name} must have one entry per step and field")
+        if ns == 0:
+            return []
+        dl = [dims_of(fs[0][j], dims[j] if dims else None) for j in range(nf)]
+        flat = lambda a: [x for step in a for x in step]  # noqa: E731
+        F, H, X, G = flat(fs), flat(fhats), flat(xis), flat(g_outs)
+        E = flat(edit_bufs) if edit_bufs is not None else None
+        for i in range(ns * nf):
+            nv = dl[i % nf][0] * dl[i % nf][1] * dl[i % nf][2]
+            _check(F[i], "f", True)
+            _check(H[i], "fhat", True)
+            if F[i].numel() != nv or H[i].numel() != nv or G[i].numel() != nv:
+                raise ValueError(f"item {i}: f, fhat and g_out must hold {nv} values")
+            if G[i].is_cuda or G[i].dtype != torch.float32 or not G[i].is_contiguous():
+                raise ValueError(f"item {i}: g_out must be a contiguous float32 host tensor")
+            if E is not None:
+                b = E[i]
+                if b.is_cuda or b.dtype != torch.uint8 or b.dim() != 2 or b.shape[1] != 16 or not b.is_contiguous():
+                    raise ValueError(f"item {i}: edit buffer must be a contiguous (cap, 16) uint8 host tensor")
+        n = ns * nf
+        xarr = (ctypes.c_float * n)(*[float(np.float32(x)) for x in X])
+        caps = [b.shape[0] for b in E] if E is not None else [0] * n
+        carr = (ctypes.c_uint64 * n)(*caps)
+        res = (N.Result * n)()
+        o = make_opts(N_steps, mode, max_iters, E is not None, False, events, direction)
+        rc = N.lib().exactz_ws_correct_batch_sequence(
+            self._h, ns, nf, (N.Dims * nf)(*[N.Dims(*d) for d in dl]), N.ptr_array([t.data_ptr() for t in F]),
+            N.ptr_array([t.data_ptr() for t in H]), xarr, ctypes.byref(o), N.ptr_array([t.data_ptr() for t in G]),
+            N.ptr_array([b.data_ptr() for b in E] if E is not None else [0] * n), carr, res,
+            ctypes.c_void_p(_stream(stream)))
+        if rc not in (N.EXACTZ_OK, N.EXACTZ_ECAP) and raise_on_error:
+            raise ExactzError(rc, "exactz_ws_correct_batch_sequence")
+        out = []
+        for st in range(ns):
+            row = []
+            for j in range(nf):
+                i = st * nf + j
+                r = _result_dict(res[i])
+                r["rc"] = rc
+                r["g"] = G[i]
+                if E is not None:
+                    r["edits"] = decode_edits(E[i], r["n_edits"])
+                    r["edits_truncated"] = r["n_edits"] > caps[i]
+                row.append(r)
+            out.append(row)
+        return out
+
 
 def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, dims=None, N_steps: int = 5,
             mode: str = "graph", max_iters: int = 1_000_000, edits: bool = True, edits_cap=None,

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -630,10 +631,13 @@ int event_setup(exactz_workspace *ws, Dev &D, const Layout &L, cudaStream_t s, u
     return EXACTZ_OK;
 }
 
+// after_launch, if set, is called once the pass loop is queued (the graph
+// launched, or the host-driven loop done): the batch sequence queues the next
+// step's bulk copies there, behind this call's own small uploads.
 int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *const *fhat,
         const exactz_dims *d, const float *xi, const exactz_opts *o, float *const *g_out,
         exactz_edit *const *edits_out, const uint64_t *caps, exactz_result *res, cudaStream_t s,
-        int host)
+        int host, const std::function<bool()> &after_launch = {})
 {
     exactz_opts opt;
     exactz_default_opts(&opt);
@@ -783,6 +787,7 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
         if ((rc = ensure_graph(ws, D, opt.mode == EXACTZ_MODE_FUSED)) != EXACTZ_OK) return rc;
         CK(cudaGraphLaunch(ws->gexec, s));
         launches += 1;  // loop-flag kernel; the body's kernels per pass are added below
+        if (after_launch && !after_launch()) return EXACTZ_ENODEV;
     } else {
         for (;;) {
             CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -809,6 +814,8 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
             loop_passes++;
             CK(cudaGetLastError());
         }
+        // (after the loop: its per-pass state reads never wait behind bulk copies)
+        if (after_launch && !after_launch()) return EXACTZ_ENODEV;
     }
     mark(5);
     bool padded = false;
@@ -1028,12 +1035,12 @@ int exactz_ws_correct(exactz_workspace *ws, uint32_t nfields, const float *const
                static_cast<cudaStream_t>(cuda_stream), host_buffers);
 }
 
-int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const float *const *f,
-                               const float *const *fhat, exactz_dims d, const float *xi,
-                               const exactz_opts *opts, float *const *g_out, exactz_edit *const *edits_out,
-                               const uint64_t *edits_cap, exactz_result *res, void *cuda_stream)
+int exactz_ws_correct_batch_sequence(exactz_workspace *ws, uint32_t nsteps, uint32_t nfields, const exactz_dims *dims,
+                                     const float *const *f, const float *const *fhat, const float *xi,
+                                     const exactz_opts *opts, float *const *g_out, exactz_edit *const *edits_out,
+                                     const uint64_t *edits_cap, exactz_result *res, void *cuda_stream)
 {
-    if (!ws || !f || !fhat || !xi || !g_out || !res) return EXACTZ_EINVAL;
+    if (!ws || !dims || !f || !fhat || !xi || !g_out || !res || nfields == 0) return EXACTZ_EINVAL;
     exactz_opts opt;
     exactz_default_opts(&opt);
     if (opts) opt = *opts;
@@ -1041,60 +1048,94 @@ int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const floa
         opt.direction > EXACTZ_EDITS_INCREASING)
         return EXACTZ_EINVAL;
     Layout L;
-    if (int rc = make_layout(1, &d, L)) return rc;
-    const uint64_t n = L.fd[0].n;
-    uint64_t ecap = 0;
-    for (uint32_t i = 0; i < nitems; i++) {
+    if (int rc = make_layout(nfields, dims, L)) return rc;
+    const uint64_t items = (uint64_t)nsteps * nfields;
+    // each field's edit records have one region in a slot, sized for its largest cap over the steps
+    std::vector<uint64_t> eoff(nfields + 1, 0);
+    for (uint64_t i = 0; i < items; i++) {
         if (!f[i] || !fhat[i] || !g_out[i]) return EXACTZ_EINVAL;
         if (!(xi[i] > 0.0f) || !std::isfinite(xi[i])) return EXACTZ_EINVAL;
-        if (edits_out && edits_out[i] && edits_cap) ecap = std::max<uint64_t>(ecap, edits_cap[i]);
     }
-    std::memset(res, 0, sizeof(exactz_result) * nitems);
-    if (nitems == 0) return EXACTZ_OK;
+    for (uint32_t j = 0; j < nfields; j++) {
+        uint64_t cap = 0;
+        for (uint32_t st = 0; st < nsteps; st++) {
+            const uint64_t i = (uint64_t)st * nfields + j;
+            if (edits_out && edits_out[i] && edits_cap) cap = std::max<uint64_t>(cap, edits_cap[i]);
+        }
+        eoff[j + 1] = eoff[j] + cap;
+    }
+    std::memset(res, 0, sizeof(exactz_result) * items);
+    if (nsteps == 0) return EXACTZ_OK;
     std::lock_guard<std::mutex> lk(ws->mu);
     CK(cudaSetDevice(ws->device));
-    if (int rc = grow_sequence(ws, n, opt.want_edit_list ? ecap : 0)) return rc;
+    if (int rc = grow_sequence(ws, L.total_v, opt.want_edit_list ? eoff[nfields] : 0)) return rc;
     const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // the copies in start after the caller's earlier work on its stream
     CK(cudaEventRecord(ws->sq_start, s));
     CK(cudaStreamWaitEvent(ws->sq_in, ws->sq_start, 0));
-    auto copy_in = [&](uint32_t i) -> bool {
-        const int b = (int)(i & 1u);
-        return cudaMemcpyAsync(ws->sq_f[b], f[i], n * 4, cudaMemcpyHostToDevice, ws->sq_in) == cudaSuccess &&
-               cudaMemcpyAsync(ws->sq_fhat[b], fhat[i], n * 4, cudaMemcpyHostToDevice, ws->sq_in) == cudaSuccess &&
-               cudaEventRecord(ws->sq_in_ev[b], ws->sq_in) == cudaSuccess;
-    };
-    int ret = copy_in(0) ? EXACTZ_OK : EXACTZ_ENODEV;
-    for (uint32_t i = 0; i < nitems && (ret == EXACTZ_OK || ret == EXACTZ_ECAP); i++) {
-        const int b = (int)(i & 1u);
-        // the next field's inputs go to the other slot, whose field (i - 1) is finished
-        if (i + 1 < nitems && !copy_in(i + 1)) {
-            ret = EXACTZ_ENODEV;
-            break;
+    auto copy_in = [&](uint32_t st) -> bool {
+        const int b = (int)(st & 1u);
+        for (uint32_t j = 0; j < nfields; j++) {
+            const uint64_t i = (uint64_t)st * nfields + j, n = L.fd[j].n, v = L.fd[j].vbase;
+            if (cudaMemcpyAsync(ws->sq_f[b] + v, f[i], n * 4, cudaMemcpyHostToDevice, ws->sq_in) != cudaSuccess ||
+                cudaMemcpyAsync(ws->sq_fhat[b] + v, fhat[i], n * 4, cudaMemcpyHostToDevice, ws->sq_in) !=
+                    cudaSuccess)
+                return false;
         }
-        // this slot's inputs have landed and its outputs (field i - 2) have left
+        return cudaEventRecord(ws->sq_in_ev[b], ws->sq_in) == cudaSuccess;
+    };
+    std::vector<const float *> fi(nfields), hi(nfields);
+    std::vector<float *> gi(nfields);
+    std::vector<exactz_edit *> ei(nfields);
+    std::vector<uint64_t> ci(nfields);
+    int ret = copy_in(0) ? EXACTZ_OK : EXACTZ_ENODEV;
+    for (uint32_t st = 0; st < nsteps && (ret == EXACTZ_OK || ret == EXACTZ_ECAP); st++) {
+        const int b = (int)(st & 1u);
+        const uint64_t i0 = (uint64_t)st * nfields;
+        // this slot's inputs have landed and its outputs (step st - 2) have left
         if (cudaStreamWaitEvent(s, ws->sq_in_ev[b], 0) != cudaSuccess ||
             cudaStreamWaitEvent(s, ws->sq_out_ev[b], 0) != cudaSuccess) {
             ret = EXACTZ_ENODEV;
             break;
         }
-        const float *fi = ws->sq_f[b], *hi = ws->sq_fhat[b];
-        float *gi = ws->sq_g[b];
-        const bool want = opt.want_edit_list && edits_out && edits_out[i] && edits_cap && edits_cap[i] > 0;
-        exactz_edit *ei = want ? reinterpret_cast<exactz_edit *>(ws->sq_edits[b]) : nullptr;
-        const uint64_t ci = want ? edits_cap[i] : 0;
-        const int rc = run(ws, 1, &fi, &hi, &d, &xi[i], &opt, &gi, &ei, &ci, &res[i], s, 0);
+        for (uint32_t j = 0; j < nfields; j++) {
+            const uint64_t i = i0 + j, v = L.fd[j].vbase;
+            fi[j] = ws->sq_f[b] + v;
+            hi[j] = ws->sq_fhat[b] + v;
+            gi[j] = ws->sq_g[b] + v;
+            const bool want = opt.want_edit_list && edits_out && edits_out[i] && edits_cap && edits_cap[i] > 0;
+            ei[j] = want ? reinterpret_cast<exactz_edit *>(ws->sq_edits[b] + eoff[j]) : nullptr;
+            ci[j] = want ? edits_cap[i] : 0;
+        }
+        // the next step's inputs go to the other slot, whose step (st - 1) is
+        // finished, once this step's loop is queued: copies queued earlier
+        // would hold up this step's own small uploads on the copy engine
+        bool next_in = st + 1 >= nsteps;
+        const auto queue_next = [&]() -> bool {
+            next_in = true;
+            return copy_in(st + 1);
+        };
+        const std::function<bool()> hook = st + 1 < nsteps ? std::function<bool()>(queue_next) : nullptr;
+        int rc = run(ws, nfields, fi.data(), hi.data(), dims, &xi[i0], &opt, gi.data(), ei.data(), ci.data(),
+                     &res[i0], s, 0, hook);
+        if (rc == EXACTZ_OK || rc == EXACTZ_ECAP) {
+            if (!next_in && !copy_in(st + 1)) rc = EXACTZ_ENODEV;  // run() ended before its loop
+        }
         if (rc != EXACTZ_OK && rc != EXACTZ_ECAP) {
             ret = rc;
             break;
         }
         if (rc == EXACTZ_ECAP) ret = rc;
-        // run() returned with the field finished: its results leave on the copy-out stream
-        bool ok = cudaMemcpyAsync(g_out[i], gi, n * 4, cudaMemcpyDeviceToHost, ws->sq_out) == cudaSuccess;
-        const uint64_t ne = want ? std::min<uint64_t>(res[i].n_edits, ci) : 0;
-        if (ok && ne)
-            ok = cudaMemcpyAsync(edits_out[i], ei, ne * sizeof(EditRec), cudaMemcpyDeviceToHost, ws->sq_out) ==
-                 cudaSuccess;
+        // run() returned with the step finished: its results leave on the copy-out stream
+        bool ok = true;
+        for (uint32_t j = 0; j < nfields && ok; j++) {
+            const uint64_t i = i0 + j;
+            ok = cudaMemcpyAsync(g_out[i], gi[j], L.fd[j].n * 4, cudaMemcpyDeviceToHost, ws->sq_out) == cudaSuccess;
+            const uint64_t ne = ei[j] ? std::min<uint64_t>(res[i].n_edits, ci[j]) : 0;
+            if (ok && ne)
+                ok = cudaMemcpyAsync(edits_out[i], ei[j], ne * sizeof(EditRec), cudaMemcpyDeviceToHost,
+                                     ws->sq_out) == cudaSuccess;
+        }
         if (!ok || cudaEventRecord(ws->sq_out_ev[b], ws->sq_out) != cudaSuccess) {
             ret = EXACTZ_ENODEV;
             break;
@@ -1107,6 +1148,16 @@ int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const floa
         if (ret == EXACTZ_OK || ret == EXACTZ_ECAP) ret = EXACTZ_ENODEV;
     }
     return ret;
+}
+
+int exactz_ws_correct_sequence(exactz_workspace *ws, uint32_t nitems, const float *const *f,
+                               const float *const *fhat, exactz_dims d, const float *xi,
+                               const exactz_opts *opts, float *const *g_out, exactz_edit *const *edits_out,
+                               const uint64_t *edits_cap, exactz_result *res, void *cuda_stream)
+{
+    // a sequence of one-field batches
+    return exactz_ws_correct_batch_sequence(ws, nitems, 1, &d, f, fhat, xi, opts, g_out, edits_out, edits_cap, res,
+                                            cuda_stream);
 }
 
 int exactz_ws_get_tuning(const exactz_workspace *ws, exactz_tuning *out)

@@ -138,3 +138,58 @@ def test_fields_larger_than_the_workspace_are_refused():
                             [xi for *_, xi in fields], gs, es, dims=DIMS)
     assert e.value.rc == -7  # EXACTZ_ESIZE, before any kernel of the first field
     ws.close()
+
+
+BATCH = [(37, 33, 9), (16, 24, 12), (64, 5, 7)]  # uneven shapes; ragged rows (nx % 4 != 0 and == 0)
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_batch_sequence_each_field_equals_oracle(steps):
+    # exactz_ws_correct_batch_sequence: steps of a batch of uneven fields, each
+    # field of each step as the oracle gives it alone; more steps than device
+    # slots, per-field output buffers in every step
+    import paper_2604_01397_b300 as ez
+
+    items = [[None] * len(BATCH) for _ in range(steps)]
+    for s in range(steps):
+        for j, d in enumerate(BATCH):
+            f, fh, xi = synth.make_case("bumps", d, 100 + 10 * s + j, 2e-2, "uniform", n_bumps=6, sigma=(1.5, 3.0))
+            items[s][j] = (f.numpy().reshape(-1).copy(), fh.numpy().reshape(-1).copy(), xi)
+    ws = ez.Workspace(BATCH)
+    gs = [[torch.empty(f.size, dtype=torch.float32).pin_memory() for f, _, _ in row] for row in items]
+    es = [[torch.empty((f.size, 16), dtype=torch.uint8).pin_memory() for f, _, _ in row] for row in items]
+    rs = ws.correct_batch_sequence([[_pinned(f) for f, _, _ in row] for row in items],
+                                   [[_pinned(h) for _, h, _ in row] for row in items],
+                                   [[xi for *_, xi in row] for row in items], gs, es, dims=BATCH)
+    torch.cuda.synchronize()
+    assert len(rs) == steps
+    for s in range(steps):
+        for j, d in enumerate(BATCH):
+            f, fh, xi = items[s][j]
+            assert_same(rs[s][j], oracle_run(f, fh, xi, d), f.size)
+    # the batch corrected device-resident gives the same (the one-step case)
+    dev = [ws.correct([torch.from_numpy(f).cuda() for f, _, _ in items[-1]],
+                      [torch.from_numpy(h).cuda() for _, h, _ in items[-1]], [xi for *_, xi in items[-1]],
+                      dims=BATCH)]
+    for r, rd in zip(rs[-1], dev[0]):
+        assert np.array_equal(r["g"].numpy().view(np.uint32), rd["g"].reshape(-1).cpu().numpy().view(np.uint32))
+    ws.close()
+
+
+def test_batch_sequence_refuses_bad_input_before_any_copy():
+    import paper_2604_01397_b300 as ez
+
+    ws = ez.Workspace(BATCH)
+    row = []
+    for j, d in enumerate(BATCH):
+        f, fh, xi = synth.make_case("bumps", d, 200 + j, 2e-2, "uniform", n_bumps=6, sigma=(1.5, 3.0))
+        row.append((f.numpy().reshape(-1).copy(), fh.numpy().reshape(-1).copy(), xi))
+    gs = [[torch.empty(f.size, dtype=torch.float32).pin_memory() for f, _, _ in row]]
+    with pytest.raises(ez.ExactzError) as e:  # xi = 0 for one field
+        ws.correct_batch_sequence([[_pinned(f) for f, _, _ in row]], [[_pinned(h) for _, h, _ in row]],
+                                  [[row[0][2], 0.0, row[2][2]]], gs, dims=BATCH)
+    assert e.value.rc == ez._native.EXACTZ_EINVAL
+    with pytest.raises(ValueError):  # a step with a field missing never reaches the library
+        ws.correct_batch_sequence([[_pinned(f) for f, _, _ in row][:2]], [[_pinned(h) for _, h, _ in row]],
+                                  [[xi for *_, xi in row]], gs, dims=BATCH)
+    ws.close()
