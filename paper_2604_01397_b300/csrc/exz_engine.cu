@@ -631,9 +631,10 @@ int event_setup(exactz_workspace *ws, Dev &D, const Layout &L, cudaStream_t s, u
     return EXACTZ_OK;
 }
 
-// after_launch, if set, is called once the pass loop is queued (the graph
-// launched, or the host-driven loop done): the batch sequence queues the next
-// step's bulk copies there, behind this call's own small uploads.
+// after_launch, if set, is called once this call has queued its own uploads
+// (graph loops, which read nothing back until they end) or once its
+// host-driven loop is done: the batch sequence queues the next step's bulk
+// copies there, so that they hold up none of this call's small copies.
 int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *const *fhat,
         const exactz_dims *d, const float *xi, const exactz_opts *o, float *const *g_out,
         exactz_edit *const *edits_out, const uint64_t *caps, exactz_result *res, cudaStream_t s,
@@ -741,6 +742,12 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     CK(cudaMemsetAsync(ws->pin_tile_bits, 0, (L.total_tiles / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->pairbits, 0, (events ? 3 * ((ws->cap_real + 31) / 32) + 1 : L.total_real / 32 + 1) * 4, s));
     CK(cudaMemsetAsync(ws->apply_flag, 0, L.total_tiles, s));
+    // the graph loop reads nothing back before it ends (the event set-up does,
+    // once per pointer-jumping round): the caller's bulk copies may start now,
+    // behind this call's uploads
+    const bool in_graph = opt.mode == EXACTZ_MODE_GRAPH || opt.mode == EXACTZ_MODE_FUSED;
+    const bool early_hook = in_graph && !events;
+    if (early_hook && after_launch && !after_launch()) return EXACTZ_ENODEV;
     Dev D = make_dev(ws, L);
     D.events = events ? 1u : 0u;
     if (nf > 1 && ws->tile_field) {  // the field of each tile: one load instead of a search over the fields
@@ -782,12 +789,11 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     launches += 1 + 4 + 3 * P + 3;
     CK(cudaGetLastError());
 
-    const bool in_graph = opt.mode == EXACTZ_MODE_GRAPH || opt.mode == EXACTZ_MODE_FUSED;
     if (in_graph) {
         if ((rc = ensure_graph(ws, D, opt.mode == EXACTZ_MODE_FUSED)) != EXACTZ_OK) return rc;
         CK(cudaGraphLaunch(ws->gexec, s));
         launches += 1;  // loop-flag kernel; the body's kernels per pass are added below
-        if (after_launch && !after_launch()) return EXACTZ_ENODEV;
+        if (!early_hook && after_launch && !after_launch()) return EXACTZ_ENODEV;
     } else {
         for (;;) {
             CK(cudaMemcpyAsync(ws->h_ls, ws->d_ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
