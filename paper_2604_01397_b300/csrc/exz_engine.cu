@@ -826,15 +826,17 @@ int run(exactz_workspace *ws, uint32_t nf, const float *const *f, const float *c
     mark(5);
     bool padded = false;
     for (uint32_t i = 0; i < nf; i++) padded = padded || L.fd[i].gm;
-    if (padded) launch_unmirror(D, s);  // g of the fields kept in padded copies, in place for what follows
-    // residual violations on pinned vertices and status; beside them the edit
-    // list (the edit counts are final; the residual check writes only request
-    // bits, flags and counters the edit list does not read)
+    // residual violations on pinned vertices and status; beside them g of the
+    // fields kept in padded copies copied back (the residual check reads g from
+    // those copies), then the edit list (the edit counts are final; the
+    // residual check writes only request bits, flags and counters that neither
+    // reads)
     cudaStream_t es = ws->aux ? ws->aux : s;
     if (es != s) {
         CK(cudaEventRecord(ws->aux_fork, s));
         CK(cudaStreamWaitEvent(es, ws->aux_fork, 0));
     }
+    if (padded) launch_unmirror(D, es);
     launch_edit_list(D, FS, opt.want_edit_list ? 1 : 0, es);
     launch_check_pinned(D, FS, s);
     launch_pairs_pinned(D, FS, s);
